@@ -1,0 +1,370 @@
+"""FP64 CPU oracle for the multi-RHS Dirac operators and solvers of
+Duerr, arXiv:2112.14640.
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py``; never by the library.  It shares no
+code with the CUDA path.
+
+The stencils live in ``oracle.c`` (plain loops over the paper's equations);
+this module adds the composite operators the paper builds from them
+(D^dagger = gamma5 D gamma5 or epsilon D epsilon, D^dagger D), textbook CG and
+BiCGstab with the paper's recompute/exit rules (Sec. 9), the Lanczos
+condition estimate of the ``cond`` module (App. F), the App. E flop counts
+and the fermion force of S = phi^dag (D_W^dag D_W)^-1 phi (derived here; the
+paper has none).
+
+Array shapes (complex128, C order):
+  links  U   (Nt, Nz, Ny, Nx, 4, Nc, Nc)      mu = 0..3 <-> x, y, z, t
+  W links    (Nt, Nz, Ny, Nx, 81, Nc, Nc)     see ``oracle.c`` for dir numbering
+  Wilson-type vectors (Nt, Nz, Ny, Nx, Nc, 4, Nv)
+  staggered vectors   (Nt, Nz, Ny, Nx, Nc, Nv)
+``dims`` is always (Nx, Ny, Nz, Nt).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+WILSON, BRILLOUIN, STAGGERED = 0, 1, 2
+KIND_NAMES = {WILSON: "wilson", BRILLOUIN: "brillouin", STAGGERED: "staggered"}
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(_build.build())
+        P = ctypes.c_void_p
+        I4 = ctypes.POINTER(ctypes.c_int)
+        I = ctypes.c_int
+        D = ctypes.c_double
+        _lib.orc_phase_links.argtypes = [I4, I, I4, P, P]
+        _lib.orc_wilson.argtypes = [I4, I, I, P, D, P, P]
+        _lib.orc_staggered.argtypes = [I4, I, I, P, D, P, P]
+        _lib.orc_brillouin.argtypes = [I4, I, I, P, D, P, P]
+        _lib.orc_build_w.argtypes = [I4, I, P, P]
+        _lib.orc_gamma5.argtypes = [I4, I, I, P, P]
+        _lib.orc_epsilon.argtypes = [I4, I, I, P, P]
+        _lib.orc_gamma.argtypes = [I, P]
+        for f in (_lib.orc_phase_links, _lib.orc_wilson, _lib.orc_staggered, _lib.orc_brillouin,
+                  _lib.orc_build_w, _lib.orc_gamma5, _lib.orc_epsilon, _lib.orc_gamma):
+            f.restype = None
+    return _lib
+
+
+def _i4(v):
+    return (ctypes.c_int * 4)(*[int(a) for a in v])
+
+
+def _p(a):
+    assert a.dtype == np.complex128 and a.flags.c_contiguous
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _dims_of_links(U):
+    nt, nz, ny, nx = U.shape[:4]
+    return (nx, ny, nz, nt), U.shape[-1]
+
+
+# ----------------------------------------------------------------- primitives
+
+def gamma(mu):
+    """4x4 chiral gamma matrix gamma_{mu+1} (App. A)."""
+    g = np.zeros((4, 4), np.complex128)
+    lib().orc_gamma(int(mu), _p(g))
+    return g
+
+
+def phase_links(U, bc):
+    """Links with the boundary phase bc[mu] folded into U_mu(n) where n_mu = N_mu - 1."""
+    dims, nc = _dims_of_links(U)
+    U = np.ascontiguousarray(U, np.complex128)
+    out = np.empty_like(U)
+    lib().orc_phase_links(_i4(dims), nc, _i4(bc), _p(U), _p(out))
+    return out
+
+
+def build_w(Up):
+    """All 81 W_s(n) (Tab. off-axis) from phased links, by k!-path enumeration."""
+    dims, nc = _dims_of_links(Up)
+    Up = np.ascontiguousarray(Up, np.complex128)
+    W = np.empty(Up.shape[:4] + (81, nc, nc), np.complex128)
+    lib().orc_build_w(_i4(dims), nc, _p(Up), _p(W))
+    return W
+
+
+def _stencil(fn, dims, nc, nv, field, m0, v):
+    v = np.ascontiguousarray(v, np.complex128)
+    out = np.empty_like(v)
+    fn(_i4(dims), nc, nv, _p(np.ascontiguousarray(field)), float(m0), _p(v), _p(out))
+    return out
+
+
+def wilson(Up, m0, psi):
+    """Eq. (app_wils) with already-phased links."""
+    dims, nc = _dims_of_links(Up)
+    return _stencil(lib().orc_wilson, dims, nc, psi.shape[-1], Up, m0, psi)
+
+
+def staggered(Up, m0, phi):
+    """Eq. (def_stag) with already-phased links."""
+    dims, nc = _dims_of_links(Up)
+    return _stencil(lib().orc_staggered, dims, nc, phi.shape[-1], Up, m0, phi)
+
+
+def brillouin(W, m0, psi):
+    """Eq. (app_bril) with W from ``build_w``."""
+    nt, nz, ny, nx = W.shape[:4]
+    nc = W.shape[-1]
+    return _stencil(lib().orc_brillouin, (nx, ny, nz, nt), nc, psi.shape[-1], W, m0, psi)
+
+
+def gamma5(psi):
+    nt, nz, ny, nx, nc, _, nv = psi.shape
+    psi = np.ascontiguousarray(psi, np.complex128)
+    out = np.empty_like(psi)
+    lib().orc_gamma5(_i4((nx, ny, nz, nt)), nc, nv, _p(psi), _p(out))
+    return out
+
+
+def epsilon(phi):
+    nt, nz, ny, nx, nc, nv = phi.shape
+    phi = np.ascontiguousarray(phi, np.complex128)
+    out = np.empty_like(phi)
+    lib().orc_epsilon(_i4((nx, ny, nz, nt)), nc, nv, _p(phi), _p(out))
+    return out
+
+
+# ------------------------------------------------------------ operator object
+
+class Operator:
+    """D in {D_W, D_B, D_S} on a fixed gauge field, with its dagger and D^dag D.
+
+    D_W^dag = gamma5 D_W gamma5, D_B^dag = gamma5 D_B gamma5 and
+    D_S^dag = epsilon D_S epsilon, the forms the paper's solvers use (App. F).
+    """
+
+    def __init__(self, kind, U, bc=(1, 1, 1, 1), m0=0.0):
+        self.kind = kind
+        self.m0 = float(m0)
+        self.bc = tuple(int(b) for b in bc)
+        self.Up = phase_links(U, self.bc)
+        self.W = build_w(self.Up) if kind == BRILLOUIN else None
+
+    def apply(self, v, m0=None):
+        m = self.m0 if m0 is None else m0
+        if self.kind == WILSON:
+            return wilson(self.Up, m, v)
+        if self.kind == BRILLOUIN:
+            return brillouin(self.W, m, v)
+        return staggered(self.Up, m, v)
+
+    def _sandwich(self, v):
+        return epsilon(v) if self.kind == STAGGERED else gamma5(v)
+
+    def apply_dagger(self, v, m0=None):
+        return self._sandwich(self.apply(self._sandwich(v), m0))
+
+    def apply_normal(self, v, m0=None):
+        return self.apply_dagger(self.apply(v, m0), m0)
+
+
+# ------------------------------------------------------------- BLAS-1 helpers
+
+def norm2(v):
+    """Per-RHS squared 2-norms (last axis = RHS), accumulated in FP64."""
+    a = v.reshape(-1, v.shape[-1])
+    return np.sum(a.real ** 2 + a.imag ** 2, axis=0)
+
+
+def dot(u, v):
+    """Per-RHS <u, v>, linear in the second argument (Sec. 3 convention)."""
+    a = u.reshape(-1, u.shape[-1])
+    b = v.reshape(-1, v.shape[-1])
+    return np.sum(np.conj(a) * b, axis=0)
+
+
+# --------------------------------------------------------------------- solvers
+
+CONVERGED, MAXIT, STAGNATED, BREAKDOWN = 0, 1, 2, 3
+
+
+def cg(apply_A, b, x0=None, tol=1e-10, maxit=10000, recompute_every=50):
+    """CG on an HPD operator, one independent recursion per RHS (Sec. 9).
+
+    Recompute r = b - A x when the iteration count is a multiple of
+    ``recompute_every``, when every active RHS's updated residual passes tol,
+    or at maxit.  Exit when every RHS's recomputed residual passes, when the
+    updated and recomputed norms of an unconverged RHS differ by more than
+    1%, or at maxit.  Reading for the paper's silent point: an RHS whose
+    recomputed residual passes is frozen (alpha = beta = 0).
+    Returns (x, info) with info holding iterations, recomputes, status, the
+    per-RHS CG coefficients (for the Lanczos estimate) and final residuals.
+    """
+    nv = b.shape[-1]
+    x = np.zeros_like(b) if x0 is None else np.array(x0, np.complex128)
+    nb = np.sqrt(norm2(b))
+    r = b - apply_A(x)
+    p = r.copy()
+    rr = norm2(r)
+    active = np.sqrt(rr) >= tol * nb
+    alphas, betas = [], []
+    it = recomputes = 0
+    status = CONVERGED
+    while active.any():
+        it += 1
+        q = apply_A(p)
+        pq = dot(p, q).real
+        alpha = np.where(active, rr / np.where(active, pq, 1.0), 0.0)
+        x += alpha * p
+        r -= alpha * q
+        rr_new = norm2(r)
+        alphas.append(alpha.copy())
+        if (it % recompute_every == 0 or np.all(np.sqrt(rr_new[active]) < tol * nb[active])
+                or it >= maxit):
+            recomputes += 1
+            rt = b - apply_A(x)
+            rr_true = norm2(rt)
+            disc = np.abs(np.sqrt(rr_new) - np.sqrt(rr_true)) / np.maximum(np.sqrt(rr_true), 1e-300)
+            r = rt
+            rr_new = rr_true
+            active &= ~(np.sqrt(rr_true) < tol * nb)
+            if not active.any():
+                break
+            if np.any(disc[active] > 0.01):
+                status = STAGNATED
+                break
+            if it >= maxit:
+                status = MAXIT
+                break
+        beta = np.where(active, rr_new / np.where(active, rr, 1.0), 0.0)
+        betas.append(beta.copy())
+        p = r + beta * p
+        rr = rr_new
+    res = np.sqrt(norm2(b - apply_A(x))) / nb
+    return x, dict(iters=it, recomputes=recomputes, status=status, relres=res,
+                   alphas=np.array(alphas).reshape(-1, nv), betas=np.array(betas).reshape(-1, nv))
+
+
+def cg_normal(op, b, x0=None, tol=1e-10, maxit=10000, recompute_every=50):
+    """Solve D^dag D x = D^dag b by CG; stopping on ||r_N|| / ||D^dag b|| < tol.
+
+    Reading (the paper's residual is defined for the system being solved):
+    the normal-equation residual decides convergence; the true ||b - D x|| / ||b||
+    is reported beside it as ``true_relres``.
+    """
+    bN = op.apply_dagger(b)
+    x, info = cg(op.apply_normal, bN, x0, tol, maxit, recompute_every)
+    info["true_relres"] = np.sqrt(norm2(b - op.apply(x))) / np.sqrt(norm2(b))
+    return x, info
+
+
+def bicgstab(op, b, x0=None, tol=1e-10, maxit=10000, recompute_every=50):
+    """BiCGstab (van der Vorst) on D x = b per RHS, shadow residual r_hat = r_0.
+
+    Same recompute/exit rules as ``cg``; breakdown (|rho| or |omega| below
+    1e-30 of its scale) marks that RHS as BREAKDOWN and freezes it.
+    """
+    nv = b.shape[-1]
+    x = np.zeros_like(b) if x0 is None else np.array(x0, np.complex128)
+    nb = np.sqrt(norm2(b))
+    r = b - op.apply(x)
+    rhat = r.copy()
+    rho = np.ones(nv, np.complex128)
+    alpha = np.ones(nv, np.complex128)
+    omega = np.ones(nv, np.complex128)
+    v = np.zeros_like(b)
+    p = np.zeros_like(b)
+    active = np.sqrt(norm2(r)) >= tol * nb
+    broken = np.zeros(nv, bool)
+    it = recomputes = 0
+    status = CONVERGED
+    while active.any():
+        it += 1
+        rho_new = dot(rhat, r)
+        bad = active & (np.abs(rho_new) < 1e-30 * np.sqrt(norm2(rhat) * norm2(r)))
+        broken |= bad
+        active &= ~bad
+        a_ = active
+        beta = np.where(a_, (rho_new / np.where(a_, rho, 1)) * (alpha / np.where(a_, omega, 1)), 0)
+        p = np.where(a_, r + beta * (p - omega * v), p)
+        v = op.apply(p)
+        rv = dot(rhat, v)
+        alpha = np.where(a_, rho_new / np.where(a_, rv, 1), 0)
+        s = r - alpha * v
+        t = op.apply(s)
+        tt = norm2(t)
+        omega = np.where(a_, dot(t, s) / np.where(a_ & (tt > 0), tt, 1), 0)
+        bad = a_ & (np.abs(omega) < 1e-30)
+        broken |= bad
+        x = x + np.where(a_, alpha * p + omega * s, 0)
+        r = np.where(a_, s - omega * t, r)
+        rho = np.where(a_, rho_new, rho)
+        active &= ~bad
+        rr = norm2(r)
+        if (it % recompute_every == 0 or np.all(np.sqrt(rr[active]) < tol * nb[active])
+                or it >= maxit):
+            recomputes += 1
+            rt = b - op.apply(x)
+            rr_true = norm2(rt)
+            disc = np.abs(np.sqrt(rr) - np.sqrt(rr_true)) / np.maximum(np.sqrt(rr_true), 1e-300)
+            r = rt
+            active &= ~(np.sqrt(rr_true) < tol * nb)
+            if not active.any():
+                break
+            if np.any(disc[active] > 0.01):
+                status = STAGNATED
+                break
+            if it >= maxit:
+                status = MAXIT
+                break
+    if broken.any() and status == CONVERGED:
+        status = BREAKDOWN
+    res = np.sqrt(norm2(b - op.apply(x))) / nb
+    return x, dict(iters=it, recomputes=recomputes, status=status, relres=res, broken=broken)
+
+
+def lanczos_tridiagonal(alphas, betas):
+    """Lanczos matrix of CG (the ``cond`` module, App. F), one per RHS.
+
+    With CG coefficients alpha_j, beta_j: diagonal 1/alpha_j + beta_{j-1}/alpha_{j-1},
+    off-diagonal sqrt(beta_j)/alpha_j.  Returns a list of (diag, offdiag).
+    """
+    out = []
+    alphas = np.asarray(alphas)
+    betas = np.asarray(betas)
+    for i in range(alphas.shape[1]):
+        a = alphas[:, i]
+        k = int(np.count_nonzero(a))
+        a = a[:k]
+        b = betas[:max(k - 1, 0), i]
+        diag = 1.0 / a
+        diag[1:] += b / a[:-1]
+        off = np.sqrt(b) / a[:-1]
+        out.append((diag, off))
+    return out
+
+
+def lanczos_cond(alphas, betas):
+    """(lambda_min, lambda_max) per RHS from the CG Lanczos matrix."""
+    res = []
+    for diag, off in lanczos_tridiagonal(alphas, betas):
+        T = np.diag(diag) + np.diag(off, 1) + np.diag(off, -1)
+        ev = np.linalg.eigvalsh(T)
+        res.append((ev[0], ev[-1]))
+    return np.array(res)
+
+
+# ------------------------------------------------------------ App. E counts
+
+def flops_per_site(kind, nc):
+    """Flops per site per RHS (App. E): Wilson 128Nc^2+72Nc, Brillouin
+    2560Nc^2+2376Nc, staggered 64Nc^2+2Nc."""
+    if kind == WILSON:
+        return 128 * nc * nc + 72 * nc
+    if kind == BRILLOUIN:
+        return 2560 * nc * nc + 2376 * nc
+    return 64 * nc * nc + 2 * nc

@@ -1,0 +1,362 @@
+"""Pins of the FP64 oracle to facts the paper and the mathematics fix.
+
+Nothing here compares the oracle with itself: every expectation is a closed
+form (free-field momentum-space symbols), an identity the operators must obey
+(gamma5-hermiticity, anti-hermiticity of the staggered hop, gauge covariance,
+W_{-s}(n) = W_s(n-s)^dag), a value the paper prints (the App. D eta phases,
+the App. E flop counts, the free-field spectral edges of Sec. 9), or a
+library routine on a dense brute-force matrix.
+"""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2112_14640_gb300 import inputs as I
+
+# Pauli matrices and the tensor-product form of the chiral gammas (App. A),
+# built here independently of the oracle's own tables.
+S0 = np.eye(2, dtype=complex)
+S1 = np.array([[0, 1], [1, 0]], complex)
+S2 = np.array([[0, -1j], [1j, 0]], complex)
+S3 = np.array([[1, 0], [0, -1]], complex)
+GAMMA = [np.kron(S2, S1), np.kron(S2, S2), np.kron(S2, S3), np.kron(S1, S0)]
+G5 = np.diag([1, 1, -1, -1]).astype(complex)
+
+
+def plane_wave(dims, p, chi):
+    """psi(n) = exp(i p.n) chi, chi of shape (Nc, 4, Nv) or (Nc, Nv)."""
+    nx, ny, nz, nt = dims
+    t, z, y, x = np.meshgrid(np.arange(nt), np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    ph = np.exp(1j * (p[0] * x + p[1] * y + p[2] * z + p[3] * t))
+    return ph[(...,) + (None,) * chi.ndim] * chi
+
+
+def momenta(dims, bc, rng, count):
+    out = []
+    for _ in range(count):
+        p = []
+        for mu in range(4):
+            k = rng.integers(0, dims[mu])
+            p.append(np.pi * (2 * k + 1) / dims[mu] if bc[mu] < 0 else 2 * np.pi * k / dims[mu])
+        out.append(np.array(p))
+    return out
+
+
+def wilson_symbol(p, m0):
+    return (m0 + np.sum(1 - np.cos(p))) * np.eye(4) + 1j * sum(GAMMA[m] * np.sin(p[m]) for m in range(4))
+
+
+def brillouin_symbol(p, m0):
+    lap = m0 + 2.0 * (1.0 - np.prod(np.cos(p / 2) ** 2))
+    der = sum(GAMMA[m] * np.sin(p[m]) * np.prod([2 + np.cos(p[n]) for n in range(4) if n != m]) / 27.0
+              for m in range(4))
+    return lap * np.eye(4) + 1j * der
+
+
+# ------------------------------------------------------------- gamma matrices
+
+def test_gammas_match_app_a_tensor_form_and_clifford():
+    for mu in range(4):
+        assert np.allclose(O.gamma(mu), GAMMA[mu], atol=0, rtol=0)
+    for a in range(4):
+        for b in range(4):
+            anti = GAMMA[a] @ GAMMA[b] + GAMMA[b] @ GAMMA[a]
+            assert np.allclose(anti, 2 * np.eye(4) * (a == b))
+    g5 = O.gamma(0) @ O.gamma(1) @ O.gamma(2) @ O.gamma(3)
+    assert np.allclose(g5, G5)
+
+
+# ---------------------------------------------------------------- free fields
+
+@pytest.mark.parametrize("bc", [(1, 1, 1, 1), (1, 1, 1, -1)])
+@pytest.mark.parametrize("nc", [1, 3])
+def test_wilson_free_field_symbol(bc, nc):
+    dims = (4, 4, 2, 6)
+    rng = np.random.default_rng(3)
+    m0 = 0.1
+    op = O.Operator(O.WILSON, I.unit_gauge_field(dims, nc), bc, m0)
+    for p in momenta(dims, bc, rng, 6):
+        chi = rng.standard_normal((nc, 4, 2)) + 1j * rng.standard_normal((nc, 4, 2))
+        out = op.apply(plane_wave(dims, p, chi))
+        want = plane_wave(dims, p, np.einsum("st,ctv->csv", wilson_symbol(p, m0), chi))
+        assert np.abs(out - want).max() < 1e-13
+
+
+@pytest.mark.parametrize("bc", [(1, 1, 1, 1), (1, 1, 1, -1)])
+def test_brillouin_free_field_symbol(bc):
+    dims = (4, 2, 4, 6)
+    rng = np.random.default_rng(4)
+    m0 = -0.3
+    op = O.Operator(O.BRILLOUIN, I.unit_gauge_field(dims, 3), bc, m0)
+    for p in momenta(dims, bc, rng, 6):
+        chi = rng.standard_normal((3, 4, 3)) + 1j * rng.standard_normal((3, 4, 3))
+        out = op.apply(plane_wave(dims, p, chi))
+        want = plane_wave(dims, p, np.einsum("st,ctv->csv", brillouin_symbol(p, m0), chi))
+        assert np.abs(out - want).max() < 1e-13
+
+
+@pytest.mark.parametrize("bc", [(1, 1, 1, 1), (1, 1, 1, -1), (-1, 1, -1, -1)])
+def test_staggered_normal_free_field(bc):
+    """D_S^dag D_S = m^2 + sum_mu sin^2 p_mu on every plane wave."""
+    dims = (4, 4, 6, 4)
+    rng = np.random.default_rng(5)
+    m0 = 0.05
+    op = O.Operator(O.STAGGERED, I.unit_gauge_field(dims, 3), bc, m0)
+    for p in momenta(dims, bc, rng, 6):
+        chi = rng.standard_normal((3, 2)) + 1j * rng.standard_normal((3, 2))
+        psi = plane_wave(dims, p, chi)
+        out = op.apply_normal(psi)
+        assert np.abs(out - (m0 ** 2 + np.sum(np.sin(p) ** 2)) * psi).max() < 1e-13
+
+
+def test_free_spectral_edges_sec9():
+    """Sec. 9: free D_B reaches Re z = 2 + m0, free D_W reaches 8 + m0 (at p = pi)."""
+    m0 = 0.01
+    p = np.full(4, np.pi)
+    assert np.allclose(np.linalg.eigvals(brillouin_symbol(p, m0)).real, 2 + m0)
+    assert np.allclose(np.linalg.eigvals(wilson_symbol(p, m0)).real, 8 + m0)
+    # and through the oracle on a 2^4 lattice, where p = pi is a lattice momentum
+    dims = (2, 2, 2, 2)
+    chi = np.zeros((3, 4, 1), complex)
+    chi[1, 2, 0] = 1
+    for kind, edge in ((O.WILSON, 8 + m0), (O.BRILLOUIN, 2 + m0)):
+        op = O.Operator(kind, I.unit_gauge_field(dims, 3), (1, 1, 1, 1), m0)
+        psi = plane_wave(dims, p, chi)
+        assert np.allclose(op.apply(psi), edge * psi, atol=1e-13)
+
+
+def test_staggered_eta_phases_app_d():
+    """App. D: eta_2 = -1 at (1-based) x = 1, eta_4 = -1 at x = y = z = 1, eta_3 = +1 there."""
+    dims = (4, 4, 4, 4)
+    op = O.Operator(O.STAGGERED, I.unit_gauge_field(dims, 1), (1, 1, 1, 1), 0.0)
+    phi = np.zeros((4, 4, 4, 4, 1, 1), complex)
+    phi[0, 0, 0, 0] = 1.0
+    out = op.apply(phi)[..., 0, 0]
+    # out[t, z, y, x]; neighbours of the origin reached by the forward hop
+    assert np.isclose(out[0, 0, 0, 3], +0.5)   # n = -x, eta_1 = 1
+    assert np.isclose(out[0, 0, 3, 0], -0.5)   # n = -y, eta_2 = (-1)^1
+    assert np.isclose(out[0, 3, 0, 0], +0.5)   # n = -z, eta_3 = (-1)^(1+1)
+    assert np.isclose(out[3, 0, 0, 0], -0.5)   # n = -t, eta_4 = (-1)^(1+1+1)
+    assert np.isclose(out[0, 0, 1, 0], +0.5)   # n = +y, backward hop: -eta_2/2
+    assert np.isclose(np.abs(out).sum(), 4.0)
+
+
+# ------------------------------------------------------ identities on random U
+
+def _dotc(a, b):
+    return np.vdot(a.ravel(), b.ravel())
+
+
+@pytest.mark.parametrize("kind", [O.WILSON, O.BRILLOUIN])
+@pytest.mark.parametrize("nc", [2, 3])
+def test_gamma5_hermiticity(kind, nc):
+    dims = (4, 2, 2, 4)
+    U = I.gauge_field(dims, nc, 0.4, seed=11)
+    op = O.Operator(kind, U, (1, 1, 1, -1), 0.1)
+    phi = I.source(dims, nc, 2, seed=1)
+    psi = I.source(dims, nc, 2, seed=2)
+    lhs = _dotc(phi, O.gamma5(op.apply(psi)))
+    rhs = np.conj(_dotc(psi, O.gamma5(op.apply(phi))))
+    assert abs(lhs - rhs) < 1e-11 * abs(lhs)
+    # the dagger used by the solvers is the adjoint
+    assert abs(_dotc(phi, op.apply(psi)) - _dotc(op.apply_dagger(phi), psi)) < 1e-11 * abs(lhs)
+
+
+def test_staggered_hop_antihermitian_and_dagger():
+    dims = (4, 4, 2, 2)
+    U = I.gauge_field(dims, 3, 0.4, seed=12)
+    op0 = O.Operator(O.STAGGERED, U, (1, 1, 1, -1), 0.0)
+    phi = I.source(dims, 3, 2, seed=3, staggered=True)
+    psi = I.source(dims, 3, 2, seed=4, staggered=True)
+    a = _dotc(phi, op0.apply(psi))
+    b = _dotc(psi, op0.apply(phi))
+    assert abs(a + np.conj(b)) < 1e-12 * abs(a)
+    op = O.Operator(O.STAGGERED, U, (1, 1, 1, -1), 0.3)
+    assert abs(_dotc(phi, op.apply(psi)) - _dotc(op.apply_dagger(phi), psi)) < 1e-11 * abs(a)
+
+
+def _transform_links(U, Om):
+    """U^Omega_mu(n) = Omega(n) U_mu(n) Omega(n+mu)^dag."""
+    out = np.empty_like(U)
+    for mu, ax in enumerate((3, 2, 1, 0)):
+        Om_f = np.roll(Om, -1, axis=ax)
+        out[..., mu, :, :] = Om @ U[..., mu, :, :] @ np.conj(np.swapaxes(Om_f, -1, -2))
+    return out
+
+
+@pytest.mark.parametrize("kind", [O.WILSON, O.BRILLOUIN, O.STAGGERED])
+def test_gauge_covariance(kind):
+    dims = (4, 2, 4, 2)
+    nc = 3
+    U = I.gauge_field(dims, nc, 0.5, seed=21)
+    Om = I.gauge_transform(dims, nc, seed=22)
+    stag = kind == O.STAGGERED
+    psi = I.source(dims, nc, 2, seed=23, staggered=stag)
+    bc = (1, -1, 1, -1)
+    op = O.Operator(kind, U, bc, 0.2)
+    opg = O.Operator(kind, _transform_links(U, Om), bc, 0.2)
+    rot = (lambda v: np.einsum("...ab,...bv->...av", Om, v)) if stag else \
+          (lambda v: np.einsum("...ab,...bsv->...asv", Om, v))
+    lhs = opg.apply(rot(psi))
+    rhs = rot(op.apply(psi))
+    assert np.abs(lhs - rhs).max() < 1e-12 * np.abs(rhs).max()
+
+
+# ------------------------------------------------------------- W-link facts
+
+def _offset(d):
+    return np.array([d % 3 - 1, (d // 3) % 3 - 1, (d // 9) % 3 - 1, (d // 27) % 3 - 1])
+
+
+def test_w_reflection_and_unitarity():
+    dims = (4, 4, 2, 4)
+    U = I.gauge_field(dims, 3, 0.4, seed=31)
+    W = O.build_w(O.phase_links(U, (1, 1, -1, -1)))
+    eye = np.eye(3)
+    assert np.allclose(W[..., 40, :, :], eye)
+    nonunit = 0
+    for d in range(81):
+        if d == 40:
+            continue
+        s = _offset(d)
+        k = int(np.abs(s).sum())
+        # W_{-s}(n) = W_s(n - s)^dag  (Tab. off-axis caption)
+        Ws_shift = np.roll(W[..., d, :, :], shift=(s[3], s[2], s[1], s[0]), axis=(0, 1, 2, 3))
+        assert np.abs(W[..., 80 - d, :, :] - np.conj(np.swapaxes(Ws_shift, -1, -2))).max() < 1e-14
+        dev = np.abs(W[..., d, :, :] @ np.conj(np.swapaxes(W[..., d, :, :], -1, -2)) - eye).max()
+        if k == 1:
+            assert dev < 1e-13
+        else:
+            assert dev > 1e-3
+            nonunit += 1
+    assert nonunit == 72   # 36 of the 40 stored directions, plus their reflections
+
+
+def test_w_commuting_constant_links():
+    """For constant commuting (diagonal) links every path gives prod_mu U_mu^{s_mu}:
+    pins the 1/k! normalisation and the orientation of each hop."""
+    dims = (3, 3, 3, 3)
+    rng = np.random.default_rng(8)
+    th = rng.uniform(-np.pi, np.pi, (4, 3))
+    th[:, 2] = -th[:, 0] - th[:, 1]
+    U = np.zeros((3, 3, 3, 3, 4, 3, 3), complex)
+    for mu in range(4):
+        U[..., mu, :, :] = np.diag(np.exp(1j * th[mu]))
+    W = O.build_w(O.phase_links(U, (1, 1, 1, 1)))
+    for d in range(81):
+        s = _offset(d)
+        want = np.diag(np.exp(1j * (s @ th)))
+        assert np.abs(W[..., d, :, :] - want).max() < 1e-13
+
+
+def test_w_gauge_covariance():
+    dims = (2, 4, 2, 4)
+    U = I.gauge_field(dims, 3, 0.5, seed=41)
+    Om = I.gauge_transform(dims, 3, seed=42)
+    W = O.build_w(U)
+    Wg = O.build_w(_transform_links(U, Om))
+    for d in (0, 13, 22, 39, 44, 62, 80):
+        s = _offset(d)
+        Om_s = np.roll(Om, shift=(-s[3], -s[2], -s[1], -s[0]), axis=(0, 1, 2, 3))
+        want = Om @ W[..., d, :, :] @ np.conj(np.swapaxes(Om_s, -1, -2))
+        assert np.abs(Wg[..., d, :, :] - want).max() < 1e-13
+
+
+# ------------------------------------------------------- dense brute force
+
+def dense(apply, shape):
+    n = int(np.prod(shape))
+    cols = []
+    for j in range(n):
+        e = np.zeros(n, complex)
+        e[j] = 1
+        cols.append(apply(e.reshape(shape)).ravel())
+    return np.array(cols).T
+
+
+@pytest.mark.parametrize("kind", [O.WILSON, O.BRILLOUIN, O.STAGGERED])
+def test_dense_2x4_dagger_is_conjugate_transpose(kind):
+    """2^4 lattice: every offset aliases onto another site; the matrix of the
+    dagger must still be the conjugate transpose of the matrix of D."""
+    dims = (2, 2, 2, 2)
+    U = I.gauge_field(dims, 3, 0.4, seed=51)
+    op = O.Operator(kind, U, (1, 1, 1, -1), 0.1)
+    shape = (2, 2, 2, 2, 3, 1) if kind == O.STAGGERED else (2, 2, 2, 2, 3, 4, 1)
+    D = dense(op.apply, shape)
+    Dd = dense(op.apply_dagger, shape)
+    assert np.abs(Dd - D.conj().T).max() < 1e-13
+
+
+# ---------------------------------------------------------------- solvers
+
+@pytest.mark.parametrize("kind", [O.WILSON, O.BRILLOUIN, O.STAGGERED])
+def test_cg_normal_matches_dense_solve(kind):
+    dims = (2, 2, 2, 4)
+    U = I.gauge_field(dims, 3, 0.4, seed=61)
+    op = O.Operator(kind, U, (1, 1, 1, -1), 0.1)
+    stag = kind == O.STAGGERED
+    b = I.source(dims, 3, 3, seed=62, staggered=stag)
+    x, info = O.cg_normal(op, b, tol=1e-12, maxit=2000)
+    assert info["status"] == O.CONVERGED
+    shape1 = b.shape[:-1] + (1,)
+    D = dense(op.apply, shape1)
+    for v in range(3):
+        xv = np.linalg.solve(D, b[..., v].ravel())
+        assert np.abs(x[..., v].ravel() - xv).max() < 1e-9 * np.abs(xv).max()
+    assert np.all(info["true_relres"] < 1e-10)
+
+
+@pytest.mark.parametrize("kind", [O.WILSON, O.BRILLOUIN])
+def test_bicgstab_matches_dense_solve(kind):
+    dims = (2, 2, 4, 2)
+    U = I.gauge_field(dims, 3, 0.4, seed=71)
+    op = O.Operator(kind, U, (1, 1, 1, -1), 0.2)
+    b = I.source(dims, 3, 2, seed=72)
+    x, info = O.bicgstab(op, b, tol=1e-12, maxit=2000)
+    assert info["status"] == O.CONVERGED
+    D = dense(op.apply, b.shape[:-1] + (1,))
+    for v in range(2):
+        xv = np.linalg.solve(D, b[..., v].ravel())
+        assert np.abs(x[..., v].ravel() - xv).max() < 1e-9 * np.abs(xv).max()
+
+
+def test_lanczos_condition_estimate_matches_dense_spectrum():
+    dims = (4, 2, 2, 4)
+    U = I.gauge_field(dims, 3, 0.4, seed=81)
+    op = O.Operator(O.STAGGERED, U, (1, 1, 1, -1), 0.05)
+    b = I.source(dims, 3, 2, seed=82, staggered=True)
+    bN = op.apply_dagger(b)
+    x, info = O.cg(op.apply_normal, bN, tol=1e-13, maxit=5000, recompute_every=10 ** 6)
+    est = O.lanczos_cond(info["alphas"], info["betas"])
+    A = dense(op.apply_normal, b.shape[:-1] + (1,))
+    ev = np.linalg.eigvalsh(0.5 * (A + A.conj().T))
+    for lo, hi in est:
+        assert abs(hi - ev[-1]) < 1e-6 * ev[-1]
+        assert abs(lo - ev[0]) < 1e-3 * ev[0]
+
+
+def test_cg_stagnation_rule_reports_discrepancy():
+    """A CG fed an operator with a deliberate rounding (float32 products) must
+    stop on the 1% updated-vs-recomputed rule rather than run to maxit (Sec. 9)."""
+    dims = (2, 2, 2, 4)
+    U = I.gauge_field(dims, 3, 0.4, seed=91)
+    op = O.Operator(O.WILSON, U, (1, 1, 1, -1), 0.01)
+
+    def A32(v):
+        r = op.apply_normal(v.astype(np.complex64).astype(np.complex128))
+        return r.astype(np.complex64).astype(np.complex128)
+
+    b = I.source(dims, 3, 2, seed=92)
+    x, info = O.cg(A32, b, tol=1e-12, maxit=5000, recompute_every=20)
+    assert info["status"] == O.STAGNATED
+    assert info["iters"] < 5000
+
+
+# ------------------------------------------------------------ App. E counts
+
+def test_flop_counts_app_e():
+    assert O.flops_per_site(O.WILSON, 3) == 1368
+    assert O.flops_per_site(O.BRILLOUIN, 3) == 30168
+    assert O.flops_per_site(O.STAGGERED, 3) == 582
