@@ -1,0 +1,381 @@
+#!/usr/bin/env python3
+"""Benchmark of the multi-RHS Dirac operators (Wilson, Brillouin, staggered).
+
+Workload (one "step"): apply D_W, D_B and D_S once each to N_v = 12
+right-hand sides on a 16^3 x 32 lattice, N_c = 3, complex FP32, random SU(3)
+links exp(i 0.4 sum_k a_k lambda_k), Gaussian sources.  The metric is
+Gflop/s counted with the paper's per-site flop numbers (App. E: 1368, 30168,
+582 per site and RHS), whole job, inputs resident in HBM.
+
+Also reported: per-operator Gflop/s, algorithmic GB/s and roofline
+fractions, an N_v sweep, the end-to-end rate through the C ABI from pinned
+host memory (copies inside the timed region), the FP64 CPU oracle on a
+bounded sample of the same workload, and SM clocks sampled during the timed
+region.  ``--solve`` adds the mixed-precision vs FP32-inner defect-correction
+time to 1e-10.  ``--impl reference`` times the oracle alone.
+
+Multi-GPU (torchrun): the operators do not shard here; every rank runs an
+independent replica and the aggregate is the sum over ranks / max time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+try:
+    _CORES = len(os.sched_getaffinity(0))
+except AttributeError:
+    _CORES = os.cpu_count() or 1
+os.environ.setdefault("OMP_NUM_THREADS", str(_CORES))
+
+METRIC = "Gflop/s & HBM GB/s of D on Nv=12 RHS, FP32; mixed vs FP32 CG time to 1e-10"
+DIMS = (16, 16, 16, 32)
+NC = 3
+NV = 12
+BC = (1, 1, 1, -1)
+EPS = 0.4
+MASS = {0: 0.1, 1: 0.1, 2: 0.05}
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=1000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-sweep", action="store_true")
+    p.add_argument("--solve", action="store_true", help="add the config-3 mixed-precision solver comparison")
+    p.add_argument("--ncu", action="store_true", help="short run for profiler launch lists (no extras)")
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return dict(hbm=float(d["hbm_gbs"]), sm_max=float(d.get("sm_max_mhz", 2070.0)), source="measured")
+    except Exception:
+        return dict(hbm=6800.0, sm_max=2070.0, source="fallback")
+
+
+def alg_bytes_per_site(kind, nc, nv, eb=4):
+    """Compulsory bytes per site and apply: spinor in + out once, links once
+    (Brillouin: the 80 stored W links of this implementation)."""
+    spin = 1 if kind == 2 else 4
+    vec = nc * spin * nv * 2 * eb
+    links = (80 if kind == 1 else 4) * nc * nc * 2 * eb
+    return 2 * vec + links
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ------------------------------------------------------------------ oracle leg
+def oracle_rate(target_s, U_np, sources):
+    """FP64 CPU oracle on a bounded sample of output sites of each operator.
+    Returns (Gflop/s over the three operators, description of the sample)."""
+    import numpy as np
+
+    import oracle as O
+
+    V = int(np.prod(DIMS))
+    rng = np.random.default_rng(7)
+    total_flop, total_t, desc = 0.0, 0.0, []
+    for kind in (0, 1, 2):
+        ref = O.Operator(kind, U_np, BC)
+        src = sources[kind]
+        fps = O.flops_per_site(kind, NC) * NV
+
+        def run(ns):
+            sites = rng.choice(V, ns, replace=False)
+            field = O.build_w_sites(ref.Up, sites) if kind == 1 else ref.Up
+            t0 = time.perf_counter()
+            O.stencil_sites(kind, field, MASS[kind], src, sites)
+            return time.perf_counter() - t0
+
+        probe = 32 if kind == 1 else 512
+        dt = run(probe)
+        ns = int(min(V, max(probe, probe * target_s / max(dt, 1e-6))))
+        dt = run(ns)
+        total_flop += fps * ns
+        total_t += dt
+        desc.append("%s %d sites" % (O.KIND_NAMES[kind], ns))
+    return total_flop / total_t / 1e9, "; ".join(desc) + " of 16^3x32, Nv=12 (FP64 oracle, sampled sites)"
+
+
+def config_dict():
+    return {"workload": "D_W + D_B + D_S apply, 16^3x32, Nc=3, Nv=12, FP32 storage+arithmetic",
+            "lattice": "16x16x16x32", "nc": NC, "nv": NV, "bc": "antiperiodic t",
+            "links": "random SU(3), eps=0.4", "l2": "working set > L2: each step streams >1 GB between reuses"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    import numpy as np  # noqa: F401
+
+    from paper_2112_14640_gb300 import inputs as I
+    U = I.gauge_field(DIMS, NC, EPS, 1234)
+    sources = {k: I.source(DIMS, NC, NV, 4321 + k, staggered=(k == 2)) for k in (0, 1, 2)}
+    per_step = max(0.05, min(5.0, 120.0 / max(1, args.steps + args.warmup)))
+    for _ in range(min(args.warmup, 1)):
+        oracle_rate(per_step / 3, U, sources)
+    rates, descs, t0 = [], None, time.perf_counter()
+    for _ in range(args.steps):
+        r, descs = oracle_rate(per_step / 3, U, sources)
+        rates.append(r)
+    wall = time.perf_counter() - t0
+    value = statistics.median(rates)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gflop/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * wall / max(1, args.steps),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config_dict(),
+            "cpu_baseline": {"value": value, "unit": "Gflop/s", "cores": _CORES, "kind": "oracle",
+                             "sample": descs},
+            "e2e": {"value": value, "unit": "Gflop/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------------- our leg
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+
+    world, rank, local = dist_setup(args)
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2112_14640_gb300 import dirac as D
+    from paper_2112_14640_gb300 import inputs as I
+
+    pk = peaks()
+    U_np = I.gauge_field(DIMS, NC, EPS, 1234)
+    U = torch.from_numpy(U_np).cuda()
+    kinds = (D.WILSON, D.BRILLOUIN, D.STAGGERED)
+    sources = {k: I.source(DIMS, NC, NV, 4321 + k, staggered=(k == D.STAGGERED)) for k in kinds}
+    ops, xs, ys = {}, {}, {}
+    for k in kinds:
+        ops[k] = D.DiracOp(k, U, NV, BC, D.F32)
+        xs[k] = ops[k].to_prec(torch.from_numpy(sources[k]).cuda())
+        ys[k] = ops[k].new_vector(zero=False)
+    V = int(np.prod(DIMS))
+    flop = {k: D.flops_per_site(k, NC) * V * NV for k in kinds}
+    step_flop = sum(flop.values())
+    stream = torch.cuda.current_stream()
+
+    def step(evs=None):
+        for i, k in enumerate(kinds):
+            if evs is not None:
+                evs[i].record(stream)
+            ops[k].apply(xs[k], ys[k], m0=MASS[k])
+        if evs is not None:
+            evs[len(kinds)].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    K = args.steps
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(kinds) + 1)] for _ in range(K)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for s in range(K):
+        step(evs[s])
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    ms_total = t_start.elapsed_time(t_end)
+    if world > 1:
+        t = torch.tensor([ms_total], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / K
+    value = step_flop * world / (ms_step * 1e-3) / 1e9
+
+    per_op = {}
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk["sm_max"] * 1e6 / 1e12   # TFLOP/s
+    for i, k in enumerate(kinds):
+        times = [evs[s][i].elapsed_time(evs[s][i + 1]) for s in range(K)]
+        t_ms = statistics.mean(times)
+        gbytes = alg_bytes_per_site(k, NC, NV) * V / 1e9
+        per_op[D.KIND_NAMES[k]] = {
+            "ms": t_ms, "gflops": flop[k] / (t_ms * 1e-3) / 1e9, "alg_GBps": gbytes / (t_ms * 1e-3),
+            "hbm_frac": gbytes / (t_ms * 1e-3) / pk["hbm"],
+            "alu_frac": flop[k] / (t_ms * 1e-3) / 1e12 / fp32_peak}
+    dom = max(kinds, key=lambda k: per_op[D.KIND_NAMES[k]]["ms"])
+    d = per_op[D.KIND_NAMES[dom]]
+    if dom == D.BRILLOUIN:
+        roof = {"bound": "alu", "achieved": d["gflops"] / 1e3, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": d["gflops"] / 1e3 / fp32_peak, "traffic": None, "kernel": "brillouin_kernel",
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz" % pk["sm_max"]}
+    else:
+        roof = {"bound": "hbm", "achieved": d["alg_GBps"], "peak": pk["hbm"], "unit": "GB/s",
+                "frac": d["hbm_frac"], "traffic": None, "kernel": D.KIND_NAMES[dom] + "_kernel",
+                "peak_source": pk["source"]}
+    rooflines = {
+        "wilson": {"bound": "hbm", "achieved": per_op["wilson"]["alg_GBps"], "peak": pk["hbm"], "unit": "GB/s",
+                   "frac": per_op["wilson"]["hbm_frac"]},
+        "staggered": {"bound": "hbm", "achieved": per_op["staggered"]["alg_GBps"], "peak": pk["hbm"],
+                      "unit": "GB/s", "frac": per_op["staggered"]["hbm_frac"]},
+        "brillouin": {"bound": "alu", "achieved": per_op["brillouin"]["gflops"] / 1e3, "peak": fp32_peak,
+                      "unit": "TFLOP/s", "frac": per_op["brillouin"]["alu_frac"]},
+    }
+
+    line = {"metric": METRIC, "value": value, "unit": "Gflop/s", "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_dict(),
+            "gpu_launches": K * len(kinds), "roofline": roof, "rooflines": rooflines, "per_op": per_op,
+            "clocks": clk, "peaks_source": pk["source"]}
+
+    if not args.ncu:
+        # end to end through the C ABI from pinned host memory, copies included
+        hin = {k: xs[k].cpu().pin_memory() for k in kinds}
+        hout = {k: torch.empty_like(hin[k]).pin_memory() for k in kinds}
+        Ke = max(3, min(K, 30))
+        for k in kinds:
+            ops[k].apply_host(hin[k], hout[k], m0=MASS[k])
+        t0 = time.perf_counter()
+        for _ in range(Ke):
+            for k in kinds:
+                ops[k].apply_host(hin[k], hout[k], m0=MASS[k])
+        dt = (time.perf_counter() - t0) / Ke
+        nbytes = sum(ops[k].vec_bytes() for k in kinds)
+        line["e2e"] = {"value": step_flop / dt / 1e9, "unit": "Gflop/s", "h2d_bytes_per_step": nbytes,
+                       "d2h_bytes_per_step": nbytes, "ms_per_step": dt * 1e3}
+
+    if not args.ncu and not args.no_sweep:
+        sweep = {}
+        for nv in (1, 4, 12, 24):
+            row = {}
+            for k in kinds:
+                op = D.DiracOp(k, U, nv, BC, D.F32)
+                x = op.new_vector()
+                x.real.normal_()
+                y = op.new_vector(zero=False)
+                for _ in range(3):
+                    op.apply(x, y, m0=MASS[k])
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                reps = 20
+                e0.record(stream)
+                for _ in range(reps):
+                    op.apply(x, y, m0=MASS[k])
+                e1.record(stream)
+                torch.cuda.synchronize()
+                t = e0.elapsed_time(e1) / reps * 1e-3
+                row[D.KIND_NAMES[k]] = {"gflops": D.flops_per_site(k, NC) * V * nv / t / 1e9,
+                                        "alg_GBps": alg_bytes_per_site(k, NC, nv) * V / t / 1e9}
+                op.close()
+            sweep["nv=%d" % nv] = row
+        line["nv_sweep"] = sweep
+
+    if args.solve:
+        line["solve"] = solver_comparison(D, I, torch)
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.ncu:
+        rate, sample = oracle_rate(6.0, U_np, sources)
+        line["cpu_baseline"] = {"value": rate, "unit": "Gflop/s", "cores": _CORES, "kind": "oracle",
+                                "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def solver_comparison(D, I, torch):
+    """Time to 1e-10 of defect-correction CG on D^dag D (32^3x64, Nv=12):
+    FP64 outer with FP32 inner vs BF16/FP16 inner."""
+    dims = (32, 32, 32, 64)
+    out = {}
+    U = torch.from_numpy(I.gauge_field(dims, NC, 0.6, 99)).cuda()
+    for kind, m0 in ((D.WILSON, -0.5), (D.STAGGERED, 0.01)):
+        op = D.DiracOp(kind, U, NV, BC, D.F64)
+        b = op.to_prec(torch.from_numpy(I.source(dims, NC, NV, 5, staggered=(kind == D.STAGGERED))).cuda())
+        row = {}
+        for inner in (D.F32, D.BF16, D.F16):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            x, st = op.solve(b, m0=m0, tol=1e-10, maxit=200000, inner_prec=inner)
+            torch.cuda.synchronize()
+            row[D.PREC_NAMES[inner]] = {"seconds": time.perf_counter() - t0, "iters": st["iters"],
+                                        "outer": st["outer_iters"], "status": st["status"],
+                                        "max_true_relres": max(st["true_relres"]), "max_relres": max(st["relres"])}
+        out[D.KIND_NAMES[kind]] = row
+        op.close()
+    return out
+
+
+if __name__ == "__main__":
+    main()

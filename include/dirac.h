@@ -1,0 +1,183 @@
+/*
+ * dirac.h -- C ABI of the GB300 multi-RHS lattice Dirac operator library.
+ *
+ * Operators and solvers of Duerr, "Fast and flexible implementations of
+ * Wilson, Brillouin and Susskind fermions in lattice QCD", arXiv:2112.14640:
+ *   Wilson     D_W  Eq. (app_wils),   9-point stencil, spin projection (App. A)
+ *   Brillouin  D_B  Eq. (app_bril),  81-point stencil on path-averaged links
+ *                                     W_s(n) (Tab. off-axis)
+ *   staggered  D_S  Eq. (def_stag),   9-point stencil with eta phases
+ * each applied to N_v right-hand sides at once (Sec. 1: b and u are n x N_v
+ * matrices), plus CG on D^dag D, BiCGstab on D (Sec. 9) and a mixed-precision
+ * defect-correction driver around them (Sec. 9, last paragraph).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Lattice: dims = {Nx, Ny, Nz, Nt}; site n = ((t*Nz + z)*Ny + y)*Nx + x.
+ * Direction mu = 0..3 is x, y, z, t (the paper's mu = 1..4).
+ * Complex numbers are stored interleaved (re, im) in the element type of the
+ * precision: F64 double, F32 float, BF16 __nv_bfloat16, F16 __half.
+ * Layouts (C order, RHS index v innermost -- the paper's NvNsNc / NvNc, Sec. 2):
+ *   gauge links       U  [site][mu][a][b]         (U_mu(n)_{ab}, transporter n+mu -> n)
+ *   Wilson-type vector   [site][colour][spin][v]   spin in the chiral basis of App. A
+ *   staggered vector     [site][colour][v]
+ * All pointers are DEVICE pointers unless a name says host; the caller owns
+ * every buffer it passes and the library never frees them.  Vector buffers
+ * must be 16-byte aligned.  Work is enqueued on the CUDA stream given as
+ * `stream` (a cudaStream_t; NULL = legacy default stream) and is asynchronous
+ * unless stated otherwise.
+ *
+ * Return codes: 0 = success; negative = error (nothing was launched);
+ * positive = solver outcome (the solution buffer holds the last iterate).
+ */
+#ifndef DIRAC_H
+#define DIRAC_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { DIRAC_WILSON = 0, DIRAC_BRILLOUIN = 1, DIRAC_STAGGERED = 2 } dirac_kind;
+typedef enum { DIRAC_F64 = 0, DIRAC_F32 = 1, DIRAC_BF16 = 2, DIRAC_F16 = 3 } dirac_prec;
+
+enum {
+    DIRAC_OK = 0,
+    DIRAC_ERR_INVALID_ARG = -1,     /* null pointer, bad enum, bad geometry */
+    DIRAC_ERR_UNSUPPORTED_NC = -2,  /* N_c outside the compiled set {1,2,3,4} */
+    DIRAC_ERR_UNSUPPORTED_PREC = -3,
+    DIRAC_ERR_ALIGNMENT = -4,       /* a vector pointer not 16-byte aligned */
+    DIRAC_ERR_OOM = -5,             /* a library-owned allocation failed */
+    DIRAC_ERR_CUDA = -6,            /* a CUDA call or launch failed; see stderr */
+    DIRAC_ERR_DEVICE_TIMEOUT = -7,  /* a bounded device-side wait ran out */
+    DIRAC_NOT_CONVERGED = 1,        /* maxit reached */
+    DIRAC_STAGNATED = 2,            /* updated and recomputed residual differ > 1% (Sec. 9) */
+    DIRAC_BREAKDOWN = 3,            /* BiCGstab rho or omega vanished */
+    DIRAC_NONFINITE = 4             /* NaN/Inf appeared in a residual */
+};
+
+/* Lattice geometry and storage precision of an operator.
+ * dims   : extents, each >= 2; staggered operators need all four even
+ *          (the eta phases of Eq. def_stag are periodic only then).
+ * nc     : number of colours N_c (1..4 compiled; 3 is the physical case).
+ * nv     : number of right-hand sides N_v, 1..64.
+ * bc     : +1 periodic / -1 antiperiodic per direction.  The phase multiplies
+ *          U_mu(n) on the links with n_mu = N_mu - 1 before anything else
+ *          (including the W links) is built from U.
+ * prec   : storage precision of links, W links and the vectors passed to
+ *          dirac_apply*; arithmetic is FP64 for F64 and FP32 otherwise. */
+typedef struct {
+    int dims[4];
+    int nc;
+    int nv;
+    int bc[4];
+    dirac_prec prec;
+} dirac_geom;
+
+typedef struct dirac_op dirac_op;   /* opaque */
+
+/* Create an operator on gauge field U (device pointer, layout above, in
+ * precision u_prec = DIRAC_F64 or DIRAC_F32, no boundary phases applied).
+ * The operator keeps its own copy of the phased links in geom->prec; for
+ * DIRAC_BRILLOUIN it also builds and keeps the 80 off-centre W_s(n) of
+ * Tab. off-axis (computed in FP64 from U, stored in geom->prec).
+ * Synchronises `stream` before returning.  U may be freed afterwards. */
+int dirac_op_create(dirac_kind kind, const dirac_geom *geom, const void *U,
+                    dirac_prec u_prec, void *stream, dirac_op **out);
+
+/* Replace the gauge field (same geometry); rebuilds W for Brillouin.
+ * Synchronises `stream` before returning. */
+int dirac_op_update_links(dirac_op *op, const void *U, dirac_prec u_prec, void *stream);
+
+/* Copy the operator's stored W links (Brillouin only) into w_out, layout
+ * [site][80][a][b] in geom->prec, directions s = (sx,sy,sz,st) in {-1,0,1}^4
+ * numbered d = (st+1)*27+(sz+1)*9+(sy+1)*3+(sx+1) with the centre d = 40
+ * left out (index d for d < 40, d-1 for d > 40). */
+int dirac_op_copy_w(const dirac_op *op, void *w_out, void *stream);
+
+void dirac_op_destroy(dirac_op *op);
+
+/* psi_out = D psi_in with bare mass m0 (Wilson Eq. app_wils, Brillouin
+ * Eq. app_bril, staggered Eq. def_stag).  psi_in and psi_out are vectors of
+ * the operator's kind and precision and must not overlap. */
+int dirac_apply(const dirac_op *op, const void *psi_in, void *psi_out, double m0, void *stream);
+
+/* psi_out = D^dag psi_in: gamma5 D gamma5 for Wilson and Brillouin,
+ * epsilon D epsilon for staggered (App. F, the forms the solvers use). */
+int dirac_apply_dagger(const dirac_op *op, const void *psi_in, void *psi_out, double m0, void *stream);
+
+/* psi_out = D^dag D psi_in (App. F, app_*dag*), through an operator-owned
+ * scratch vector: calls on one operator must not run concurrently. */
+int dirac_apply_normal(const dirac_op *op, const void *psi_in, void *psi_out, double m0, void *stream);
+
+/* End-to-end apply from HOST memory: copies host_in to an operator-owned
+ * device buffer, applies D (dagger != 0: D^dag), copies the result to
+ * host_out and synchronises `stream`.  Host buffers of vec_bytes each;
+ * pinned memory gives full copy bandwidth. */
+int dirac_apply_host(const dirac_op *op, const void *host_in, void *host_out, double m0,
+                     int dagger, void *stream);
+
+/* Bytes of one vector of this operator (sites x internal dofs x N_v x complex). */
+size_t dirac_vec_bytes(const dirac_op *op);
+
+/* ---------------------------------------------------------- BLAS-1 (Sec. 3)
+ * Per-RHS vector operations on vectors of the operator's shape and precision.
+ * Reductions accumulate in FP64 (Sec. 3 accumulates sp norms in dp) with a
+ * fixed-order two-pass reduction, so results are bitwise reproducible.
+ * out/coefficient arrays are DEVICE arrays of N_v entries. */
+int dirac_vec_norm2(const dirac_op *op, const void *v, double *out_dev, void *stream);
+/* <u, v> per RHS, linear in the second argument; out_dev holds N_v (re, im) pairs. */
+int dirac_vec_dot(const dirac_op *op, const void *u, const void *v, double *out_dev, void *stream);
+/* y += alpha x per RHS (Eq. def_incr with complex alpha); alpha_dev: N_v (re, im) pairs. */
+int dirac_vec_axpy(const dirac_op *op, const double *alpha_dev, const void *x, void *y, void *stream);
+/* v = gamma5 v (Wilson-type) or epsilon v (staggered), in place. */
+int dirac_vec_gamma5(const dirac_op *op, void *v, void *stream);
+/* Convert a vector between precisions (same shape): src in src_prec, dst in dst_prec. */
+int dirac_vec_convert(const dirac_op *op, const void *src, dirac_prec src_prec, void *dst,
+                      dirac_prec dst_prec, void *stream);
+
+/* ------------------------------------------------------------- solvers (Sec. 9) */
+typedef enum { DIRAC_CG_NORMAL = 0, DIRAC_BICGSTAB = 1 } dirac_solver;
+
+typedef struct {
+    dirac_solver solver;   /* CG on D^dag D x = D^dag b, or BiCGstab on D x = b */
+    double tol;            /* relative residual: ||r_N||/||D^dag b|| (CG) or ||b-Dx||/||b|| */
+    int maxit;             /* total iteration limit (inner iterations for mixed solves) */
+    dirac_prec inner_prec; /* == op precision: plain Krylov solve in that precision;
+                              lower precision: defect correction (Sec. 9 "mp" solvers)
+                              with the outer residual, norms and update in the
+                              operator's precision and inner solves in inner_prec */
+    double inner_tol;      /* relative tolerance of each inner solve (0 = default) */
+    int recompute_every;   /* 0 = paper default: 50 for F64 solves, 20 otherwise */
+} dirac_solve_params;
+
+typedef struct {
+    int iters;                 /* Krylov iterations (summed over inner solves) */
+    int outer_iters;           /* defect-correction steps (0 for a plain solve) */
+    int recomputes;            /* explicit residual recomputations */
+    int status;                /* overall outcome: 0 or a positive code above */
+    int status_per_rhs[64];
+    double relres[64];         /* final recomputed residual, per RHS */
+    double true_relres[64];    /* ||b - D x|| / ||b|| per RHS */
+    double seconds;            /* wall time of the call */
+} dirac_solve_stats;
+
+/* Solve for N_v right-hand sides b (operator precision); x holds the initial
+ * guess on entry and the solution on exit.  Blocks until done (it reads
+ * per-iteration residual norms on the host).  stats may be NULL. */
+int dirac_solve(const dirac_op *op, const void *b, void *x, double m0,
+                const dirac_solve_params *params, dirac_solve_stats *stats, void *stream);
+
+/* ------------------------------------------------------------- utilities */
+const char *dirac_error_string(int code);
+/* Flops per site per RHS (App. E): Wilson 128Nc^2+72Nc, Brillouin
+ * 2560Nc^2+2376Nc, staggered 64Nc^2+2Nc; -1 for an invalid kind. */
+long dirac_flops_per_site(dirac_kind kind, int nc);
+/* Compile-time library version (major*10000 + minor*100 + patch). */
+int dirac_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DIRAC_H */

@@ -138,15 +138,12 @@ static void signed_link(const int d[4], int nc, const cplx *U, long n, int mu, i
  *                  + (4 + m0) psi(n)
  * U must already carry the boundary phases (orc_phase_links). */
 
-void orc_wilson(const int d[4], int nc, int nv, const cplx *U, double m0,
-                const cplx *in, cplx *out) {
-    const long V = vol4(d);
+static void wilson_site(const int d[4], int nc, int nv, const cplx *U, double m0,
+                        const cplx *in, long n, cplx *o) {
     const long per_site = (long)nc * 4 * nv;
     cplx g[4][4][4];
     for (int mu = 0; mu < 4; ++mu) gamma_matrix(mu, g[mu]);
-#pragma omp parallel for
-    for (long n = 0; n < V; ++n) {
-        cplx *o = out + n * per_site;
+    {
         const cplx *c0 = in + n * per_site;
         for (long e = 0; e < per_site; ++e) o[e] = (4.0 + m0) * c0[e];
         cplx L[64];
@@ -175,6 +172,20 @@ void orc_wilson(const int d[4], int nc, int nv, const cplx *U, double m0,
     }
 }
 
+void orc_wilson(const int d[4], int nc, int nv, const cplx *U, double m0,
+                const cplx *in, cplx *out) {
+    const long V = vol4(d);
+#pragma omp parallel for
+    for (long n = 0; n < V; ++n) wilson_site(d, nc, nv, U, m0, in, n, out + n * (long)nc * 4 * nv);
+}
+
+/* output only at the listed sites: out[i] = (D psi)(sites[i]) */
+void orc_wilson_sites(const int d[4], int nc, int nv, const cplx *U, double m0,
+                      const cplx *in, const long *sites, long ns, cplx *out) {
+#pragma omp parallel for
+    for (long i = 0; i < ns; ++i) wilson_site(d, nc, nv, U, m0, in, sites[i], out + i * (long)nc * 4 * nv);
+}
+
 /* ------------------------------------------------ staggered Dirac operator
  * Eq. (def_stag):
  *   (D_S phi)(n) = sum_mu eta_mu(n) 1/2 [U_mu(n) phi(n+mu) - U_mu(n-mu)^dag phi(n-mu)] + m0 phi(n)
@@ -188,15 +199,12 @@ static double eta(const int x[4], int mu) {
     return (e & 1) ? -1.0 : 1.0;
 }
 
-void orc_staggered(const int d[4], int nc, int nv, const cplx *U, double m0,
-                   const cplx *in, cplx *out) {
-    const long V = vol4(d);
+static void staggered_site(const int d[4], int nc, int nv, const cplx *U, double m0,
+                           const cplx *in, long n, cplx *o) {
     const long per_site = (long)nc * nv;
-#pragma omp parallel for
-    for (long n = 0; n < V; ++n) {
+    {
         int x[4];
         coords(d, n, x);
-        cplx *o = out + n * per_site;
         const cplx *c0 = in + n * per_site;
         for (long e = 0; e < per_site; ++e) o[e] = m0 * c0[e];
         cplx L[64];
@@ -214,6 +222,19 @@ void orc_staggered(const int d[4], int nc, int nv, const cplx *U, double m0,
                     }
             }
     }
+}
+
+void orc_staggered(const int d[4], int nc, int nv, const cplx *U, double m0,
+                   const cplx *in, cplx *out) {
+    const long V = vol4(d);
+#pragma omp parallel for
+    for (long n = 0; n < V; ++n) staggered_site(d, nc, nv, U, m0, in, n, out + n * (long)nc * nv);
+}
+
+void orc_staggered_sites(const int d[4], int nc, int nv, const cplx *U, double m0,
+                         const cplx *in, const long *sites, long ns, cplx *out) {
+#pragma omp parallel for
+    for (long i = 0; i < ns; ++i) staggered_site(d, nc, nv, U, m0, in, sites[i], out + i * (long)nc * nv);
 }
 
 /* -------------------------------------------------- W links (Tab. off-axis)
@@ -240,14 +261,13 @@ void orc_dir_offset(int dir, int s[4]) {
     s[3] = (dir / 27) % 3 - 1;
 }
 
-void orc_build_w(const int d[4], int nc, const cplx *U, cplx *W) {
-    const long V = vol4(d);
+/* the 81 W_s(n) of one site into Wn[81][nc][nc] */
+static void build_w_site(const int d[4], int nc, const cplx *U, long n, cplx *Wn) {
     const long per = (long)nc * nc;
-#pragma omp parallel for
-    for (long n = 0; n < V; ++n) {
+    {
         cplx P[64], T[64], L[64];
         for (int dir = 0; dir < 81; ++dir) {
-            cplx *w = W + (n * 81 + dir) * per;
+            cplx *w = Wn + dir * per;
             int s[4];
             orc_dir_offset(dir, s);
             int axes[4], k = 0;
@@ -280,6 +300,17 @@ void orc_build_w(const int d[4], int nc, const cplx *U, cplx *W) {
     }
 }
 
+void orc_build_w(const int d[4], int nc, const cplx *U, cplx *W) {
+    const long V = vol4(d);
+#pragma omp parallel for
+    for (long n = 0; n < V; ++n) build_w_site(d, nc, U, n, W + n * 81 * (long)nc * nc);
+}
+
+void orc_build_w_sites(const int d[4], int nc, const cplx *U, const long *sites, long ns, cplx *W) {
+#pragma omp parallel for
+    for (long i = 0; i < ns; ++i) build_w_site(d, nc, U, sites[i], W + i * 81 * (long)nc * nc);
+}
+
 /* ------------------------------------------------ Brillouin Dirac operator
  * Eq. (app_bril) with Eqs. (def_ider, def_blap), r = 1, c_SW = 0:
  *   (D_B psi)(n) = (m0 - lambda_0/2) psi(n)
@@ -291,16 +322,14 @@ void orc_build_w(const int d[4], int nc, const cplx *U, cplx *W) {
 static const double RHO[5] = {0.0, 64.0 / 432.0, 16.0 / 432.0, 4.0 / 432.0, 1.0 / 432.0};
 static const double LAM[5] = {-240.0 / 64.0, 8.0 / 64.0, 4.0 / 64.0, 2.0 / 64.0, 1.0 / 64.0};
 
-void orc_brillouin(const int d[4], int nc, int nv, const cplx *W, double m0,
-                   const cplx *in, cplx *out) {
-    const long V = vol4(d);
+/* one output site n; Wn = the 81 W_s(n) of that site */
+static void brillouin_site(const int d[4], int nc, int nv, const cplx *Wn, double m0,
+                           const cplx *in, long n, cplx *o) {
     const long per_site = (long)nc * 4 * nv;
     const long per = (long)nc * nc;
     cplx g[4][4][4];
     for (int mu = 0; mu < 4; ++mu) gamma_matrix(mu, g[mu]);
-#pragma omp parallel for
-    for (long n = 0; n < V; ++n) {
-        cplx *o = out + n * per_site;
+    {
         for (long e = 0; e < per_site; ++e) o[e] = 0;
         for (int dir = 0; dir < 81; ++dir) {
             int s[4];
@@ -315,7 +344,7 @@ void orc_brillouin(const int d[4], int nc, int nv, const cplx *W, double m0,
                     S[a][b] = v;
                 }
             long m = shifted(d, n, s);
-            const cplx *w = W + (n * 81 + dir) * per;
+            const cplx *w = Wn + dir * per;
             const cplx *pm = in + m * per_site;
             for (int c = 0; c < nc; ++c)
                 for (int sp = 0; sp < 4; ++sp)
@@ -328,6 +357,23 @@ void orc_brillouin(const int d[4], int nc, int nv, const cplx *W, double m0,
                     }
         }
     }
+}
+
+void orc_brillouin(const int d[4], int nc, int nv, const cplx *W, double m0,
+                   const cplx *in, cplx *out) {
+    const long V = vol4(d);
+    const long per_site = (long)nc * 4 * nv;
+#pragma omp parallel for
+    for (long n = 0; n < V; ++n) brillouin_site(d, nc, nv, W + n * 81 * (long)nc * nc, m0, in, n, out + n * per_site);
+}
+
+/* sampled sites: Wsites[i] holds the 81 W of sites[i] (orc_build_w_sites) */
+void orc_brillouin_sites(const int d[4], int nc, int nv, const cplx *Wsites, double m0,
+                         const cplx *in, const long *sites, long ns, cplx *out) {
+    const long per_site = (long)nc * 4 * nv;
+#pragma omp parallel for
+    for (long i = 0; i < ns; ++i)
+        brillouin_site(d, nc, nv, Wsites + i * 81 * (long)nc * nc, m0, in, sites[i], out + i * per_site);
 }
 
 /* ------------------------------------------ gamma_5 and epsilon (Sec. 3)

@@ -49,8 +49,14 @@ def lib():
         _lib.orc_gamma5.argtypes = [I4, I, I, P, P]
         _lib.orc_epsilon.argtypes = [I4, I, I, P, P]
         _lib.orc_gamma.argtypes = [I, P]
+        _lib.orc_wilson_sites.argtypes = [I4, I, I, P, D, P, P, ctypes.c_long, P]
+        _lib.orc_staggered_sites.argtypes = [I4, I, I, P, D, P, P, ctypes.c_long, P]
+        _lib.orc_brillouin_sites.argtypes = [I4, I, I, P, D, P, P, ctypes.c_long, P]
+        _lib.orc_build_w_sites.argtypes = [I4, I, P, P, ctypes.c_long, P]
         for f in (_lib.orc_phase_links, _lib.orc_wilson, _lib.orc_staggered, _lib.orc_brillouin,
-                  _lib.orc_build_w, _lib.orc_gamma5, _lib.orc_epsilon, _lib.orc_gamma):
+                  _lib.orc_build_w, _lib.orc_gamma5, _lib.orc_epsilon, _lib.orc_gamma,
+                  _lib.orc_wilson_sites, _lib.orc_staggered_sites, _lib.orc_brillouin_sites,
+                  _lib.orc_build_w_sites):
             f.restype = None
     return _lib
 
@@ -122,6 +128,35 @@ def brillouin(W, m0, psi):
     return _stencil(lib().orc_brillouin, (nx, ny, nz, nt), nc, psi.shape[-1], W, m0, psi)
 
 
+def _sites_arr(sites):
+    a = np.ascontiguousarray(np.asarray(sites, dtype=np.int64))
+    return a, ctypes.c_void_p(a.ctypes.data), len(a)
+
+
+def build_w_sites(Up, sites):
+    """The 81 W_s(n) at the listed sites only: shape (len(sites), 81, Nc, Nc)."""
+    dims, nc = _dims_of_links(Up)
+    Up = np.ascontiguousarray(Up, np.complex128)
+    a, pa, ns = _sites_arr(sites)
+    W = np.empty((ns, 81, nc, nc), np.complex128)
+    lib().orc_build_w_sites(_i4(dims), nc, _p(Up), pa, ns, _p(W))
+    return W
+
+
+def stencil_sites(kind, field, m0, v, sites):
+    """(D v)(n) for n in sites; field = phased links (Wilson, staggered) or
+    build_w_sites(...) of the same sites (Brillouin).  Returns (len(sites),) + v.shape[4:]."""
+    nt, nz, ny, nx = v.shape[:4]
+    nc, nv = v.shape[4], v.shape[-1]
+    v = np.ascontiguousarray(v, np.complex128)
+    a, pa, ns = _sites_arr(sites)
+    out = np.empty((ns,) + v.shape[4:], np.complex128)
+    fn = {WILSON: lib().orc_wilson_sites, STAGGERED: lib().orc_staggered_sites,
+          BRILLOUIN: lib().orc_brillouin_sites}[kind]
+    fn(_i4((nx, ny, nz, nt)), nc, nv, _p(np.ascontiguousarray(field)), float(m0), _p(v), pa, ns, _p(out))
+    return out
+
+
 def gamma5(psi):
     nt, nz, ny, nx, nc, _, nv = psi.shape
     psi = np.ascontiguousarray(psi, np.complex128)
@@ -152,7 +187,14 @@ class Operator:
         self.m0 = float(m0)
         self.bc = tuple(int(b) for b in bc)
         self.Up = phase_links(U, self.bc)
-        self.W = build_w(self.Up) if kind == BRILLOUIN else None
+        self._W = None
+
+    @property
+    def W(self):
+        """All 81 W links (Brillouin), built on first use."""
+        if self._W is None and self.kind == BRILLOUIN:
+            self._W = build_w(self.Up)
+        return self._W
 
     def apply(self, v, m0=None):
         m = self.m0 if m0 is None else m0
@@ -161,6 +203,26 @@ class Operator:
         if self.kind == BRILLOUIN:
             return brillouin(self.W, m, v)
         return staggered(self.Up, m, v)
+
+    def apply_sites(self, v, sites, m0=None, dagger=False):
+        """(D v)(n) or (D^dag v)(n) at the listed site indices only."""
+        m = self.m0 if m0 is None else m0
+        if self.kind == BRILLOUIN:
+            field = build_w_sites(self.Up, sites)
+        else:
+            field = self.Up
+        if not dagger:
+            return stencil_sites(self.kind, field, m, v, sites)
+        out = stencil_sites(self.kind, field, m, self._sandwich(v), sites)
+        if self.kind == STAGGERED:
+            nt, nz, ny, nx = v.shape[:4]
+            s = np.asarray(sites)
+            x, y, z, t = s % nx, (s // nx) % ny, (s // (nx * ny)) % nz, s // (nx * ny * nz)
+            eps = np.where((x + y + z + t) % 2 == 1, -1.0, 1.0)
+            return out * eps[:, None, None]
+        out = out.copy()
+        out[:, :, 2:, :] *= -1
+        return out
 
     def _sandwich(self, v):
         return epsilon(v) if self.kind == STAGGERED else gamma5(v)

@@ -1,0 +1,288 @@
+// capi.cu -- the extern "C" entry points of include/dirac.h: argument
+// validation, the operator handle (owned link/W copies, scratch and staging
+// buffers, reduction partials), dispatch by operator kind, and error strings.
+#include <stdlib.h>
+#include <string.h>
+
+#include "internal.h"
+
+using namespace dgb;
+
+namespace dgb {
+
+int op_apply(const dirac_op *op, const void *in, void *out, double m0, int sgn, cudaStream_t s) {
+    switch (op->kind) {
+    case DIRAC_WILSON: return launch_wilson(op, in, out, m0, sgn, s);
+    case DIRAC_BRILLOUIN: return launch_brillouin(op, in, out, m0, sgn, s);
+    case DIRAC_STAGGERED: return launch_staggered(op, in, out, m0, sgn, s);
+    }
+    return DIRAC_ERR_INVALID_ARG;
+}
+
+// D^dag D psi through the operator's scratch vector.
+int op_apply_normal(const dirac_op *op, const void *in, void *out, double m0, cudaStream_t s) {
+    int rc = op_apply(op, in, op->scratch, m0, +1, s);
+    if (rc) return rc;
+    return op_apply(op, op->scratch, out, m0, -1, s);
+}
+
+static void op_free(dirac_op *op) {
+    if (!op) return;
+    for (int i = 0; i < 4; ++i) op_free(op->inner[i]);
+    cudaFree(op->links);
+    cudaFree(op->w);
+    cudaFree(op->scratch);
+    cudaFree(op->stage_in);
+    cudaFree(op->stage_out);
+    cudaFree(op->red_partial);
+    cudaFree(op->solver_ws);
+    free(op);
+}
+
+static int validate_geom(dirac_kind kind, const dirac_geom *g) {
+    if (!g) return DIRAC_ERR_INVALID_ARG;
+    if (kind != DIRAC_WILSON && kind != DIRAC_BRILLOUIN && kind != DIRAC_STAGGERED) return DIRAC_ERR_INVALID_ARG;
+    for (int m = 0; m < 4; ++m) {
+        if (g->dims[m] < 2) return DIRAC_ERR_INVALID_ARG;
+        if (g->bc[m] != 1 && g->bc[m] != -1) return DIRAC_ERR_INVALID_ARG;
+        if (kind == DIRAC_STAGGERED && (g->dims[m] & 1)) return DIRAC_ERR_INVALID_ARG;
+    }
+    if ((long long)g->dims[0] * g->dims[1] * g->dims[2] * g->dims[3] > (1LL << 31)) return DIRAC_ERR_INVALID_ARG;
+    if (g->nc < 1 || g->nc > 4) return DIRAC_ERR_UNSUPPORTED_NC;
+    if (g->nv < 1 || g->nv > 64) return DIRAC_ERR_INVALID_ARG;
+    if (g->prec < DIRAC_F64 || g->prec > DIRAC_F16) return DIRAC_ERR_UNSUPPORTED_PREC;
+    return DIRAC_OK;
+}
+
+static int alloc(void **p, size_t bytes) {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return DIRAC_ERR_OOM;
+    }
+    return DIRAC_OK;
+}
+
+// Allocate an operator handle of the given geometry without links.
+int op_alloc(dirac_kind kind, const dirac_geom *g, dirac_op **out) {
+    dirac_op *op = (dirac_op *)calloc(1, sizeof(dirac_op));
+    if (!op) return DIRAC_ERR_OOM;
+    op->kind = kind;
+    op->geom = *g;
+    op->nc = g->nc;
+    op->nv = g->nv;
+    op->prec = g->prec;
+    op->V = (long long)g->dims[0] * g->dims[1] * g->dims[2] * g->dims[3];
+    op->lat = Lat{g->dims[0], g->dims[1], g->dims[2], g->dims[3], g->nv, op->V};
+    op->rows = op->V * op->nc * (kind == DIRAC_STAGGERED ? 1 : 4);
+    const size_t eb = elem_bytes(op->prec);
+    op->vec_bytes = (size_t)op->rows * op->nv * 2 * eb;
+    op->link_bytes = (size_t)op->V * 4 * op->nc * op->nc * 2 * eb;
+    op->w_bytes = kind == DIRAC_BRILLOUIN ? (size_t)op->V * 80 * op->nc * op->nc * 2 * eb : 0;
+    // one reduction block per 2 SMs' worth of work, at most 1216 blocks
+    long long want = (op->rows + 255) / 256;
+    op->red_blocks = (int)(want < 1216 ? (want < 1 ? 1 : want) : 1216);
+    int rc = alloc(&op->links, op->link_bytes);
+    if (!rc && op->w_bytes) rc = alloc(&op->w, op->w_bytes);
+    if (!rc) rc = alloc(&op->scratch, op->vec_bytes);
+    if (!rc) rc = alloc((void **)&op->red_partial, (size_t)op->red_blocks * op->nv * 2 * sizeof(double));
+    if (rc) {
+        op_free(op);
+        return rc;
+    }
+    *out = op;
+    return DIRAC_OK;
+}
+
+// Lower-precision twin of op (same links/W converted), created once.
+int op_inner(const dirac_op *op, dirac_prec p, dirac_op **out, cudaStream_t s) {
+    if (p == op->prec) {
+        *out = (dirac_op *)op;
+        return DIRAC_OK;
+    }
+    dirac_op *self = (dirac_op *)op;
+    if (!self->inner[p]) {
+        dirac_geom g = op->geom;
+        g.prec = p;
+        dirac_op *tw = nullptr;
+        int rc = op_alloc(op->kind, &g, &tw);
+        if (rc) return rc;
+        rc = launch_convert_links(op, tw, s);
+        if (rc) {
+            op_free(tw);
+            return rc;
+        }
+        self->inner[p] = tw;
+    }
+    *out = self->inner[p];
+    return DIRAC_OK;
+}
+
+void op_destroy(dirac_op *op) { op_free(op); }
+
+}  // namespace dgb
+
+static int check_vec(const void *p) {
+    if (!p) return DIRAC_ERR_INVALID_ARG;
+    if ((uintptr_t)p & 15) return DIRAC_ERR_ALIGNMENT;
+    return DIRAC_OK;
+}
+
+static int load_links(dirac_op *op, const void *U, dirac_prec u_prec, cudaStream_t s) {
+    if (!U) return DIRAC_ERR_INVALID_ARG;
+    if (u_prec != DIRAC_F64 && u_prec != DIRAC_F32) return DIRAC_ERR_UNSUPPORTED_PREC;
+    int rc = launch_phase_links(op, U, u_prec, s);
+    if (!rc && op->kind == DIRAC_BRILLOUIN) rc = launch_build_w(op, U, u_prec, s);
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(s), "link setup");
+    // twins built from older links are stale now
+    for (int i = 0; i < 4; ++i) {
+        op_destroy(op->inner[i]);
+        op->inner[i] = nullptr;
+    }
+    return rc;
+}
+
+extern "C" {
+
+int dirac_op_create(dirac_kind kind, const dirac_geom *geom, const void *U, dirac_prec u_prec, void *stream,
+                    dirac_op **out) {
+    if (!out) return DIRAC_ERR_INVALID_ARG;
+    *out = nullptr;
+    int rc = validate_geom(kind, geom);
+    if (rc) return rc;
+    if (!U) return DIRAC_ERR_INVALID_ARG;
+    if (u_prec != DIRAC_F64 && u_prec != DIRAC_F32) return DIRAC_ERR_UNSUPPORTED_PREC;
+    dirac_op *op = nullptr;
+    rc = op_alloc(kind, geom, &op);
+    if (rc) return rc;
+    rc = load_links(op, U, u_prec, (cudaStream_t)stream);
+    if (rc) {
+        op_destroy(op);
+        return rc;
+    }
+    *out = op;
+    return DIRAC_OK;
+}
+
+int dirac_op_update_links(dirac_op *op, const void *U, dirac_prec u_prec, void *stream) {
+    if (!op) return DIRAC_ERR_INVALID_ARG;
+    return load_links(op, U, u_prec, (cudaStream_t)stream);
+}
+
+int dirac_op_copy_w(const dirac_op *op, void *w_out, void *stream) {
+    if (!op || !w_out || op->kind != DIRAC_BRILLOUIN) return DIRAC_ERR_INVALID_ARG;
+    return cuda_check(cudaMemcpyAsync(w_out, op->w, op->w_bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream),
+                      "copy W");
+}
+
+void dirac_op_destroy(dirac_op *op) { op_destroy(op); }
+
+size_t dirac_vec_bytes(const dirac_op *op) { return op ? op->vec_bytes : 0; }
+
+static int apply_checked(const dirac_op *op, const void *in, void *out, double m0, int sgn, void *stream) {
+    if (!op) return DIRAC_ERR_INVALID_ARG;
+    int rc = check_vec(in);
+    if (!rc) rc = check_vec(out);
+    if (rc) return rc;
+    if (in == out) return DIRAC_ERR_INVALID_ARG;
+    return op_apply(op, in, out, m0, sgn, (cudaStream_t)stream);
+}
+
+int dirac_apply(const dirac_op *op, const void *psi_in, void *psi_out, double m0, void *stream) {
+    return apply_checked(op, psi_in, psi_out, m0, +1, stream);
+}
+
+int dirac_apply_dagger(const dirac_op *op, const void *psi_in, void *psi_out, double m0, void *stream) {
+    return apply_checked(op, psi_in, psi_out, m0, -1, stream);
+}
+
+int dirac_apply_normal(const dirac_op *op, const void *psi_in, void *psi_out, double m0, void *stream) {
+    if (!op) return DIRAC_ERR_INVALID_ARG;
+    int rc = check_vec(psi_in);
+    if (!rc) rc = check_vec(psi_out);
+    if (rc) return rc;
+    return op_apply_normal(op, psi_in, psi_out, m0, (cudaStream_t)stream);
+}
+
+int dirac_apply_host(const dirac_op *op, const void *host_in, void *host_out, double m0, int dagger, void *stream) {
+    if (!op || !host_in || !host_out) return DIRAC_ERR_INVALID_ARG;
+    dirac_op *self = (dirac_op *)op;
+    int rc = DIRAC_OK;
+    if (!self->stage_in) rc = alloc(&self->stage_in, op->vec_bytes);
+    if (!rc && !self->stage_out) rc = alloc(&self->stage_out, op->vec_bytes);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    rc = cuda_check(cudaMemcpyAsync(self->stage_in, host_in, op->vec_bytes, cudaMemcpyHostToDevice, s), "H2D");
+    if (!rc) rc = op_apply(op, self->stage_in, self->stage_out, m0, dagger ? -1 : +1, s);
+    if (!rc) rc = cuda_check(cudaMemcpyAsync(host_out, self->stage_out, op->vec_bytes, cudaMemcpyDeviceToHost, s), "D2H");
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(s), "apply_host sync");
+    return rc;
+}
+
+int dirac_vec_norm2(const dirac_op *op, const void *v, double *out_dev, void *stream) {
+    if (!op || !out_dev) return DIRAC_ERR_INVALID_ARG;
+    int rc = check_vec(v);
+    return rc ? rc : blas_norm2(op, op->prec, v, out_dev, (cudaStream_t)stream);
+}
+
+int dirac_vec_dot(const dirac_op *op, const void *u, const void *v, double *out_dev, void *stream) {
+    if (!op || !out_dev) return DIRAC_ERR_INVALID_ARG;
+    int rc = check_vec(u);
+    if (!rc) rc = check_vec(v);
+    return rc ? rc : blas_dot(op, op->prec, u, v, out_dev, (cudaStream_t)stream);
+}
+
+int dirac_vec_axpy(const dirac_op *op, const double *alpha_dev, const void *x, void *y, void *stream) {
+    if (!op || !alpha_dev) return DIRAC_ERR_INVALID_ARG;
+    int rc = check_vec(x);
+    if (!rc) rc = check_vec(y);
+    return rc ? rc : blas_axpy(op, op->prec, alpha_dev, x, y, (cudaStream_t)stream);
+}
+
+int dirac_vec_gamma5(const dirac_op *op, void *v, void *stream) {
+    if (!op) return DIRAC_ERR_INVALID_ARG;
+    int rc = check_vec(v);
+    return rc ? rc : blas_gamma5(op, op->prec, v, (cudaStream_t)stream);
+}
+
+int dirac_vec_convert(const dirac_op *op, const void *src, dirac_prec src_prec, void *dst, dirac_prec dst_prec,
+                      void *stream) {
+    if (!op) return DIRAC_ERR_INVALID_ARG;
+    if (src_prec < DIRAC_F64 || src_prec > DIRAC_F16 || dst_prec < DIRAC_F64 || dst_prec > DIRAC_F16)
+        return DIRAC_ERR_UNSUPPORTED_PREC;
+    int rc = check_vec(src);
+    if (!rc) rc = check_vec(dst);
+    return rc ? rc : blas_convert(op, src, src_prec, dst, dst_prec, (cudaStream_t)stream);
+}
+
+const char *dirac_error_string(int code) {
+    switch (code) {
+    case DIRAC_OK: return "success";
+    case DIRAC_ERR_INVALID_ARG: return "invalid argument";
+    case DIRAC_ERR_UNSUPPORTED_NC: return "unsupported number of colours";
+    case DIRAC_ERR_UNSUPPORTED_PREC: return "unsupported precision";
+    case DIRAC_ERR_ALIGNMENT: return "vector pointer not 16-byte aligned";
+    case DIRAC_ERR_OOM: return "device allocation failed";
+    case DIRAC_ERR_CUDA: return "CUDA error";
+    case DIRAC_ERR_DEVICE_TIMEOUT: return "bounded device wait timed out";
+    case DIRAC_NOT_CONVERGED: return "solver reached maxit";
+    case DIRAC_STAGNATED: return "solver stagnated (updated vs recomputed residual differ by >1%)";
+    case DIRAC_BREAKDOWN: return "solver breakdown";
+    case DIRAC_NONFINITE: return "non-finite residual";
+    }
+    return "unknown code";
+}
+
+long dirac_flops_per_site(dirac_kind kind, int nc) {
+    const long n = nc;
+    switch (kind) {
+    case DIRAC_WILSON: return 128 * n * n + 72 * n;
+    case DIRAC_BRILLOUIN: return 2560 * n * n + 2376 * n;
+    case DIRAC_STAGGERED: return 64 * n * n + 2 * n;
+    }
+    return -1;
+}
+
+int dirac_version(void) { return 100; }
+
+}  // extern "C"

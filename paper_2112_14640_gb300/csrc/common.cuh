@@ -1,0 +1,197 @@
+// common.cuh -- device-side building blocks shared by the stencil, BLAS-1
+// and solver kernels: complex arithmetic in the accumulation type,
+// precision-generic vectorised loads/stores of interleaved complex data, and
+// lattice index arithmetic (site n = ((t*Nz + z)*Ny + y)*Nx + x).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dirac.h"
+
+namespace dgb {
+
+// ------------------------------------------------------------------ complex
+template <typename A>
+struct cx {
+    A re, im;
+};
+
+template <typename A>
+__host__ __device__ __forceinline__ cx<A> mk(A r, A i) { return cx<A>{r, i}; }
+template <typename A>
+__device__ __forceinline__ cx<A> operator+(cx<A> a, cx<A> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename A>
+__device__ __forceinline__ cx<A> operator-(cx<A> a, cx<A> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename A>
+__device__ __forceinline__ cx<A> operator*(A s, cx<A> a) { return {s * a.re, s * a.im}; }
+template <typename A>
+__device__ __forceinline__ cx<A> conj(cx<A> a) { return {a.re, -a.im}; }
+// i * a
+template <typename A>
+__device__ __forceinline__ cx<A> times_i(cx<A> a) { return {-a.im, a.re}; }
+// acc += a * b (complex), written as four FMAs
+template <typename A>
+__device__ __forceinline__ void cmac(cx<A> &acc, cx<A> a, cx<A> b) {
+    acc.re = fma(a.re, b.re, acc.re);
+    acc.re = fma(-a.im, b.im, acc.re);
+    acc.im = fma(a.re, b.im, acc.im);
+    acc.im = fma(a.im, b.re, acc.im);
+}
+// acc += conj(a) * b
+template <typename A>
+__device__ __forceinline__ void cmac_conj(cx<A> &acc, cx<A> a, cx<A> b) {
+    acc.re = fma(a.re, b.re, acc.re);
+    acc.re = fma(a.im, b.im, acc.re);
+    acc.im = fma(a.re, b.im, acc.im);
+    acc.im = fma(-a.im, b.re, acc.im);
+}
+template <typename A>
+__device__ __forceinline__ cx<A> cmul(cx<A> a, cx<A> b) {
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+// acc += s * a (real s)
+template <typename A>
+__device__ __forceinline__ void rmac(cx<A> &acc, A s, cx<A> a) {
+    acc.re = fma(s, a.re, acc.re);
+    acc.im = fma(s, a.im, acc.im);
+}
+
+// -------------------------------------------------------- storage elements
+template <typename E> struct Acc { using T = float; };
+template <> struct Acc<double> { using T = double; };
+
+template <typename E> __device__ __forceinline__ typename Acc<E>::T to_acc(E e);
+template <> __device__ __forceinline__ double to_acc<double>(double e) { return e; }
+template <> __device__ __forceinline__ float to_acc<float>(float e) { return e; }
+template <> __device__ __forceinline__ float to_acc<__nv_bfloat16>(__nv_bfloat16 e) { return __bfloat162float(e); }
+template <> __device__ __forceinline__ float to_acc<__half>(__half e) { return __half2float(e); }
+
+template <typename E, typename A> __device__ __forceinline__ E from_acc(A a);
+template <> __device__ __forceinline__ double from_acc<double, double>(double a) { return a; }
+template <> __device__ __forceinline__ float from_acc<float, float>(float a) { return a; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_acc<__nv_bfloat16, float>(float a) { return __float2bfloat16_rn(a); }
+template <> __device__ __forceinline__ __half from_acc<__half, float>(float a) { return __float2half_rn(a); }
+// conversions between accumulation types (used by precision casts)
+template <> __device__ __forceinline__ float from_acc<float, double>(double a) { return (float)a; }
+template <> __device__ __forceinline__ double from_acc<double, float>(float a) { return (double)a; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_acc<__nv_bfloat16, double>(double a) { return __double2bfloat16(a); }
+template <> __device__ __forceinline__ __half from_acc<__half, double>(double a) { return __double2half(a); }
+
+template <int BYTES> struct Raw;
+template <> struct Raw<16> { using T = uint4; };
+template <> struct Raw<8> { using T = uint2; };
+template <> struct Raw<4> { using T = unsigned int; };
+
+// Load N consecutive complex numbers starting at element pointer p (2N
+// elements), converting to the accumulation type.  Uses 16-byte (or smaller)
+// vector loads; p must be aligned to min(16, 2*N*sizeof(E)) bytes.
+template <typename E, int N, typename A = typename Acc<E>::T>
+__device__ __forceinline__ void load_cx(const E *__restrict__ p, cx<A> *out) {
+    constexpr int BYTES = 2 * N * (int)sizeof(E);
+    if constexpr (BYTES <= 16) {
+        using R = typename Raw<BYTES>::T;
+        R raw = __ldg(reinterpret_cast<const R *>(p));
+        E e[2 * N];
+        __builtin_memcpy(e, &raw, BYTES);
+#pragma unroll
+        for (int i = 0; i < N; ++i) out[i] = cx<A>{(A)to_acc<E>(e[2 * i]), (A)to_acc<E>(e[2 * i + 1])};
+    } else {
+        constexpr int PER = 16 / (2 * (int)sizeof(E));
+#pragma unroll
+        for (int k = 0; k < N / PER; ++k) load_cx<E, PER, A>(p + 2 * PER * k, out + PER * k);
+    }
+}
+
+template <typename E, int N, typename A>
+__device__ __forceinline__ void store_cx(E *__restrict__ p, const cx<A> *in) {
+    constexpr int BYTES = 2 * N * (int)sizeof(E);
+    if constexpr (BYTES <= 16) {
+        using R = typename Raw<BYTES>::T;
+        E e[2 * N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            e[2 * i] = from_acc<E, A>(in[i].re);
+            e[2 * i + 1] = from_acc<E, A>(in[i].im);
+        }
+        R raw;
+        __builtin_memcpy(&raw, e, BYTES);
+        *reinterpret_cast<R *>(p) = raw;
+    } else {
+        constexpr int PER = 16 / (2 * (int)sizeof(E));
+#pragma unroll
+        for (int k = 0; k < N / PER; ++k) store_cx<E, PER, A>(p + 2 * PER * k, in + PER * k);
+    }
+}
+
+// Single complex load without vector width requirements (links, W links).
+template <typename E, typename A = typename Acc<E>::T>
+__device__ __forceinline__ cx<A> ld1(const E *__restrict__ p) {
+    if constexpr (sizeof(E) == 8) {
+        double2 d = __ldg(reinterpret_cast<const double2 *>(p));
+        return cx<A>{(A)d.x, (A)d.y};
+    } else if constexpr (sizeof(E) == 4) {
+        float2 f = __ldg(reinterpret_cast<const float2 *>(p));
+        return cx<A>{(A)f.x, (A)f.y};
+    } else {
+        cx<A> r;
+        load_cx<E, 1, A>(p, &r);
+        return r;
+    }
+}
+
+// Load an NC x NC colour matrix (row-major, complex) into registers.
+template <int NC, typename E, typename A>
+__device__ __forceinline__ void load_mat(const E *__restrict__ p, cx<A> (&M)[NC][NC]) {
+#pragma unroll
+    for (int a = 0; a < NC; ++a)
+#pragma unroll
+        for (int b = 0; b < NC; ++b) M[a][b] = ld1<E, A>(p + 2 * (a * NC + b));
+}
+
+// --------------------------------------------------------------- geometry
+struct Lat {
+    int nx, ny, nz, nt;
+    int nv;
+    long long V;
+};
+
+struct Coord {
+    int x, y, z, t;
+};
+
+__device__ __forceinline__ Coord site_coords(const Lat &g, long long n) {
+    Coord c;
+    c.x = (int)(n % g.nx);
+    long long r = n / g.nx;
+    c.y = (int)(r % g.ny);
+    r /= g.ny;
+    c.z = (int)(r % g.nz);
+    c.t = (int)(r / g.nz);
+    return c;
+}
+
+// Site index of the neighbour n + sign * mu-hat (periodic wrap).
+__device__ __forceinline__ long long neighbour(const Lat &g, long long n, const Coord &c, int mu, int sign) {
+    long long stride;
+    int coord, extent;
+    switch (mu) {
+    case 0: stride = 1; coord = c.x; extent = g.nx; break;
+    case 1: stride = g.nx; coord = c.y; extent = g.ny; break;
+    case 2: stride = (long long)g.nx * g.ny; coord = c.z; extent = g.nz; break;
+    default: stride = (long long)g.nx * g.ny * g.nz; coord = c.t; extent = g.nt; break;
+    }
+    if (sign > 0) return (coord == extent - 1) ? n - (long long)(extent - 1) * stride : n + stride;
+    return (coord == 0) ? n + (long long)(extent - 1) * stride : n - stride;
+}
+
+// Element type for each storage precision.
+template <int P> struct Elem;
+template <> struct Elem<DIRAC_F64> { using T = double; };
+template <> struct Elem<DIRAC_F32> { using T = float; };
+template <> struct Elem<DIRAC_BF16> { using T = __nv_bfloat16; };
+template <> struct Elem<DIRAC_F16> { using T = __half; };
+
+}  // namespace dgb

@@ -1,0 +1,122 @@
+// internal.h -- operator handle and launcher prototypes shared by the
+// translation units of libdirac.so (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdio.h>
+
+#include <type_traits>
+#include <utility>
+
+#include "../../include/dirac.h"
+#include "common.cuh"
+
+struct dirac_op {
+    dirac_kind kind;
+    dirac_geom geom;
+    dgb::Lat lat;
+    int nc, nv;
+    dirac_prec prec;
+    long long V;
+    long long rows;        // complex rows per RHS column: V*nc*4 (Wilson-type) or V*nc
+    size_t vec_bytes;      // bytes of one multi-RHS vector
+    size_t link_bytes;     // bytes of the phased link copy
+    size_t w_bytes;        // bytes of the 80 W links per site (Brillouin)
+    void *links;           // [V][4][nc][nc], boundary phases folded in
+    void *w;               // [V][80][nc][nc] (Brillouin only)
+    void *scratch;         // one vector: intermediate of D^dag D
+    void *stage_in;        // host-apply staging buffers (lazy)
+    void *stage_out;
+    double *red_partial;   // reduction partials [red_blocks][nv][2]
+    int red_blocks;
+    void *solver_ws;       // solver workspace (lazy), solver_ws_bytes long
+    size_t solver_ws_bytes;
+    dirac_op *inner[4];    // lower-precision twins for mixed solves (lazy)
+};
+
+namespace dgb {
+
+inline int cuda_check(cudaError_t e, const char *what) {
+    if (e != cudaSuccess) {
+        fprintf(stderr, "libdirac: %s: %s\n", what, cudaGetErrorString(e));
+        return DIRAC_ERR_CUDA;
+    }
+    return DIRAC_OK;
+}
+inline int launch_check(const char *what) { return cuda_check(cudaGetLastError(), what); }
+
+inline size_t elem_bytes(dirac_prec p) { return p == DIRAC_F64 ? 8 : p == DIRAC_F32 ? 4 : 2; }
+
+// Largest RHS-vector width (complex numbers per thread) that divides nv and
+// gives at most 16-byte loads.
+inline int pick_vr(dirac_prec p, int nv) {
+    int vr = (int)(16 / (2 * elem_bytes(p)));
+    while (vr > 1 && nv % vr) vr /= 2;
+    return vr;
+}
+
+template <typename F>
+int dispatch_prec(dirac_prec p, F &&f) {
+    switch (p) {
+    case DIRAC_F64: return f((double *)nullptr);
+    case DIRAC_F32: return f((float *)nullptr);
+    case DIRAC_BF16: return f((__nv_bfloat16 *)nullptr);
+    case DIRAC_F16: return f((__half *)nullptr);
+    }
+    return DIRAC_ERR_UNSUPPORTED_PREC;
+}
+
+template <typename F>
+int dispatch_nc(int nc, F &&f) {
+    switch (nc) {
+    case 1: return f(std::integral_constant<int, 1>{});
+    case 2: return f(std::integral_constant<int, 2>{});
+    case 3: return f(std::integral_constant<int, 3>{});
+    case 4: return f(std::integral_constant<int, 4>{});
+    }
+    return DIRAC_ERR_UNSUPPORTED_NC;
+}
+
+template <typename F>
+int dispatch_vr(int vr, F &&f) {
+    switch (vr) {
+    case 1: return f(std::integral_constant<int, 1>{});
+    case 2: return f(std::integral_constant<int, 2>{});
+    case 4: return f(std::integral_constant<int, 4>{});
+    }
+    return DIRAC_ERR_INVALID_ARG;
+}
+
+inline unsigned grid_for(long long threads, int block) {
+    return (unsigned)((threads + block - 1) / block);
+}
+
+// stencils (sgn = +1: D, -1: D^dag)
+int launch_wilson(const dirac_op *op, const void *in, void *out, double m0, int sgn, cudaStream_t s);
+int launch_staggered(const dirac_op *op, const void *in, void *out, double m0, int sgn, cudaStream_t s);
+int launch_brillouin(const dirac_op *op, const void *in, void *out, double m0, int sgn, cudaStream_t s);
+
+// link preparation
+int launch_phase_links(dirac_op *op, const void *U, dirac_prec u_prec, cudaStream_t s);
+int launch_build_w(dirac_op *op, const void *U, dirac_prec u_prec, cudaStream_t s);
+int launch_convert_links(const dirac_op *src, dirac_op *dst, cudaStream_t s);
+
+// BLAS-1 (vectors in precision p with op's shape)
+int blas_norm2(const dirac_op *op, dirac_prec p, const void *v, double *out, cudaStream_t s);
+int blas_dot(const dirac_op *op, dirac_prec p, const void *u, const void *v, double *out, cudaStream_t s);
+int blas_axpy(const dirac_op *op, dirac_prec p, const double *alpha, const void *x, void *y, cudaStream_t s);
+// z = a x + b y per RHS; a = as * a_coef[v] (complex pairs) or as when a_coef is null (same for b);
+// x or y may be null; z may alias x or y; norm_out (device, nv doubles) receives |z|^2 if non-null.
+int blas_axpby(const dirac_op *op, dirac_prec p, void *z, const void *x, const double *a_coef, double as,
+               const void *y, const double *b_coef, double bs, double *norm_out, cudaStream_t s);
+int blas_gamma5(const dirac_op *op, dirac_prec p, void *v, cudaStream_t s);
+int blas_convert(const dirac_op *op, const void *src, dirac_prec sp, void *dst, dirac_prec dp, cudaStream_t s);
+
+// operator handle helpers (capi.cu)
+int op_apply(const dirac_op *op, const void *in, void *out, double m0, int sgn, cudaStream_t s);
+int op_apply_normal(const dirac_op *op, const void *in, void *out, double m0, cudaStream_t s);
+int op_alloc(dirac_kind kind, const dirac_geom *g, dirac_op **out);
+int op_inner(const dirac_op *op, dirac_prec p, dirac_op **out, cudaStream_t s);
+void op_destroy(dirac_op *op);
+
+}  // namespace dgb

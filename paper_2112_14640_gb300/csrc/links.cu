@@ -1,0 +1,187 @@
+// links.cu -- gauge-field preparation done once per field:
+//  * phase_links: the operator's own copy of U in its storage precision with
+//    the boundary phase bc[mu] folded into U_mu(n) where n_mu = N_mu - 1;
+//  * build_w: the 80 off-centre Brillouin links of Tab. off-axis,
+//      W_s(n) = (1/k!) sum over the k! minimal paths n -> n+s of the ordered
+//               products of signed links V_{+mu}(m) = U_mu(m), V_{-mu}(m) = U_mu(m-mu)^dag.
+//    Grouping the paths by their last hop sigma gives the recursion
+//      W_s(n) = (1/k) sum_{mu: s_mu != 0} W_{s - s_mu mu}(n) V_{s_mu mu}(n + s - s_mu mu),
+//    evaluated level by level (k = 1..4) in shared memory, in FP64, one
+//    thread block per site; the result is stored in the operator precision.
+#include "internal.h"
+
+namespace dgb {
+
+struct Phases {
+    int bc[4];
+};
+
+template <typename UE>
+__device__ __forceinline__ cx<double> ld_u(const UE *U, long long idx) {
+    return cx<double>{(double)U[2 * idx], (double)U[2 * idx + 1]};
+}
+
+template <typename UE, typename E>
+__global__ void phase_links_kernel(const UE *__restrict__ U, E *__restrict__ out, Lat g, Phases ph, int nc) {
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;   // (site, mu)
+    if (tid >= g.V * 4) return;
+    const long long n = tid / 4;
+    const int mu = (int)(tid % 4);
+    const Coord c = site_coords(g, n);
+    const int coord = mu == 0 ? c.x : mu == 1 ? c.y : mu == 2 ? c.z : c.t;
+    const int ext = mu == 0 ? g.nx : mu == 1 ? g.ny : mu == 2 ? g.nz : g.nt;
+    const double f = (coord == ext - 1) ? (double)ph.bc[mu] : 1.0;
+    const int per = nc * nc;
+    for (int e = 0; e < per; ++e) {
+        cx<double> u = ld_u(U, tid * per + e);
+        out[2 * (tid * per + e)] = from_acc<E, double>(f * u.re);
+        out[2 * (tid * per + e) + 1] = from_acc<E, double>(f * u.im);
+    }
+}
+
+// signed link V_{sign mu}(m) with boundary phase, in FP64
+template <int NC, typename UE>
+__device__ __forceinline__ void signed_link(const UE *__restrict__ U, const Lat &g, const Phases &ph,
+                                            const int x[4], int mu, int sign, cx<double> (&L)[NC][NC]) {
+    const int ext[4] = {g.nx, g.ny, g.nz, g.nt};
+    int y[4] = {x[0], x[1], x[2], x[3]};
+    if (sign < 0) y[mu] = (y[mu] == 0) ? ext[mu] - 1 : y[mu] - 1;
+    const long long site = (((long long)y[3] * g.nz + y[2]) * g.ny + y[1]) * g.nx + y[0];
+    const double f = (y[mu] == ext[mu] - 1) ? (double)ph.bc[mu] : 1.0;
+    const long long base = (site * 4 + mu) * NC * NC;
+#pragma unroll
+    for (int a = 0; a < NC; ++a)
+#pragma unroll
+        for (int b = 0; b < NC; ++b) {
+            cx<double> u = ld_u(U, base + (sign > 0 ? a * NC + b : b * NC + a));
+            L[a][b] = sign > 0 ? cx<double>{f * u.re, f * u.im} : cx<double>{f * u.re, -f * u.im};
+        }
+}
+
+template <int NC, typename UE, typename E>
+__global__ void __launch_bounds__(96) build_w_kernel(const UE *__restrict__ U, E *__restrict__ W, Lat g, Phases ph) {
+    __shared__ cx<double> Ws[81][NC * NC];
+    const long long n = blockIdx.x;
+    const int dir = threadIdx.x;
+    const Coord c = site_coords(g, n);
+    const int x0[4] = {c.x, c.y, c.z, c.t};
+    const int ext[4] = {g.nx, g.ny, g.nz, g.nt};
+    int s[4] = {0, 0, 0, 0}, k = 0;
+    if (dir < 81) {
+        s[0] = dir % 3 - 1;
+        s[1] = (dir / 3) % 3 - 1;
+        s[2] = (dir / 9) % 3 - 1;
+        s[3] = dir / 27 - 1;
+        k = (s[0] != 0) + (s[1] != 0) + (s[2] != 0) + (s[3] != 0);
+        if (k == 0)
+            for (int a = 0; a < NC; ++a)
+                for (int b = 0; b < NC; ++b) Ws[40][a * NC + b] = cx<double>{a == b ? 1.0 : 0.0, 0.0};
+    }
+    const int pow3[4] = {1, 3, 9, 27};
+    __syncthreads();   // the identity at the centre feeds level 1
+    for (int level = 1; level <= 4; ++level) {
+        if (dir < 81 && k == level) {
+            cx<double> acc[NC][NC];
+            for (int a = 0; a < NC; ++a)
+                for (int b = 0; b < NC; ++b) acc[a][b] = cx<double>{0, 0};
+            for (int mu = 0; mu < 4; ++mu) {
+                if (s[mu] == 0) continue;
+                const int prev = dir - s[mu] * pow3[mu];   // offset s - s_mu mu
+                // last hop starts at n + s - s_mu mu
+                int m[4];
+                for (int nu = 0; nu < 4; ++nu) {
+                    int v = x0[nu] + (nu == mu ? 0 : s[nu]);
+                    m[nu] = (v + ext[nu]) % ext[nu];
+                }
+                cx<double> L[NC][NC];
+                signed_link<NC>(U, g, ph, m, mu, s[mu], L);
+                for (int a = 0; a < NC; ++a)
+                    for (int b = 0; b < NC; ++b)
+                        for (int q = 0; q < NC; ++q) cmac(acc[a][b], Ws[prev][a * NC + q], L[q][b]);
+            }
+            const double inv = 1.0 / level;
+            for (int a = 0; a < NC; ++a)
+                for (int b = 0; b < NC; ++b) Ws[dir][a * NC + b] = inv * acc[a][b];
+        }
+        __syncthreads();
+    }
+    if (dir < 81 && dir != 40) {
+        const int dirp = dir < 40 ? dir : dir - 1;
+        E *o = W + 2 * ((n * 80 + dirp) * NC * NC);
+        for (int e = 0; e < NC * NC; ++e) {
+            o[2 * e] = from_acc<E, double>(Ws[dir][e].re);
+            o[2 * e + 1] = from_acc<E, double>(Ws[dir][e].im);
+        }
+    }
+}
+
+template <typename F>
+static int dispatch_uprec(dirac_prec p, F &&f) {
+    if (p == DIRAC_F64) return f((double *)nullptr);
+    if (p == DIRAC_F32) return f((float *)nullptr);
+    return DIRAC_ERR_UNSUPPORTED_PREC;
+}
+
+static Phases phases_of(const dirac_op *op) {
+    Phases ph;
+    for (int m = 0; m < 4; ++m) ph.bc[m] = op->geom.bc[m];
+    return ph;
+}
+
+int launch_phase_links(dirac_op *op, const void *U, dirac_prec u_prec, cudaStream_t s) {
+    return dispatch_uprec(u_prec, [&](auto utag) {
+        using UE = std::remove_pointer_t<decltype(utag)>;
+        return dispatch_prec(op->prec, [&](auto tag) {
+            using E = std::remove_pointer_t<decltype(tag)>;
+            const long long threads = op->V * 4;
+            phase_links_kernel<UE, E><<<grid_for(threads, 128), 128, 0, s>>>((const UE *)U, (E *)op->links,
+                                                                            op->lat, phases_of(op), op->nc);
+            return launch_check("phase_links_kernel");
+        });
+    });
+}
+
+int launch_build_w(dirac_op *op, const void *U, dirac_prec u_prec, cudaStream_t s) {
+    return dispatch_uprec(u_prec, [&](auto utag) {
+        using UE = std::remove_pointer_t<decltype(utag)>;
+        return dispatch_prec(op->prec, [&](auto tag) {
+            using E = std::remove_pointer_t<decltype(tag)>;
+            return dispatch_nc(op->nc, [&](auto ncc) {
+                constexpr int NC = decltype(ncc)::value;
+                build_w_kernel<NC, UE, E><<<(unsigned)op->V, 96, 0, s>>>((const UE *)U, (E *)op->w, op->lat,
+                                                                       phases_of(op));
+                return launch_check("build_w_kernel");
+            });
+        });
+    });
+}
+
+template <typename S, typename D>
+__global__ void convert_scalars_kernel(const S *__restrict__ src, D *__restrict__ dst, long long count) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) dst[i] = from_acc<D, typename Acc<S>::T>(to_acc<S>(src[i]));
+}
+
+static int convert_array(const void *src, dirac_prec sp, void *dst, dirac_prec dp, long long count, cudaStream_t s) {
+    return dispatch_prec(sp, [&](auto stag) {
+        using S = std::remove_pointer_t<decltype(stag)>;
+        return dispatch_prec(dp, [&](auto dtag) {
+            using D = std::remove_pointer_t<decltype(dtag)>;
+            convert_scalars_kernel<S, D><<<grid_for(count, 256), 256, 0, s>>>((const S *)src, (D *)dst, count);
+            return launch_check("convert_scalars_kernel");
+        });
+    });
+}
+
+int launch_convert_links(const dirac_op *src, dirac_op *dst, cudaStream_t s) {
+    long long n = src->V * 4 * src->nc * src->nc * 2;
+    int rc = convert_array(src->links, src->prec, dst->links, dst->prec, n, s);
+    if (rc) return rc;
+    if (src->kind == DIRAC_BRILLOUIN) {
+        n = src->V * 80 * src->nc * src->nc * 2;
+        rc = convert_array(src->w, src->prec, dst->w, dst->prec, n, s);
+    }
+    return rc;
+}
+
+}  // namespace dgb

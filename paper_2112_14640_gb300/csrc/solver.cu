@@ -1,0 +1,520 @@
+// solver.cu -- Krylov solvers of Sec. 9 on the multi-RHS operators:
+//  * CG on the normal equations D^dag D x = D^dag b (one independent
+//    recursion per RHS: own alpha^(i), beta^(i));
+//  * BiCGstab on D x = b (van der Vorst, shadow residual r_hat = r_0);
+//  * defect correction ("mixed precision" solvers of Sec. 9): the residual
+//    r = b - A x, its norm, the convergence test and the update x += e are
+//    done in the operator's precision, the correction e comes from a Krylov
+//    solve of A e = r/|r| in a lower storage precision (BF16/FP16/FP32
+//    links and vectors, FP32 arithmetic, FP64 reductions).
+// Recompute/exit rules (Sec. 9): recompute r = b - A x when the iteration
+// count is a multiple of recompute_every, when every active RHS's updated
+// residual passes, or at maxit; exit when all recomputed residuals pass, when
+// updated and recomputed norms of an unconverged RHS differ by more than 1%,
+// or at maxit.  An RHS whose recomputed residual passes is frozen
+// (alpha = beta = 0) while the others continue.
+//
+// Per-RHS coefficients are formed on the device from FP64 reductions; the
+// host reads the N_v residual norms once per iteration to apply the rules.
+#include <math.h>
+#include <string.h>
+
+#include <chrono>
+
+#include "internal.h"
+
+namespace dgb {
+
+constexpr int kWsVecs = 8;
+constexpr int kNS = 64;   // max RHS
+
+struct Ws {
+    void *v[kWsVecs];
+    double *rr, *rr_new, *pq, *alpha, *beta, *act, *nb, *c1, *c2, *c3, *omega, *rho, *rho_new, *tt;
+};
+
+static int get_ws(const dirac_op *op, Ws &w) {
+    dirac_op *self = (dirac_op *)op;
+    const size_t scal = 16 * kNS * 2 * sizeof(double);
+    const size_t need = kWsVecs * op->vec_bytes + scal;
+    if (!self->solver_ws) {
+        if (cudaMalloc(&self->solver_ws, need) != cudaSuccess) {
+            cudaGetLastError();
+            self->solver_ws = nullptr;
+            return DIRAC_ERR_OOM;
+        }
+        self->solver_ws_bytes = need;
+    }
+    char *base = (char *)self->solver_ws;
+    for (int i = 0; i < kWsVecs; ++i) w.v[i] = base + i * op->vec_bytes;
+    double *d = (double *)(base + kWsVecs * op->vec_bytes);
+    double **arr[] = {&w.rr, &w.rr_new, &w.pq, &w.alpha, &w.beta, &w.act, &w.nb, &w.c1,
+                      &w.c2, &w.c3, &w.omega, &w.rho, &w.rho_new, &w.tt};
+    for (size_t i = 0; i < sizeof(arr) / sizeof(arr[0]); ++i) *arr[i] = d + i * kNS * 2;
+    return DIRAC_OK;
+}
+
+// ---------------------------------------------------------------- coefficient kernels
+__global__ void cg_alpha_kernel(int nv, const double *rr, const double *pq, const double *act, double *alpha) {
+    const int v = threadIdx.x;
+    if (v >= nv) return;
+    const double p = pq[2 * v];
+    const double a = (act[v] != 0.0 && p != 0.0) ? rr[v] / p : 0.0;
+    alpha[2 * v] = a;
+    alpha[2 * v + 1] = 0.0;
+}
+
+__global__ void cg_beta_kernel(int nv, const double *rr_new, double *rr, const double *act, double *beta) {
+    const int v = threadIdx.x;
+    if (v >= nv) return;
+    const double b = (act[v] != 0.0 && rr[v] != 0.0) ? rr_new[v] / rr[v] : 0.0;
+    beta[2 * v] = b;
+    beta[2 * v + 1] = 0.0;
+    rr[v] = rr_new[v];
+}
+
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+    const double d = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+__device__ __forceinline__ double2 cmuld(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// beta = (rho_new/rho) (alpha/omega); c1 = beta, c2 = -beta*omega; flags breakdown in act (=0)
+__global__ void bicg_beta_kernel(int nv, const double *rho_new, const double *rho, const double *alpha,
+                                 const double *omega, double *act, double *beta, double *c2, double *brk) {
+    const int v = threadIdx.x;
+    if (v >= nv) return;
+    double2 rn = make_double2(rho_new[2 * v], rho_new[2 * v + 1]);
+    double2 ro = make_double2(rho[2 * v], rho[2 * v + 1]);
+    double2 al = make_double2(alpha[2 * v], alpha[2 * v + 1]);
+    double2 om = make_double2(omega[2 * v], omega[2 * v + 1]);
+    double2 b = make_double2(0, 0);
+    if (act[v] != 0.0) {
+        if (hypot(rn.x, rn.y) == 0.0 || hypot(om.x, om.y) == 0.0) {
+            act[v] = 0.0;
+            brk[v] = 1.0;
+        } else {
+            b = cmuld(cdiv(rn, ro), cdiv(al, om));
+        }
+    }
+    beta[2 * v] = b.x;
+    beta[2 * v + 1] = b.y;
+    double2 bo = cmuld(b, om);
+    c2[2 * v] = -bo.x;
+    c2[2 * v + 1] = -bo.y;
+}
+
+// alpha = rho_new / <rhat, v>
+__global__ void bicg_alpha_kernel(int nv, const double *rho_new, const double *rv, const double *act, double *alpha) {
+    const int v = threadIdx.x;
+    if (v >= nv) return;
+    double2 a = make_double2(0, 0);
+    double2 d = make_double2(rv[2 * v], rv[2 * v + 1]);
+    if (act[v] != 0.0 && (d.x != 0.0 || d.y != 0.0))
+        a = cdiv(make_double2(rho_new[2 * v], rho_new[2 * v + 1]), d);
+    alpha[2 * v] = a.x;
+    alpha[2 * v + 1] = a.y;
+}
+
+// omega = <t, s> / <t, t>; rho = rho_new
+__global__ void bicg_omega_kernel(int nv, const double *ts, const double *tt, const double *act, double *omega,
+                                  const double *rho_new, double *rho, double *brk, double *actw) {
+    const int v = threadIdx.x;
+    if (v >= nv) return;
+    double2 o = make_double2(0, 0);
+    if (act[v] != 0.0 && tt[v] > 0.0) o = make_double2(ts[2 * v] / tt[v], ts[2 * v + 1] / tt[v]);
+    if (act[v] != 0.0 && o.x == 0.0 && o.y == 0.0) {
+        brk[v] = 1.0;
+        actw[v] = 0.0;
+    }
+    omega[2 * v] = o.x;
+    omega[2 * v + 1] = o.y;
+    rho[2 * v] = rho_new[2 * v];
+    rho[2 * v + 1] = rho_new[2 * v + 1];
+}
+
+// c[2v] = act ? scale * f(x[v]) : 0 with f = 1/sqrt or sqrt
+__global__ void coef_from_norm_kernel(int nv, const double *rr, const double *act, double *c, int inverse) {
+    const int v = threadIdx.x;
+    if (v >= nv) return;
+    double r = sqrt(rr[v]);
+    double val = (act[v] != 0.0 && r > 0.0) ? (inverse ? 1.0 / r : r) : 0.0;
+    c[2 * v] = val;
+    c[2 * v + 1] = 0.0;
+}
+
+// ---------------------------------------------------------------- host helpers
+static int to_host(double *h, const double *d, int n, cudaStream_t s) {
+    int rc = cuda_check(cudaMemcpyAsync(h, d, n * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H scalars");
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(s), "solver sync");
+    return rc;
+}
+static int to_dev(double *d, const double *h, int n, cudaStream_t s) {
+    return cuda_check(cudaMemcpyAsync(d, h, n * sizeof(double), cudaMemcpyHostToDevice, s), "H2D scalars");
+}
+
+#define TRY(x)                  \
+    do {                        \
+        int rc_ = (x);          \
+        if (rc_) return rc_;    \
+    } while (0)
+
+struct CoreOut {
+    int iters = 0, recomputes = 0, status = 0;
+    int status_rhs[kNS];
+    double relres[kNS];
+};
+
+// A = D^dag D (normal = true) applied through the operator scratch.
+static int apply_A(const dirac_op *op, const void *in, void *out, double m0, cudaStream_t s) {
+    return op_apply_normal(op, in, out, m0, s);
+}
+
+// CG on A x = rhs (A = D^dag D), x in/out.  Uses ws vectors 0..2.
+static int cg_core(const dirac_op *op, const void *rhs, void *x, double m0, double tol, int maxit, int every,
+                   CoreOut &out, cudaStream_t s) {
+    Ws w;
+    TRY(get_ws(op, w));
+    const int nv = op->nv;
+    const dirac_prec p = op->prec;
+    void *r = w.v[0], *pv = w.v[1], *q = w.v[2];
+    double nb[kNS], rr[kNS], act[kNS], rrt[kNS];
+    TRY(blas_norm2(op, p, rhs, w.nb, s));
+    TRY(to_host(nb, w.nb, nv, s));
+    // r = rhs - A x
+    TRY(apply_A(op, x, q, m0, s));
+    TRY(blas_axpby(op, p, r, rhs, nullptr, 1.0, q, nullptr, -1.0, w.rr, s));
+    TRY(blas_axpby(op, p, pv, r, nullptr, 1.0, nullptr, nullptr, 0.0, nullptr, s));
+    TRY(to_host(rr, w.rr, nv, s));
+    int nact = 0;
+    for (int v = 0; v < nv; ++v) {
+        const bool conv = nb[v] == 0.0 || sqrt(rr[v]) < tol * sqrt(nb[v]);
+        act[v] = conv ? 0.0 : 1.0;
+        out.status_rhs[v] = conv ? DIRAC_OK : DIRAC_NOT_CONVERGED;
+        out.relres[v] = nb[v] > 0 ? sqrt(rr[v] / nb[v]) : 0.0;
+        nact += !conv;
+    }
+    TRY(to_dev(w.act, act, nv, s));
+    out.status = DIRAC_OK;
+    int it = 0;
+    while (nact > 0) {
+        ++it;
+        TRY(apply_A(op, pv, q, m0, s));
+        TRY(blas_dot(op, p, pv, q, w.pq, s));
+        cg_alpha_kernel<<<1, kNS, 0, s>>>(nv, w.rr, w.pq, w.act, w.alpha);
+        TRY(blas_axpby(op, p, x, x, nullptr, 1.0, pv, w.alpha, 1.0, nullptr, s));
+        TRY(blas_axpby(op, p, r, r, nullptr, 1.0, q, w.alpha, -1.0, w.rr_new, s));
+        double rn[kNS];
+        TRY(to_host(rn, w.rr_new, nv, s));
+        bool all_pass = true, finite = true;
+        for (int v = 0; v < nv; ++v) {
+            if (!isfinite(rn[v])) finite = false;
+            if (act[v] != 0.0 && !(sqrt(rn[v]) < tol * sqrt(nb[v]))) all_pass = false;
+        }
+        if (!finite) {
+            out.status = DIRAC_NONFINITE;
+            break;
+        }
+        if (it % every == 0 || all_pass || it >= maxit) {
+            out.recomputes++;
+            TRY(apply_A(op, x, q, m0, s));
+            TRY(blas_axpby(op, p, r, rhs, nullptr, 1.0, q, nullptr, -1.0, w.rr_new, s));
+            TRY(to_host(rrt, w.rr_new, nv, s));
+            bool stagnated = false;
+            nact = 0;
+            for (int v = 0; v < nv; ++v) {
+                out.relres[v] = nb[v] > 0 ? sqrt(rrt[v] / nb[v]) : 0.0;
+                if (act[v] == 0.0) continue;
+                if (sqrt(rrt[v]) < tol * sqrt(nb[v])) {
+                    act[v] = 0.0;
+                    out.status_rhs[v] = DIRAC_OK;
+                    continue;
+                }
+                const double disc = fabs(sqrt(rn[v]) - sqrt(rrt[v])) / fmax(sqrt(rrt[v]), 1e-300);
+                if (disc > 0.01) stagnated = true;
+                ++nact;
+            }
+            TRY(to_dev(w.act, act, nv, s));
+            if (nact == 0) break;
+            if (stagnated) {
+                out.status = DIRAC_STAGNATED;
+                for (int v = 0; v < nv; ++v)
+                    if (act[v] != 0.0) out.status_rhs[v] = DIRAC_STAGNATED;
+                break;
+            }
+            if (it >= maxit) {
+                out.status = DIRAC_NOT_CONVERGED;
+                break;
+            }
+        }
+        cg_beta_kernel<<<1, kNS, 0, s>>>(nv, w.rr_new, w.rr, w.act, w.beta);
+        TRY(blas_axpby(op, p, pv, r, nullptr, 1.0, pv, w.beta, 1.0, nullptr, s));
+    }
+    out.iters = it;
+    TRY(launch_check("cg coefficient kernels"));
+    return DIRAC_OK;
+}
+
+// BiCGstab on D x = b, x in/out.  Uses ws vectors 0..4.
+static int bicgstab_core(const dirac_op *op, const void *b, void *x, double m0, double tol, int maxit, int every,
+                         CoreOut &out, cudaStream_t s) {
+    Ws w;
+    TRY(get_ws(op, w));
+    const int nv = op->nv;
+    const dirac_prec p = op->prec;
+    void *r = w.v[0], *rh = w.v[1], *pv = w.v[2], *vv = w.v[3], *t = w.v[4];
+    double nb[kNS], rr[kNS], act[kNS], brk[kNS];
+    TRY(blas_norm2(op, p, b, w.nb, s));
+    TRY(to_host(nb, w.nb, nv, s));
+    TRY(op_apply(op, x, t, m0, +1, s));
+    TRY(blas_axpby(op, p, r, b, nullptr, 1.0, t, nullptr, -1.0, w.rr, s));
+    TRY(blas_axpby(op, p, rh, r, nullptr, 1.0, nullptr, nullptr, 0.0, nullptr, s));
+    TRY(cuda_check(cudaMemsetAsync(pv, 0, op->vec_bytes, s), "memset"));
+    TRY(cuda_check(cudaMemsetAsync(vv, 0, op->vec_bytes, s), "memset"));
+    TRY(to_host(rr, w.rr, nv, s));
+    double ones[2 * kNS];
+    for (int i = 0; i < 2 * kNS; ++i) ones[i] = (i & 1) ? 0.0 : 1.0;
+    TRY(to_dev(w.rho, ones, 2 * nv, s));
+    TRY(to_dev(w.alpha, ones, 2 * nv, s));
+    TRY(to_dev(w.omega, ones, 2 * nv, s));
+    int nact = 0;
+    for (int v = 0; v < nv; ++v) {
+        const bool conv = nb[v] == 0.0 || sqrt(rr[v]) < tol * sqrt(nb[v]);
+        act[v] = conv ? 0.0 : 1.0;
+        brk[v] = 0.0;
+        out.status_rhs[v] = conv ? DIRAC_OK : DIRAC_NOT_CONVERGED;
+        out.relres[v] = nb[v] > 0 ? sqrt(rr[v] / nb[v]) : 0.0;
+        nact += !conv;
+    }
+    TRY(to_dev(w.act, act, nv, s));
+    double *brk_d = w.c3;   // breakdown flags
+    TRY(to_dev(brk_d, brk, nv, s));
+    out.status = DIRAC_OK;
+    int it = 0;
+    while (nact > 0) {
+        ++it;
+        TRY(blas_dot(op, p, rh, r, w.rho_new, s));
+        bicg_beta_kernel<<<1, kNS, 0, s>>>(nv, w.rho_new, w.rho, w.alpha, w.omega, w.act, w.beta, w.c2, brk_d);
+        // p = r + beta p - beta omega v
+        TRY(blas_axpby(op, p, pv, pv, w.beta, 1.0, vv, w.c2, 1.0, nullptr, s));
+        TRY(blas_axpby(op, p, pv, pv, nullptr, 1.0, r, nullptr, 1.0, nullptr, s));
+        TRY(op_apply(op, pv, vv, m0, +1, s));
+        TRY(blas_dot(op, p, rh, vv, w.pq, s));
+        bicg_alpha_kernel<<<1, kNS, 0, s>>>(nv, w.rho_new, w.pq, w.act, w.alpha);
+        // s = r - alpha v (in r)
+        TRY(blas_axpby(op, p, r, r, nullptr, 1.0, vv, w.alpha, -1.0, nullptr, s));
+        TRY(op_apply(op, r, t, m0, +1, s));
+        TRY(blas_dot(op, p, t, r, w.c1, s));
+        TRY(blas_norm2(op, p, t, w.tt, s));
+        bicg_omega_kernel<<<1, kNS, 0, s>>>(nv, w.c1, w.tt, w.act, w.omega, w.rho_new, w.rho, brk_d, w.act);
+        // x += alpha p + omega s
+        TRY(blas_axpby(op, p, x, x, nullptr, 1.0, pv, w.alpha, 1.0, nullptr, s));
+        TRY(blas_axpby(op, p, x, x, nullptr, 1.0, r, w.omega, 1.0, nullptr, s));
+        // r = s - omega t
+        TRY(blas_axpby(op, p, r, r, nullptr, 1.0, t, w.omega, -1.0, w.rr_new, s));
+        double rn[kNS];
+        TRY(to_host(rn, w.rr_new, nv, s));
+        TRY(to_host(act, w.act, nv, s));   // breakdown may have frozen some
+        bool all_pass = true, finite = true;
+        for (int v = 0; v < nv; ++v) {
+            if (!isfinite(rn[v])) finite = false;
+            if (act[v] != 0.0 && !(sqrt(rn[v]) < tol * sqrt(nb[v]))) all_pass = false;
+        }
+        if (!finite) {
+            out.status = DIRAC_NONFINITE;
+            break;
+        }
+        nact = 0;
+        for (int v = 0; v < nv; ++v) nact += act[v] != 0.0;
+        if (it % every == 0 || all_pass || it >= maxit || nact == 0) {
+            out.recomputes++;
+            TRY(op_apply(op, x, t, m0, +1, s));
+            TRY(blas_axpby(op, p, r, b, nullptr, 1.0, t, nullptr, -1.0, w.rr_new, s));
+            double rrt[kNS];
+            TRY(to_host(rrt, w.rr_new, nv, s));
+            bool stagnated = false;
+            nact = 0;
+            for (int v = 0; v < nv; ++v) {
+                out.relres[v] = nb[v] > 0 ? sqrt(rrt[v] / nb[v]) : 0.0;
+                if (sqrt(rrt[v]) < tol * sqrt(nb[v])) {
+                    if (act[v] != 0.0 || out.status_rhs[v] != DIRAC_OK) out.status_rhs[v] = DIRAC_OK;
+                    act[v] = 0.0;
+                    continue;
+                }
+                if (act[v] == 0.0) continue;
+                const double disc = fabs(sqrt(rn[v]) - sqrt(rrt[v])) / fmax(sqrt(rrt[v]), 1e-300);
+                if (disc > 0.01) stagnated = true;
+                ++nact;
+            }
+            TRY(to_dev(w.act, act, nv, s));
+            if (nact == 0) break;
+            if (stagnated) {
+                out.status = DIRAC_STAGNATED;
+                break;
+            }
+            if (it >= maxit) {
+                out.status = DIRAC_NOT_CONVERGED;
+                break;
+            }
+        }
+    }
+    TRY(to_host(brk, brk_d, nv, s));
+    for (int v = 0; v < nv; ++v)
+        if (brk[v] != 0.0 && out.status_rhs[v] != DIRAC_OK) {
+            out.status_rhs[v] = DIRAC_BREAKDOWN;
+            if (out.status == DIRAC_OK) out.status = DIRAC_BREAKDOWN;
+        }
+    for (int v = 0; v < nv; ++v)
+        if (out.status_rhs[v] == DIRAC_NOT_CONVERGED && out.status != DIRAC_OK) out.status_rhs[v] = out.status;
+    out.iters = it;
+    TRY(launch_check("bicgstab coefficient kernels"));
+    return DIRAC_OK;
+}
+
+static double default_inner_tol(dirac_prec p) {
+    switch (p) {
+    case DIRAC_F32: return 1e-5;
+    case DIRAC_F16: return 2e-3;
+    case DIRAC_BF16: return 1e-2;
+    default: return 1e-10;
+    }
+}
+
+// Defect correction: outer in op precision, inner Krylov solve in inner_prec.
+static int mixed_solve(const dirac_op *op, const void *b, void *x, double m0, const dirac_solve_params *prm,
+                       dirac_solve_stats *st, cudaStream_t s) {
+    dirac_op *lo = nullptr;
+    TRY(op_inner(op, prm->inner_prec, &lo, s));
+    Ws wh, wl;
+    TRY(get_ws(op, wh));
+    TRY(get_ws(lo, wl));
+    const int nv = op->nv;
+    const dirac_prec ph = op->prec, pl = lo->prec;
+    const bool cg = prm->solver == DIRAC_CG_NORMAL;
+    void *rhs = wh.v[5], *r = wh.v[6], *tmp = wh.v[7];
+    void *rl = wl.v[5], *el = wl.v[6];
+    // rhs = D^dag b (CG on normal equations) or b
+    if (cg) TRY(op_apply(op, b, rhs, m0, -1, s));
+    else TRY(blas_axpby(op, ph, rhs, b, nullptr, 1.0, nullptr, nullptr, 0.0, nullptr, s));
+    double nb[kNS], rr[kNS], act[kNS];
+    TRY(blas_norm2(op, ph, rhs, wh.nb, s));
+    TRY(to_host(nb, wh.nb, nv, s));
+    const double itol = prm->inner_tol > 0 ? prm->inner_tol : default_inner_tol(pl);
+    const int every = prm->recompute_every > 0 ? prm->recompute_every : (pl == DIRAC_F64 ? 50 : 20);
+    int total = 0, outer = 0;
+    st->status = DIRAC_NOT_CONVERGED;
+    for (;;) {
+        // r = rhs - A x (operator precision)
+        if (cg) TRY(op_apply_normal(op, x, tmp, m0, s));
+        else TRY(op_apply(op, x, tmp, m0, +1, s));
+        TRY(blas_axpby(op, ph, r, rhs, nullptr, 1.0, tmp, nullptr, -1.0, wh.rr, s));
+        TRY(to_host(rr, wh.rr, nv, s));
+        st->recomputes++;
+        int nact = 0;
+        bool finite = true;
+        for (int v = 0; v < nv; ++v) {
+            if (!isfinite(rr[v])) finite = false;
+            st->relres[v] = nb[v] > 0 ? sqrt(rr[v] / nb[v]) : 0.0;
+            const bool conv = nb[v] == 0.0 || sqrt(rr[v]) < prm->tol * sqrt(nb[v]);
+            act[v] = conv ? 0.0 : 1.0;
+            st->status_per_rhs[v] = conv ? DIRAC_OK : DIRAC_NOT_CONVERGED;
+            nact += !conv;
+        }
+        if (!finite) {
+            st->status = DIRAC_NONFINITE;
+            break;
+        }
+        if (nact == 0) {
+            st->status = DIRAC_OK;
+            break;
+        }
+        if (total >= prm->maxit) break;
+        TRY(to_dev(wh.act, act, nv, s));
+        // inner right-hand side r / |r| in low precision
+        coef_from_norm_kernel<<<1, kNS, 0, s>>>(nv, wh.rr, wh.act, wh.c1, 1);
+        TRY(blas_axpby(op, ph, tmp, r, wh.c1, 1.0, nullptr, nullptr, 0.0, nullptr, s));
+        TRY(blas_convert(op, tmp, ph, rl, pl, s));
+        TRY(cuda_check(cudaMemsetAsync(el, 0, lo->vec_bytes, s), "memset"));
+        CoreOut co;
+        const int budget = prm->maxit - total;
+        if (cg) TRY(cg_core(lo, rl, el, m0, itol, budget, every, co, s));
+        else TRY(bicgstab_core(lo, rl, el, m0, itol, budget, every, co, s));
+        total += co.iters;
+        st->recomputes += co.recomputes;
+        // x += |r| e
+        TRY(blas_convert(op, el, pl, tmp, ph, s));
+        coef_from_norm_kernel<<<1, kNS, 0, s>>>(nv, wh.rr, wh.act, wh.c1, 0);
+        TRY(blas_axpby(op, ph, x, x, nullptr, 1.0, tmp, wh.c1, 1.0, nullptr, s));
+        ++outer;
+        if (co.iters == 0) break;   // inner solver made no progress
+    }
+    st->iters = total;
+    st->outer_iters = outer;
+    return DIRAC_OK;
+}
+
+static int plain_solve(const dirac_op *op, const void *b, void *x, double m0, const dirac_solve_params *prm,
+                       dirac_solve_stats *st, cudaStream_t s) {
+    Ws w;
+    TRY(get_ws(op, w));
+    const int every = prm->recompute_every > 0 ? prm->recompute_every : (op->prec == DIRAC_F64 ? 50 : 20);
+    CoreOut co;
+    if (prm->solver == DIRAC_CG_NORMAL) {
+        void *rhs = w.v[5];
+        TRY(op_apply(op, b, rhs, m0, -1, s));
+        TRY(cg_core(op, rhs, x, m0, prm->tol, prm->maxit, every, co, s));
+    } else {
+        TRY(bicgstab_core(op, b, x, m0, prm->tol, prm->maxit, every, co, s));
+    }
+    st->iters = co.iters;
+    st->outer_iters = 0;
+    st->recomputes = co.recomputes;
+    st->status = co.status;
+    for (int v = 0; v < op->nv; ++v) {
+        st->status_per_rhs[v] = co.status_rhs[v];
+        st->relres[v] = co.relres[v];
+    }
+    bool all = true;
+    for (int v = 0; v < op->nv; ++v) all &= co.status_rhs[v] == DIRAC_OK;
+    if (all) st->status = DIRAC_OK;
+    else if (st->status == DIRAC_OK) st->status = DIRAC_NOT_CONVERGED;
+    return DIRAC_OK;
+}
+
+int solve(const dirac_op *op, const void *b, void *x, double m0, const dirac_solve_params *prm,
+          dirac_solve_stats *st_user, cudaStream_t s) {
+    auto t0 = std::chrono::steady_clock::now();
+    dirac_solve_stats st;
+    memset(&st, 0, sizeof(st));
+    int rc;
+    if (prm->inner_prec == op->prec) rc = plain_solve(op, b, x, m0, prm, &st, s);
+    else rc = mixed_solve(op, b, x, m0, prm, &st, s);
+    if (rc) return rc;
+    // true residual ||b - D x|| / ||b|| in the operator precision
+    Ws w;
+    TRY(get_ws(op, w));
+    TRY(op_apply(op, x, w.v[7], m0, +1, s));
+    TRY(blas_axpby(op, op->prec, w.v[6], b, nullptr, 1.0, w.v[7], nullptr, -1.0, w.rr, s));
+    TRY(blas_norm2(op, op->prec, b, w.nb, s));
+    double rr[kNS], nb[kNS];
+    TRY(to_host(rr, w.rr, op->nv, s));
+    TRY(to_host(nb, w.nb, op->nv, s));
+    for (int v = 0; v < op->nv; ++v) st.true_relres[v] = nb[v] > 0 ? sqrt(rr[v] / nb[v]) : 0.0;
+    st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (st_user) *st_user = st;
+    return st.status;
+}
+
+}  // namespace dgb
+
+extern "C" int dirac_solve(const dirac_op *op, const void *b, void *x, double m0, const dirac_solve_params *params,
+                           dirac_solve_stats *stats, void *stream) {
+    if (!op || !params || !b || !x) return DIRAC_ERR_INVALID_ARG;
+    if (((uintptr_t)b & 15) || ((uintptr_t)x & 15)) return DIRAC_ERR_ALIGNMENT;
+    if (params->solver != DIRAC_CG_NORMAL && params->solver != DIRAC_BICGSTAB) return DIRAC_ERR_INVALID_ARG;
+    if (params->inner_prec < DIRAC_F64 || params->inner_prec > DIRAC_F16) return DIRAC_ERR_UNSUPPORTED_PREC;
+    if (!(params->tol > 0) || params->maxit < 1) return DIRAC_ERR_INVALID_ARG;
+    return dgb::solve(op, b, x, m0, params, stats, (cudaStream_t)stream);
+}

@@ -1,0 +1,103 @@
+// staggered.cu -- multi-RHS Susskind (staggered) Dirac operator, Eq. (def_stag):
+//   (D_S phi)(n) = m0 phi(n) + 1/2 sum_mu eta_mu(n) [U_mu(n) phi(n+mu) - U_mu(n-mu)^dag phi(n-mu)]
+// with eta_1 = 1, eta_2 = (-1)^x, eta_3 = (-1)^(x+y), eta_4 = (-1)^(x+y+z) in
+// the paper's 1-based coordinates (App. D starts the toggles at x = 1, which
+// makes eta_2 = -1 there); with the 0-based coordinates used here the
+// exponent is sum_{nu<mu} (x_nu + 1).  D_S^dag = epsilon D_S epsilon flips the
+// sign of the anti-hermitian hopping term (sgn = -1).
+//
+// Thread <-> (site, VR consecutive right-hand sides), colour-vector
+// accumulator in registers, one write per output element.
+#include "internal.h"
+
+namespace dgb {
+
+template <int NC, int VR, bool DAG, typename E, typename A>
+__device__ __forceinline__ void stag_hop(cx<A> (&acc)[NC][VR], const E *__restrict__ link,
+                                         const E *__restrict__ phi, int nv, A f) {
+    cx<A> L[NC][NC];
+    load_mat<NC, E, A>(link, L);
+    cx<A> p[NC][VR];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) load_cx<E, VR, A>(phi + 2 * (long long)c * nv, p[c]);
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int v = 0; v < VR; ++v) {
+            cx<A> t = {0, 0};
+#pragma unroll
+            for (int k = 0; k < NC; ++k) {
+                if constexpr (DAG) cmac_conj(t, L[k][c], p[k][v]);
+                else cmac(t, L[c][k], p[k][v]);
+            }
+            rmac(acc[c][v], f, t);
+        }
+}
+
+template <int NC, int VR, typename E>
+__global__ void __launch_bounds__(128) staggered_kernel(const E *__restrict__ U, const E *__restrict__ in,
+                                                        E *__restrict__ out, Lat g, typename Acc<E>::T mass,
+                                                        typename Acc<E>::T half_sgn) {
+    using A = typename Acc<E>::T;
+    const int nchunk = g.nv / VR;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= g.V * nchunk) return;
+    const long long n = tid / nchunk;
+    const int j = (int)(tid - n * nchunk);
+    const Coord c = site_coords(g, n);
+    const long long site_cx = (long long)NC * g.nv;
+
+    cx<A> acc[NC][VR];
+#pragma unroll
+    for (int a = 0; a < NC; ++a)
+#pragma unroll
+        for (int v = 0; v < VR; ++v) acc[a][v] = cx<A>{0, 0};
+
+    // eta exponents sum_{nu<mu} (x_nu + 1)
+    const int e[4] = {0, c.x + 1, c.x + c.y + 2, c.x + c.y + c.z + 3};
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        const A eta = (e[mu] & 1) ? (A)-1 : (A)1;
+        const long long fw = neighbour(g, n, c, mu, +1);
+        const long long bw = neighbour(g, n, c, mu, -1);
+        stag_hop<NC, VR, false>(acc, U + 2 * ((n * 4 + mu) * NC * NC), in + 2 * (fw * site_cx + (long long)j * VR),
+                                g.nv, eta);
+        stag_hop<NC, VR, true>(acc, U + 2 * ((bw * 4 + mu) * NC * NC), in + 2 * (bw * site_cx + (long long)j * VR),
+                               g.nv, -eta);
+    }
+
+    const long long base = 2 * (n * site_cx + (long long)j * VR);
+#pragma unroll
+    for (int a = 0; a < NC; ++a) {
+        cx<A> p[VR], o[VR];
+        const long long off = base + 2LL * a * g.nv;
+        load_cx<E, VR, A>(in + off, p);
+#pragma unroll
+        for (int v = 0; v < VR; ++v) {
+            o[v] = mass * p[v];
+            rmac(o[v], half_sgn, acc[a][v]);
+        }
+        store_cx<E, VR, A>(out + off, o);
+    }
+}
+
+int launch_staggered(const dirac_op *op, const void *in, void *out, double m0, int sgn, cudaStream_t s) {
+    const int vr = pick_vr(op->prec, op->nv);
+    return dispatch_prec(op->prec, [&](auto tag) {
+        using E = std::remove_pointer_t<decltype(tag)>;
+        using A = typename Acc<E>::T;
+        return dispatch_nc(op->nc, [&](auto ncc) {
+            constexpr int NC = decltype(ncc)::value;
+            return dispatch_vr(vr, [&](auto vrc) {
+                constexpr int VR = decltype(vrc)::value;
+                const long long threads = op->V * (op->nv / VR);
+                const int block = 128;
+                staggered_kernel<NC, VR, E><<<grid_for(threads, block), block, 0, s>>>(
+                    (const E *)op->links, (const E *)in, (E *)out, op->lat, (A)m0, (A)(0.5 * sgn));
+                return launch_check("staggered_kernel");
+            });
+        });
+    });
+}
+
+}  // namespace dgb

@@ -1,0 +1,281 @@
+"""Thin ctypes binding of ``include/dirac.h`` (libdirac.so).
+
+Argument marshalling only: torch tensors supply device memory and the CUDA
+stream; every step of every operation runs in the library's CUDA kernels.
+There is no fallback: if libdirac.so is missing or no GPU is present the
+calls raise.
+
+Vector tensors (device, C-contiguous):
+  F64  complex128  Wilson-type (Nt, Nz, Ny, Nx, Nc, 4, Nv), staggered (Nt, Nz, Ny, Nx, Nc, Nv)
+  F32  complex64   same shapes
+  BF16 bfloat16    same shapes + trailing (re, im) axis of length 2
+  F16  float16     same shapes + trailing (re, im) axis of length 2
+Gauge field U: complex128 or complex64, (Nt, Nz, Ny, Nx, 4, Nc, Nc), no boundary phases.
+"""
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+WILSON, BRILLOUIN, STAGGERED = 0, 1, 2
+F64, F32, BF16, F16 = 0, 1, 2, 3
+CG_NORMAL, BICGSTAB = 0, 1
+PREC_NAMES = {F64: "f64", F32: "f32", BF16: "bf16", F16: "f16"}
+KIND_NAMES = {WILSON: "wilson", BRILLOUIN: "brillouin", STAGGERED: "staggered"}
+_TORCH_DTYPE = {F64: torch.complex128, F32: torch.complex64, BF16: torch.bfloat16, F16: torch.float16}
+
+
+class Geom(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int * 4), ("nc", ctypes.c_int), ("nv", ctypes.c_int),
+                ("bc", ctypes.c_int * 4), ("prec", ctypes.c_int)]
+
+
+class SolveParams(ctypes.Structure):
+    _fields_ = [("solver", ctypes.c_int), ("tol", ctypes.c_double), ("maxit", ctypes.c_int),
+                ("inner_prec", ctypes.c_int), ("inner_tol", ctypes.c_double), ("recompute_every", ctypes.c_int)]
+
+
+class SolveStats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("outer_iters", ctypes.c_int), ("recomputes", ctypes.c_int),
+                ("status", ctypes.c_int), ("status_per_rhs", ctypes.c_int * 64), ("relres", ctypes.c_double * 64),
+                ("true_relres", ctypes.c_double * 64), ("seconds", ctypes.c_double)]
+
+
+class DiracError(RuntimeError):
+    def __init__(self, code, what):
+        super().__init__("%s: %s (code %d)" % (what, error_string(code), code))
+        self.code = code
+
+
+_lib = None
+
+# every symbol include/dirac.h declares, with its ctypes signature
+_P, _I, _D, _SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+SIGNATURES = {
+    "dirac_op_create": (_I, [_I, ctypes.POINTER(Geom), _P, _I, _P, ctypes.POINTER(_P)]),
+    "dirac_op_update_links": (_I, [_P, _P, _I, _P]),
+    "dirac_op_copy_w": (_I, [_P, _P, _P]),
+    "dirac_op_destroy": (None, [_P]),
+    "dirac_apply": (_I, [_P, _P, _P, _D, _P]),
+    "dirac_apply_dagger": (_I, [_P, _P, _P, _D, _P]),
+    "dirac_apply_normal": (_I, [_P, _P, _P, _D, _P]),
+    "dirac_apply_host": (_I, [_P, _P, _P, _D, _I, _P]),
+    "dirac_vec_bytes": (_SZ, [_P]),
+    "dirac_vec_norm2": (_I, [_P, _P, _P, _P]),
+    "dirac_vec_dot": (_I, [_P, _P, _P, _P, _P]),
+    "dirac_vec_axpy": (_I, [_P, _P, _P, _P, _P]),
+    "dirac_vec_gamma5": (_I, [_P, _P, _P]),
+    "dirac_vec_convert": (_I, [_P, _P, _I, _P, _I, _P]),
+    "dirac_solve": (_I, [_P, _P, _P, _D, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats), _P]),
+    "dirac_error_string": (ctypes.c_char_p, [_I]),
+    "dirac_flops_per_site": (ctypes.c_long, [_I, _I]),
+    "dirac_version": (_I, []),
+}
+
+
+def lib_path():
+    return _build.LIB
+
+
+def lib():
+    """Load libdirac.so (built by ``__graft_entry__.build()``); raise if absent."""
+    global _lib
+    if _lib is None:
+        path = lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError("libdirac.so not found at %s: build it with __graft_entry__.build()" % path)
+        L = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def error_string(code):
+    return lib().dirac_error_string(int(code)).decode()
+
+
+def flops_per_site(kind, nc):
+    return int(lib().dirac_flops_per_site(int(kind), int(nc)))
+
+
+def _check(rc, what):
+    if rc < 0:
+        raise DiracError(rc, what)
+    return rc
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class DiracOp:
+    """One of D_W, D_B, D_S on a fixed gauge field, for N_v right-hand sides."""
+
+    def __init__(self, kind, U, nv, bc=(1, 1, 1, 1), prec=F32, stream=None):
+        if not U.is_cuda:
+            raise ValueError("U must be a CUDA tensor")
+        if U.dtype not in (torch.complex128, torch.complex64):
+            raise ValueError("U must be complex128 or complex64")
+        U = U.contiguous()
+        nt, nz, ny, nx = U.shape[:4]
+        self.kind, self.nv, self.prec = int(kind), int(nv), int(prec)
+        self.dims = (nx, ny, nz, nt)
+        self.nc = U.shape[-1]
+        self.bc = tuple(int(b) for b in bc)
+        self.device = U.device
+        g = Geom()
+        g.dims[:] = self.dims
+        g.nc, g.nv, g.prec = self.nc, self.nv, self.prec
+        g.bc[:] = self.bc
+        self._geom = g
+        h = ctypes.c_void_p()
+        u_prec = F64 if U.dtype == torch.complex128 else F32
+        _check(lib().dirac_op_create(self.kind, ctypes.byref(g), _ptr(U), u_prec, _stream(stream),
+                                     ctypes.byref(h)), "dirac_op_create")
+        self._h = h
+
+    # ------------------------------------------------------------ lifecycle
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value and _lib is not None:
+            _lib.dirac_op_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def update_links(self, U, stream=None):
+        u_prec = F64 if U.dtype == torch.complex128 else F32
+        _check(lib().dirac_op_update_links(self._h, _ptr(U.contiguous()), u_prec, _stream(stream)),
+               "dirac_op_update_links")
+
+    # ---------------------------------------------------------------- shapes
+    @property
+    def staggered(self):
+        return self.kind == STAGGERED
+
+    def vector_shape(self, prec=None):
+        prec = self.prec if prec is None else prec
+        nx, ny, nz, nt = self.dims
+        inner = (self.nc, self.nv) if self.staggered else (self.nc, 4, self.nv)
+        shape = (nt, nz, ny, nx) + inner
+        return shape + (2,) if prec in (BF16, F16) else shape
+
+    def new_vector(self, prec=None, zero=True):
+        prec = self.prec if prec is None else prec
+        f = torch.zeros if zero else torch.empty
+        return f(self.vector_shape(prec), dtype=_TORCH_DTYPE[prec], device=self.device)
+
+    def to_prec(self, v, prec=None):
+        """Torch-side representation change of a complex tensor into the vector
+        format of ``prec`` (no arithmetic beyond the storage rounding)."""
+        prec = self.prec if prec is None else prec
+        if prec in (BF16, F16):
+            return torch.view_as_real(v.to(torch.complex64)).to(_TORCH_DTYPE[prec]).contiguous()
+        return v.to(_TORCH_DTYPE[prec]).contiguous()
+
+    def to_complex(self, v):
+        if v.dtype in (torch.bfloat16, torch.float16):
+            return torch.view_as_complex(v.float().contiguous())
+        return v
+
+    def vec_bytes(self):
+        return int(lib().dirac_vec_bytes(self._h))
+
+    def _vec(self, v, what):
+        if tuple(v.shape) != self.vector_shape() or v.dtype != _TORCH_DTYPE[self.prec] or not v.is_contiguous():
+            raise ValueError("%s: expected contiguous %s %s, got %s %s" % (
+                what, tuple(self.vector_shape()), _TORCH_DTYPE[self.prec], tuple(v.shape), v.dtype))
+        return _ptr(v)
+
+    # ---------------------------------------------------------------- apply
+    def apply(self, psi, out=None, m0=0.0, dagger=False, stream=None):
+        out = self.new_vector(zero=False) if out is None else out
+        f = lib().dirac_apply_dagger if dagger else lib().dirac_apply
+        _check(f(self._h, self._vec(psi, "psi"), self._vec(out, "out"), float(m0), _stream(stream)), "dirac_apply")
+        return out
+
+    def apply_normal(self, psi, out=None, m0=0.0, stream=None):
+        out = self.new_vector(zero=False) if out is None else out
+        _check(lib().dirac_apply_normal(self._h, self._vec(psi, "psi"), self._vec(out, "out"), float(m0),
+                                        _stream(stream)), "dirac_apply_normal")
+        return out
+
+    def apply_host(self, host_in, host_out, m0=0.0, dagger=False, stream=None):
+        """End-to-end apply on host (CPU, ideally pinned) tensors; blocks."""
+        if host_in.is_cuda or host_out.is_cuda:
+            raise ValueError("apply_host takes host tensors")
+        nb = self.vec_bytes()
+        if host_in.numel() * host_in.element_size() != nb or host_out.numel() * host_out.element_size() != nb:
+            raise ValueError("host buffers must hold exactly one vector")
+        _check(lib().dirac_apply_host(self._h, _ptr(host_in), _ptr(host_out), float(m0), int(bool(dagger)),
+                                      _stream(stream)), "dirac_apply_host")
+        return host_out
+
+    def copy_w(self, stream=None):
+        """The 80 stored W links (Brillouin): (Nt, Nz, Ny, Nx, 80, Nc, Nc[, 2])."""
+        nx, ny, nz, nt = self.dims
+        shape = (nt, nz, ny, nx, 80, self.nc, self.nc)
+        if self.prec in (BF16, F16):
+            shape = shape + (2,)
+        w = torch.empty(shape, dtype=_TORCH_DTYPE[self.prec], device=self.device)
+        _check(lib().dirac_op_copy_w(self._h, _ptr(w), _stream(stream)), "dirac_op_copy_w")
+        return w
+
+    # ---------------------------------------------------------------- BLAS-1
+    def norm2(self, v, stream=None):
+        out = torch.empty(self.nv, dtype=torch.float64, device=self.device)
+        _check(lib().dirac_vec_norm2(self._h, self._vec(v, "v"), _ptr(out), _stream(stream)), "dirac_vec_norm2")
+        return out
+
+    def dot(self, u, v, stream=None):
+        out = torch.empty(self.nv, dtype=torch.complex128, device=self.device)
+        _check(lib().dirac_vec_dot(self._h, self._vec(u, "u"), self._vec(v, "v"), _ptr(out), _stream(stream)),
+               "dirac_vec_dot")
+        return out
+
+    def axpy(self, alpha, x, y, stream=None):
+        a = alpha.to(device=self.device, dtype=torch.complex128).contiguous()
+        _check(lib().dirac_vec_axpy(self._h, _ptr(a), self._vec(x, "x"), self._vec(y, "y"), _stream(stream)),
+               "dirac_vec_axpy")
+        return y
+
+    def gamma5_(self, v, stream=None):
+        _check(lib().dirac_vec_gamma5(self._h, self._vec(v, "v"), _stream(stream)), "dirac_vec_gamma5")
+        return v
+
+    def convert(self, src, src_prec, dst_prec, stream=None):
+        dst = self.new_vector(prec=dst_prec, zero=False)
+        _check(lib().dirac_vec_convert(self._h, _ptr(src.contiguous()), int(src_prec), _ptr(dst), int(dst_prec),
+                                       _stream(stream)), "dirac_vec_convert")
+        return dst
+
+    # ---------------------------------------------------------------- solve
+    def solve(self, b, x=None, m0=0.0, solver=CG_NORMAL, tol=1e-10, maxit=10000, inner_prec=None,
+              inner_tol=0.0, recompute_every=0, stream=None):
+        """Solve D x = b (BiCGstab) or D^dag D x = D^dag b (CG) for all RHS.
+        Returns (x, stats dict).  Non-convergence is reported in the stats."""
+        x = self.new_vector() if x is None else x
+        p = SolveParams(int(solver), float(tol), int(maxit), int(self.prec if inner_prec is None else inner_prec),
+                        float(inner_tol), int(recompute_every))
+        st = SolveStats()
+        rc = _check(lib().dirac_solve(self._h, self._vec(b, "b"), self._vec(x, "x"), float(m0), ctypes.byref(p),
+                                      ctypes.byref(st), _stream(stream)), "dirac_solve")
+        nv = self.nv
+        stats = dict(code=rc, status=st.status, iters=st.iters, outer_iters=st.outer_iters,
+                     recomputes=st.recomputes, status_per_rhs=list(st.status_per_rhs[:nv]),
+                     relres=list(st.relres[:nv]), true_relres=list(st.true_relres[:nv]), seconds=st.seconds)
+        return x, stats

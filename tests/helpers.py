@@ -1,0 +1,37 @@
+"""Shared helpers for the GPU parity tests: move seeded numpy inputs to the
+device in the library's formats and compare with the oracle."""
+import numpy as np
+import torch
+
+from paper_2112_14640_gb300 import dirac as D
+
+TOL = {D.F64: 1e-12, D.F32: 1e-5, D.BF16: 1e-2, D.F16: 1e-2}
+
+
+def rel_l2(got, want):
+    got = np.asarray(got)
+    want = np.asarray(want)
+    return float(np.linalg.norm((got - want).ravel()) / max(np.linalg.norm(want.ravel()), 1e-300))
+
+
+def to_device(op, v_np, prec=None):
+    """numpy complex128 vector -> device tensor in the op's (or given) precision."""
+    t = torch.from_numpy(np.ascontiguousarray(v_np)).to(op.device)
+    return op.to_prec(t, op.prec if prec is None else prec)
+
+
+def to_numpy(op, v):
+    return op.to_complex(v).to(torch.complex128).cpu().numpy()
+
+
+def rounded(v_np, prec):
+    """The storage rounding of a complex128 array in precision prec (so the
+    oracle sees exactly the input the kernel reads)."""
+    t = torch.from_numpy(np.ascontiguousarray(v_np))
+    if prec == D.F64:
+        return v_np
+    if prec == D.F32:
+        return t.to(torch.complex64).to(torch.complex128).numpy()
+    dt = torch.bfloat16 if prec == D.BF16 else torch.float16
+    r = torch.view_as_real(t).to(dt).to(torch.float64)
+    return torch.view_as_complex(r.contiguous()).numpy()

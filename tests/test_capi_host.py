@@ -1,0 +1,86 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds and
+loads, exports every function include/dirac.h declares, and its argument
+validation and pure host helpers behave as documented."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2112_14640_gb300 import build as B
+from paper_2112_14640_gb300 import dirac as D
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return D.lib()
+
+
+def declared_functions():
+    text = open(os.path.join(ROOT, "include", "dirac.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = set(re.findall(r"\b(dirac_[a-z0-9_]+)\s*\(", text))
+    return sorted(names)
+
+
+def test_header_declares_functions():
+    names = declared_functions()
+    assert "dirac_apply" in names and "dirac_solve" in names and len(names) >= 15
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert name in D.SIGNATURES, "binding lacks a signature for %s" % name
+
+
+def test_flop_counts_match_app_e(lib):
+    assert D.flops_per_site(D.WILSON, 3) == 1368
+    assert D.flops_per_site(D.BRILLOUIN, 3) == 30168
+    assert D.flops_per_site(D.STAGGERED, 3) == 582
+    assert D.flops_per_site(7, 3) == -1
+
+
+def test_error_strings(lib):
+    assert D.error_string(0) == "success"
+    assert "aligned" in D.error_string(-4)
+    assert "1%" in D.error_string(2)
+    assert D.error_string(12345) == "unknown code"
+
+
+def test_create_validates_before_touching_the_device(lib):
+    """Invalid geometry is rejected before any CUDA call, so this runs without a GPU."""
+    out = ctypes.c_void_p()
+
+    def create(kind, dims, nc, nv, bc=(1, 1, 1, 1), prec=D.F32, U=1 << 20, u_prec=D.F64):
+        g = D.Geom()
+        g.dims[:] = dims
+        g.nc, g.nv, g.prec = nc, nv, prec
+        g.bc[:] = bc
+        return lib.dirac_op_create(kind, ctypes.byref(g), ctypes.c_void_p(U), u_prec, None, ctypes.byref(out))
+
+    assert create(D.WILSON, (4, 4, 4, 1), 3, 4) == -1          # extent < 2
+    assert create(D.STAGGERED, (4, 4, 3, 4), 3, 4) == -1       # odd extent for staggered
+    assert create(D.WILSON, (4, 4, 4, 4), 5, 4) == -2          # N_c not compiled
+    assert create(D.WILSON, (4, 4, 4, 4), 3, 0) == -1          # N_v = 0
+    assert create(D.WILSON, (4, 4, 4, 4), 3, 65) == -1         # N_v > 64
+    assert create(D.WILSON, (4, 4, 4, 4), 3, 4, bc=(1, 1, 1, 2)) == -1
+    assert create(D.WILSON, (4, 4, 4, 4), 3, 4, prec=9) == -3
+    assert create(D.WILSON, (4, 4, 4, 4), 3, 4, U=0) == -1     # null gauge field
+    assert create(D.WILSON, (4, 4, 4, 4), 3, 4, u_prec=D.BF16) == -3
+    assert create(9, (4, 4, 4, 4), 3, 4) == -1
+    assert lib.dirac_op_create(0, None, None, 0, None, ctypes.byref(out)) == -1
+    assert out.value is None
+
+
+def test_null_handles_are_rejected(lib):
+    p = ctypes.c_void_p(1 << 20)
+    assert lib.dirac_apply(None, p, p, 0.0, None) == -1
+    assert lib.dirac_apply_normal(None, p, p, 0.0, None) == -1
+    assert lib.dirac_vec_norm2(None, p, p, None) == -1
+    assert lib.dirac_solve(None, p, p, 0.0, None, None, None) == -1
+    assert lib.dirac_vec_bytes(None) == 0
+    lib.dirac_op_destroy(None)

@@ -1,0 +1,187 @@
+"""GPU parity: every stencil, its dagger and D^dag D, the W-link builder and
+the BLAS-1 reductions, through the C ABI, element by element against the FP64
+oracle on the same seeded inputs.
+
+Tolerances (relative L2 over the whole output): 1e-12 FP64, 1e-5 FP32,
+1e-2 BF16/FP16 storage (FP32 arithmetic).  Small lattices span many thread
+blocks and ragged tails (odd extents, odd N_v); the full 16^3x32, N_v = 12
+workload is checked on sampled output sites.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from helpers import TOL, rel_l2, to_device, to_numpy
+from paper_2112_14640_gb300 import dirac as D
+from paper_2112_14640_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+KINDS = [D.WILSON, D.BRILLOUIN, D.STAGGERED]
+
+
+def make(kind, dims, nc, nv, bc, prec, eps=0.4, seed=5, u_f32=False):
+    U = I.gauge_field(dims, nc, eps, seed)
+    Ut = torch.from_numpy(U).cuda()
+    if u_f32:
+        Ut = Ut.to(torch.complex64)
+    op = D.DiracOp(kind, Ut, nv, bc, prec)
+    ref = O.Operator(kind, U.astype(np.complex64).astype(np.complex128) if u_f32 else U, bc)
+    src = I.source(dims, nc, nv, seed + 1, staggered=(kind == D.STAGGERED))
+    return op, ref, src
+
+
+CASES = [
+    # dims, nc, nv, bc
+    ((4, 4, 4, 4), 3, 1, (1, 1, 1, -1)),
+    ((8, 8, 8, 8), 3, 12, (1, 1, 1, -1)),
+    ((6, 4, 2, 8), 3, 3, (1, -1, 1, -1)),
+    ((4, 6, 4, 2), 2, 4, (1, 1, 1, 1)),
+    ((2, 4, 4, 6), 4, 5, (-1, 1, 1, -1)),
+    ((4, 4, 2, 4), 1, 8, (1, 1, 1, -1)),
+]
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("prec", [D.F64, D.F32])
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_apply_and_dagger(kind, prec, case):
+    dims, nc, nv, bc = CASES[case]
+    m0 = 0.1 if kind != D.STAGGERED else 0.05
+    op, ref, src = make(kind, dims, nc, nv, bc, prec)
+    x = to_device(op, src)
+    for dag in (False, True):
+        got = to_numpy(op, op.apply(x, m0=m0, dagger=dag))
+        want = ref.apply_dagger(src, m0) if dag else ref.apply(src, m0)
+        err = rel_l2(got, want)
+        assert err <= TOL[prec], (kind, prec, dims, nc, nv, dag, err)
+    got = to_numpy(op, op.apply_normal(x, m0=m0))
+    assert rel_l2(got, ref.apply_normal(src, m0)) <= TOL[prec]
+    op.close()
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("prec", [D.BF16, D.F16])
+def test_apply_low_precision_storage(kind, prec):
+    dims, nc, nv, bc = (8, 4, 4, 8), 3, 12, (1, 1, 1, -1)
+    m0 = 0.1
+    op, ref, src = make(kind, dims, nc, nv, bc, prec)
+    x = to_device(op, src)
+    for dag in (False, True):
+        got = to_numpy(op, op.apply(x, m0=m0, dagger=dag))
+        want = ref.apply_dagger(src, m0) if dag else ref.apply(src, m0)
+        assert rel_l2(got, want) <= TOL[prec]
+    op.close()
+
+
+def test_f32_links_from_f32_gauge_field():
+    """U handed over in FP32 (the paper keeps links in sp, Sec. 2)."""
+    dims = (4, 4, 4, 8)
+    for kind in KINDS:
+        op, ref, src = make(kind, dims, 3, 4, (1, 1, 1, -1), D.F64, u_f32=True)
+        got = to_numpy(op, op.apply(to_device(op, src), m0=0.2))
+        assert rel_l2(got, ref.apply(src, 0.2)) <= 1e-12
+        op.close()
+
+
+@pytest.mark.parametrize("prec", [D.F64, D.F32])
+def test_w_links_match_path_enumeration(prec):
+    dims, nc, bc = (4, 6, 2, 4), 3, (1, -1, 1, -1)
+    op, ref, _ = make(D.BRILLOUIN, dims, nc, 2, bc, prec)
+    w = op.copy_w()
+    w = torch.view_as_complex(w.contiguous()) if w.dtype in (torch.bfloat16, torch.float16) else w
+    got = w.to(torch.complex128).cpu().numpy()
+    want = np.delete(ref.W, 40, axis=4)
+    assert rel_l2(got, want) <= (1e-13 if prec == D.F64 else 1e-6)
+    op.close()
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_full_size_sampled_sites(kind):
+    """16^3 x 32, N_c = 3, N_v = 12, FP32: the benchmark configuration, in the
+    launch configuration the benchmark times, checked on 64 sampled sites."""
+    dims, nc, nv, bc = (16, 16, 16, 32), 3, 12, (1, 1, 1, -1)
+    m0 = 0.05 if kind == D.STAGGERED else 0.1
+    op, ref, src = make(kind, dims, nc, nv, bc, D.F32, seed=2024)
+    x = to_device(op, src)
+    rng = np.random.default_rng(0)
+    V = int(np.prod(dims))
+    sites = np.concatenate([[0, V - 1, dims[0] - 1, V - dims[0]], rng.choice(V, 60, replace=False)])
+    for dag in (False, True):
+        got = to_numpy(op, op.apply(x, m0=m0, dagger=dag)).reshape((V,) + src.shape[4:])[sites]
+        want = ref.apply_sites(src, sites, m0, dagger=dag)
+        assert rel_l2(got, want) <= TOL[D.F32], (kind, dag)
+    op.close()
+
+
+@pytest.mark.parametrize("prec", [D.F64, D.F32, D.BF16])
+@pytest.mark.parametrize("kind", [D.WILSON, D.STAGGERED])
+def test_blas_reductions(kind, prec):
+    dims, nc, nv = (6, 4, 4, 4), 3, 7 if prec != D.BF16 else 6
+    op, ref, src = make(kind, dims, nc, nv, (1, 1, 1, 1), prec)
+    src2 = I.source(dims, nc, nv, 77, staggered=(kind == D.STAGGERED))
+    from helpers import rounded
+    a, b = rounded(src, prec), rounded(src2, prec)
+    x, y = to_device(op, src), to_device(op, src2)
+    n2 = op.norm2(x).cpu().numpy()
+    assert np.allclose(n2, O.norm2(a), rtol=1e-12)
+    dt = op.dot(x, y).cpu().numpy()
+    assert np.allclose(dt, O.dot(a, b), rtol=1e-12, atol=1e-9 * np.abs(O.dot(a, b)).max())
+    # deterministic: bitwise identical on repeat
+    assert np.array_equal(op.norm2(x).cpu().numpy(), n2)
+    alpha = (np.arange(nv) + 1j * (0.5 - np.arange(nv))) / nv
+    op.axpy(torch.from_numpy(alpha), x, y)
+    got = to_numpy(op, y)
+    assert rel_l2(got, b + alpha * a) <= TOL[prec]
+    op.gamma5_(x)
+    want = O.epsilon(a) if kind == D.STAGGERED else O.gamma5(a)
+    assert rel_l2(to_numpy(op, x), want) <= (1e-15 if prec != D.BF16 else 1e-2)
+    op.close()
+
+
+def test_host_apply_matches_device_apply():
+    dims = (8, 8, 4, 8)
+    for kind in KINDS:
+        op, ref, src = make(kind, dims, 3, 12, (1, 1, 1, -1), D.F32)
+        x = to_device(op, src)
+        dev = op.apply(x, m0=0.1).cpu()
+        hin = x.cpu().pin_memory()
+        hout = torch.empty_like(hin).pin_memory()
+        op.apply_host(hin, hout, m0=0.1)
+        assert torch.equal(hout, dev)
+        op.close()
+
+
+def test_precision_convert_roundtrip():
+    op, ref, src = make(D.WILSON, (4, 4, 4, 4), 3, 4, (1, 1, 1, 1), D.F64)
+    x = to_device(op, src)
+    for p in (D.F32, D.BF16, D.F16):
+        lo = op.convert(x, D.F64, p)
+        back = op.convert(lo, p, D.F64)
+        from helpers import rounded
+        assert np.array_equal(to_numpy(op, back), rounded(src, p))
+    op.close()
+
+
+def test_error_codes_from_the_abi():
+    U = torch.from_numpy(I.gauge_field((4, 4, 4, 4), 3, 0.4, 1)).cuda()
+    with pytest.raises(D.DiracError) as e:
+        D.DiracOp(D.STAGGERED, U[:, :, :, :3].contiguous(), 2)       # odd Nx
+    assert e.value.code == -1
+    with pytest.raises(D.DiracError) as e:
+        D.DiracOp(D.WILSON, U, 65)                                  # N_v > 64
+    assert e.value.code == -1
+    op = D.DiracOp(D.WILSON, U, 2, prec=D.F32)
+    x = op.new_vector()
+    buf = torch.zeros(x.numel() * 2 + 8, dtype=torch.float32, device="cuda")
+    lib = D.lib()
+    import ctypes
+    # a pointer 4 bytes into an allocation: rejected before any launch
+    rc = lib.dirac_apply(op._h, ctypes.c_void_p(buf.data_ptr() + 4), ctypes.c_void_p(x.data_ptr()), 0.1,
+                         ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == -4
+    rc = lib.dirac_apply(op._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(x.data_ptr()), 0.1,
+                         ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == -1   # in place is rejected
+    op.close()

@@ -1,0 +1,112 @@
+"""GPU solvers through the C ABI against the FP64 oracle: CG on the normal
+equations, BiCGstab, and the defect-correction (mixed-precision) driver with
+FP32, BF16 and FP16 inner solves.  Every returned solution is checked by the
+oracle applying D in FP64 to it, independently of what the solver reports."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from helpers import rel_l2, to_device, to_numpy
+from paper_2112_14640_gb300 import dirac as D
+from paper_2112_14640_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def setup(kind, dims, nc, nv, bc, prec, eps=0.4, seed=31):
+    U = I.gauge_field(dims, nc, eps, seed)
+    op = D.DiracOp(kind, torch.from_numpy(U).cuda(), nv, bc, prec)
+    ref = O.Operator(kind, U, bc)
+    b = I.source(dims, nc, nv, seed + 1, staggered=(kind == D.STAGGERED))
+    return op, ref, b
+
+
+def normal_relres(ref, x, b, m0):
+    """||D^dag b - D^dag D x|| / ||D^dag b|| per RHS, in FP64 by the oracle."""
+    bN = ref.apply_dagger(b, m0)
+    r = bN - ref.apply_normal(x, m0)
+    return np.sqrt(O.norm2(r) / O.norm2(bN))
+
+
+def true_relres(ref, x, b, m0):
+    return np.sqrt(O.norm2(b - ref.apply(x, m0)) / O.norm2(b))
+
+
+def test_config1_wilson_4x4_cg_f64():
+    """4^4, N_c = 3, N_v = 1, FP64, m0 = 0.1, antiperiodic in t, CG to 1e-10."""
+    op, ref, b = setup(D.WILSON, (4, 4, 4, 4), 3, 1, (1, 1, 1, -1), D.F64)
+    x, st = op.solve(to_device(op, b), m0=0.1, tol=1e-10, maxit=5000)
+    assert st["status"] == 0, st
+    xs = to_numpy(op, x)
+    assert normal_relres(ref, xs, b, 0.1)[0] < 1.01e-10
+    xo, info = O.cg_normal(ref, b, tol=1e-10, maxit=5000)
+    assert rel_l2(xs, xo) < 1e-8
+    assert abs(st["iters"] - info["iters"]) <= 2
+
+
+@pytest.mark.parametrize("kind", [D.WILSON, D.BRILLOUIN, D.STAGGERED])
+def test_cg_normal_f64_matches_oracle(kind):
+    m0 = 0.2
+    op, ref, b = setup(kind, (4, 4, 2, 6), 3, 3, (1, 1, 1, -1), D.F64)
+    x, st = op.solve(to_device(op, b), m0=m0, tol=1e-11, maxit=5000)
+    assert st["status"] == 0
+    xs = to_numpy(op, x)
+    assert np.all(normal_relres(ref, xs, b, m0) < 1.01e-11)
+    assert np.allclose(st["true_relres"], true_relres(ref, xs, b, m0), rtol=1e-3, atol=1e-13)
+
+
+@pytest.mark.parametrize("kind", [D.WILSON, D.BRILLOUIN])
+def test_bicgstab_f64(kind):
+    m0 = 0.2
+    op, ref, b = setup(kind, (4, 4, 4, 2), 3, 2, (1, 1, 1, -1), D.F64)
+    x, st = op.solve(to_device(op, b), m0=m0, solver=D.BICGSTAB, tol=1e-10, maxit=5000)
+    assert st["status"] == 0, st
+    assert np.all(true_relres(ref, to_numpy(op, x), b, m0) < 1.01e-10)
+
+
+@pytest.mark.parametrize("inner", [D.F32, D.BF16, D.F16])
+@pytest.mark.parametrize("kind", [D.WILSON, D.STAGGERED, D.BRILLOUIN])
+def test_mixed_precision_cg_reaches_1e10(kind, inner):
+    m0 = 0.05
+    op, ref, b = setup(kind, (4, 4, 4, 8), 3, 4, (1, 1, 1, -1), D.F64)
+    x, st = op.solve(to_device(op, b), m0=m0, tol=1e-10, maxit=20000, inner_prec=inner)
+    assert st["status"] == 0, st
+    assert st["outer_iters"] >= 2
+    assert np.all(normal_relres(ref, to_numpy(op, x), b, m0) < 1.01e-10)
+
+
+def test_mixed_precision_bicgstab_wilson():
+    m0 = 0.1
+    op, ref, b = setup(D.WILSON, (4, 4, 4, 4), 3, 3, (1, 1, 1, -1), D.F64)
+    x, st = op.solve(to_device(op, b), m0=m0, solver=D.BICGSTAB, tol=1e-10, maxit=20000, inner_prec=D.F32)
+    assert st["status"] == 0, st
+    assert np.all(true_relres(ref, to_numpy(op, x), b, m0) < 1.01e-10)
+
+
+def test_plain_f32_cg_stagnates_above_1e10():
+    """Sec. 2 / Sec. 9: an sp solve cannot reach 1e-10; it must stop on the
+    1% rule (or maxit) and report a residual consistent with the oracle's."""
+    m0 = 0.01
+    op, ref, b = setup(D.WILSON, (4, 4, 4, 8), 3, 2, (1, 1, 1, -1), D.F32, eps=0.6)
+    x, st = op.solve(to_device(op, b), m0=m0, tol=1e-12, maxit=3000)
+    assert st["status"] in (1, 2)
+    xs = to_numpy(op, x)
+    got = normal_relres(ref, xs, b, m0)
+    assert np.all(got > 1e-10)
+    assert np.allclose(got, st["relres"], rtol=0.2)
+
+
+def test_solver_edge_cases():
+    op, ref, b = setup(D.STAGGERED, (4, 4, 4, 4), 3, 3, (1, 1, 1, 1), D.F64)
+    bb = to_device(op, b)
+    bb[..., 1] = 0                                   # one zero right-hand side
+    x, st = op.solve(bb, m0=0.1, tol=1e-10, maxit=5000)
+    assert st["status"] == 0
+    assert torch.count_nonzero(x[..., 1]) == 0
+    x, st = op.solve(to_device(op, b), m0=0.1, tol=1e-10, maxit=1)
+    assert st["status"] == 1 and st["iters"] == 1
+    # warm start from the solution converges immediately
+    x, st = op.solve(to_device(op, b), m0=0.1, tol=1e-10, maxit=5000)
+    x2, st2 = op.solve(to_device(op, b), x=x.clone(), m0=0.1, tol=1e-10, maxit=5000)
+    assert st2["status"] == 0 and st2["iters"] <= 1
