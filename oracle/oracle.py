@@ -311,20 +311,20 @@ def cg(apply_A, b, x0=None, tol=1e-10, maxit=10000, recompute_every=50):
                    alphas=np.array(alphas).reshape(-1, nv), betas=np.array(betas).reshape(-1, nv))
 
 
-def cg_normal(op, b, x0=None, tol=1e-10, maxit=10000, recompute_every=50):
+def cg_normal(op, b, x0=None, tol=1e-10, maxit=10000, recompute_every=50, m0=None):
     """Solve D^dag D x = D^dag b by CG; stopping on ||r_N|| / ||D^dag b|| < tol.
 
     Reading (the paper's residual is defined for the system being solved):
     the normal-equation residual decides convergence; the true ||b - D x|| / ||b||
     is reported beside it as ``true_relres``.
     """
-    bN = op.apply_dagger(b)
-    x, info = cg(op.apply_normal, bN, x0, tol, maxit, recompute_every)
-    info["true_relres"] = np.sqrt(norm2(b - op.apply(x))) / np.sqrt(norm2(b))
+    bN = op.apply_dagger(b, m0)
+    x, info = cg(lambda v: op.apply_normal(v, m0), bN, x0, tol, maxit, recompute_every)
+    info["true_relres"] = np.sqrt(norm2(b - op.apply(x, m0))) / np.sqrt(norm2(b))
     return x, info
 
 
-def bicgstab(op, b, x0=None, tol=1e-10, maxit=10000, recompute_every=50):
+def bicgstab(op, b, x0=None, tol=1e-10, maxit=10000, recompute_every=50, m0=None):
     """BiCGstab (van der Vorst) on D x = b per RHS, shadow residual r_hat = r_0.
 
     Same recompute/exit rules as ``cg``; breakdown (|rho| or |omega| below
@@ -333,7 +333,7 @@ def bicgstab(op, b, x0=None, tol=1e-10, maxit=10000, recompute_every=50):
     nv = b.shape[-1]
     x = np.zeros_like(b) if x0 is None else np.array(x0, np.complex128)
     nb = np.sqrt(norm2(b))
-    r = b - op.apply(x)
+    r = b - op.apply(x, m0)
     rhat = r.copy()
     rho = np.ones(nv, np.complex128)
     alpha = np.ones(nv, np.complex128)
@@ -353,11 +353,11 @@ def bicgstab(op, b, x0=None, tol=1e-10, maxit=10000, recompute_every=50):
         a_ = active
         beta = np.where(a_, (rho_new / np.where(a_, rho, 1)) * (alpha / np.where(a_, omega, 1)), 0)
         p = np.where(a_, r + beta * (p - omega * v), p)
-        v = op.apply(p)
+        v = op.apply(p, m0)
         rv = dot(rhat, v)
         alpha = np.where(a_, rho_new / np.where(a_, rv, 1), 0)
         s = r - alpha * v
-        t = op.apply(s)
+        t = op.apply(s, m0)
         tt = norm2(t)
         omega = np.where(a_, dot(t, s) / np.where(a_ & (tt > 0), tt, 1), 0)
         bad = a_ & (np.abs(omega) < 1e-30)
@@ -370,7 +370,7 @@ def bicgstab(op, b, x0=None, tol=1e-10, maxit=10000, recompute_every=50):
         if (it % recompute_every == 0 or np.all(np.sqrt(rr[active]) < tol * nb[active])
                 or it >= maxit):
             recomputes += 1
-            rt = b - op.apply(x)
+            rt = b - op.apply(x, m0)
             rr_true = norm2(rt)
             disc = np.abs(np.sqrt(rr) - np.sqrt(rr_true)) / np.maximum(np.sqrt(rr_true), 1e-300)
             r = rt
@@ -385,7 +385,7 @@ def bicgstab(op, b, x0=None, tol=1e-10, maxit=10000, recompute_every=50):
                 break
     if broken.any() and status == CONVERGED:
         status = BREAKDOWN
-    res = np.sqrt(norm2(b - op.apply(x))) / nb
+    res = np.sqrt(norm2(b - op.apply(x, m0))) / nb
     return x, dict(iters=it, recomputes=recomputes, status=status, relres=res, broken=broken)
 
 

@@ -45,7 +45,11 @@ def _expi_hermitian(H, eps):
 
 
 def random_su_n(shape, nc, eps, rng):
-    """Array of random SU(nc) matrices of the given leading shape."""
+    """Array of random SU(nc) matrices of the given leading shape.  For nc = 1
+    (no su(1) generators) the links are U(1) phases exp(i eps a), a ~ N(0,1)."""
+    if nc == 1:
+        a = rng.standard_normal(tuple(shape))
+        return np.exp(1j * eps * a)[..., None, None]
     gm = gell_mann(nc)
     out = np.empty(tuple(shape) + (nc, nc), np.complex128)
     flat = out.reshape(-1, nc, nc)

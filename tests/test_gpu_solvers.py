@@ -40,7 +40,7 @@ def test_config1_wilson_4x4_cg_f64():
     assert st["status"] == 0, st
     xs = to_numpy(op, x)
     assert normal_relres(ref, xs, b, 0.1)[0] < 1.01e-10
-    xo, info = O.cg_normal(ref, b, tol=1e-10, maxit=5000)
+    xo, info = O.cg_normal(ref, b, tol=1e-10, maxit=5000, m0=0.1)
     assert rel_l2(xs, xo) < 1e-8
     assert abs(st["iters"] - info["iters"]) <= 2
 
