@@ -79,6 +79,26 @@ def alg_bytes_per_site(kind, nc, nv, eb=4):
     return 2 * vec + links
 
 
+def ncu_traffic(op_name):
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from
+    the committed ncu summary of this kernel, or None when the kernel source
+    changed since the counters were taken."""
+    import hashlib
+    prof = os.path.join(ROOT, "profiles", "%s_kernel_16x16x16x32_nv12.md" % op_name)
+    csrc = os.path.join(ROOT, "paper_2112_14640_gb300", "csrc")
+    try:
+        text = open(prof).read()
+        h = hashlib.sha256()
+        for f in ("%s.cu" % op_name, "common.cuh"):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+        fields = dict(l.split(":", 1) for l in text.splitlines() if ":" in l and not l.startswith(("#", " ", "|")))
+        if fields.get("kernel_source_sha256_16", "").strip() != h.hexdigest()[:16]:
+            return None
+        return int(fields["traffic_bytes_per_launch"].strip())
+    except Exception:
+        return None
+
+
 class ClockSampler:
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -286,19 +306,21 @@ def main():
     d = per_op[D.KIND_NAMES[dom]]
     if dom == D.BRILLOUIN:
         roof = {"bound": "alu", "achieved": d["gflops"] / 1e3, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": d["gflops"] / 1e3 / fp32_peak, "traffic": None, "kernel": "brillouin_kernel",
+                "frac": d["gflops"] / 1e3 / fp32_peak, "traffic": ncu_traffic("brillouin"),
+                "traffic_unit": "bytes/launch", "kernel": "brillouin_kernel",
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz" % pk["sm_max"]}
     else:
         roof = {"bound": "hbm", "achieved": d["alg_GBps"], "peak": pk["hbm"], "unit": "GB/s",
-                "frac": d["hbm_frac"], "traffic": None, "kernel": D.KIND_NAMES[dom] + "_kernel",
+                "frac": d["hbm_frac"], "traffic": ncu_traffic(D.KIND_NAMES[dom]), "traffic_unit": "bytes/launch",
+                "kernel": D.KIND_NAMES[dom] + "_kernel",
                 "peak_source": pk["source"]}
     rooflines = {
         "wilson": {"bound": "hbm", "achieved": per_op["wilson"]["alg_GBps"], "peak": pk["hbm"], "unit": "GB/s",
-                   "frac": per_op["wilson"]["hbm_frac"]},
+                   "frac": per_op["wilson"]["hbm_frac"], "traffic": ncu_traffic("wilson")},
         "staggered": {"bound": "hbm", "achieved": per_op["staggered"]["alg_GBps"], "peak": pk["hbm"],
-                      "unit": "GB/s", "frac": per_op["staggered"]["hbm_frac"]},
+                      "unit": "GB/s", "frac": per_op["staggered"]["hbm_frac"], "traffic": ncu_traffic("staggered")},
         "brillouin": {"bound": "alu", "achieved": per_op["brillouin"]["gflops"] / 1e3, "peak": fp32_peak,
-                      "unit": "TFLOP/s", "frac": per_op["brillouin"]["alu_frac"]},
+                      "unit": "TFLOP/s", "frac": per_op["brillouin"]["alu_frac"], "traffic": ncu_traffic("brillouin")},
     }
 
     line = {"metric": METRIC, "value": value, "unit": "Gflop/s", "n_gpus": world, "steps": K,
