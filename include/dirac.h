@@ -118,6 +118,21 @@ int dirac_apply_normal(const dirac_op *op, const void *psi_in, void *psi_out, do
 int dirac_apply_host(const dirac_op *op, const void *host_in, void *host_out, double m0,
                      int dagger, void *stream);
 
+/* ----------------------------------------------------- launch tuning
+ * A stencil launch variant is (vr, minb): vr = right-hand sides per thread
+ * (1, 2 or 4, dividing N_v) and minb = minimum resident blocks per SM the
+ * kernel was compiled for (1 = no register cap; 2, 3, 4, 6 compiled for
+ * N_c = 3 only).  vr = 0 restores the default choice.  Errors:
+ * DIRAC_ERR_INVALID_ARG for a variant that is not compiled or does not divide N_v. */
+int dirac_op_set_launch(dirac_op *op, int vr, int minb);
+int dirac_op_get_launch(const dirac_op *op, int *vr, int *minb);
+/* Time every compiled variant of D (bare mass m0) on operator-owned buffers
+ * and keep the fastest for this operator; the choice is also remembered for
+ * operators created later in this process with the same kind, precision,
+ * N_c, N_v and volume (including the lower-precision twins of mixed solves).
+ * best_ms (may be NULL) receives the winner's time per apply.  Synchronises. */
+int dirac_op_autotune(dirac_op *op, double m0, void *stream, double *best_ms);
+
 /* Bytes of one vector of this operator (sites x internal dofs x N_v x complex). */
 size_t dirac_vec_bytes(const dirac_op *op);
 

@@ -1,4 +1,4 @@
-// brillouin.cu -- multi-RHS Brillouin Dirac operator, Eq. (app_bril) with
+// brillouin.cuh -- multi-RHS Brillouin Dirac operator, Eq. (app_bril) with
 // Eqs. (def_ider, def_blap) at r = 1, c_SW = 0:
 //   (D_B psi)(n) = (m0 - lambda_0/2) psi(n)
 //       + sum_{s in {-1,0,1}^4, s != 0} [rho_k sum_mu s_mu gamma_mu - lambda_k/2] (x) W_s(n) psi(n+s)
@@ -16,12 +16,13 @@
 // then the colour matrix W_s(n) multiplies the result into the register
 // accumulator; each W_s(n) is loaded once and used for all 4 spins and the
 // thread's VR right-hand sides.
+#pragma once
 #include "internal.h"
 
 namespace dgb {
 
-template <int NC, int VR, typename E>
-__global__ void __launch_bounds__(128) brillouin_kernel(const E *__restrict__ W, const E *__restrict__ in,
+template <int NC, int VR, typename E, int MINB>
+__global__ void __launch_bounds__(kStencilBlock, MINB) brillouin_kernel(const E *__restrict__ W, const E *__restrict__ in,
                                                         E *__restrict__ out, Lat g, typename Acc<E>::T centre,
                                                         typename Acc<E>::T sgn) {
     using A = typename Acc<E>::T;
@@ -119,21 +120,23 @@ __global__ void __launch_bounds__(128) brillouin_kernel(const E *__restrict__ W,
         }
 }
 
-int launch_brillouin(const dirac_op *op, const void *in, void *out, double m0, int sgn, cudaStream_t s) {
-    const int vr = pick_vr(op->prec, op->nv);
-    return dispatch_prec(op->prec, [&](auto tag) {
-        using E = std::remove_pointer_t<decltype(tag)>;
-        using A = typename Acc<E>::T;
-        return dispatch_nc(op->nc, [&](auto ncc) {
-            constexpr int NC = decltype(ncc)::value;
-            return dispatch_vr(vr, [&](auto vrc) {
-                constexpr int VR = decltype(vrc)::value;
-                const long long threads = op->V * (op->nv / VR);
-                const int block = 128;
-                // m0 - lambda_0 / 2 = m0 + 240/128
-                brillouin_kernel<NC, VR, E><<<grid_for(threads, block), block, 0, s>>>(
-                    (const E *)op->w, (const E *)in, (E *)out, op->lat, (A)(m0 + 240.0 / 128.0), (A)sgn);
-                return launch_check("brillouin_kernel");
+template <typename E>
+int launch_brillouin_t(const dirac_op *op, const void *in, void *out, double m0, int sgn, cudaStream_t s) {
+    int vr, minb;
+    launch_variant(op, vr, minb);
+    using A = typename Acc<E>::T;
+    return dispatch_nc(op->nc, [&](auto ncc) {
+        constexpr int NC = decltype(ncc)::value;
+        return dispatch_vr(vr, [&](auto vrc) {
+            constexpr int VR = decltype(vrc)::value;
+            return dispatch_minb(NC, minb, [&](auto mbc) {
+            constexpr int MINB = decltype(mbc)::value;
+            const long long threads = op->V * (op->nv / VR);
+            const int block = kStencilBlock;
+            // m0 - lambda_0 / 2 = m0 + 240/128
+            brillouin_kernel<NC, VR, E, MINB><<<grid_for(threads, block), block, 0, s>>>(
+                (const E *)op->w, (const E *)in, (E *)out, op->lat, (A)(m0 + 240.0 / 128.0), (A)sgn);
+            return launch_check("brillouin_kernel");
             });
         });
     });

@@ -4,6 +4,10 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "internal.h"
 
 using namespace dgb;
@@ -63,6 +67,30 @@ static int alloc(void **p, size_t bytes) {
     return DIRAC_OK;
 }
 
+// Process-wide memory of autotuned launch variants, keyed by what decides
+// the kernel's behaviour.
+using TuneKey = std::tuple<int, int, int, int, long long>;
+static std::mutex g_tune_mu;
+static std::map<TuneKey, std::pair<int, int>> g_tune;
+
+static TuneKey tune_key(const dirac_op *op) {
+    return TuneKey{(int)op->kind, (int)op->prec, op->nc, op->nv, op->V};
+}
+
+static void remember_tuning(const dirac_op *op) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[tune_key(op)] = {op->vr, op->minb};
+}
+
+static void recall_tuning(dirac_op *op) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(tune_key(op));
+    if (it != g_tune.end()) {
+        op->vr = it->second.first;
+        op->minb = it->second.second;
+    }
+}
+
 // Allocate an operator handle of the given geometry without links.
 int op_alloc(dirac_kind kind, const dirac_geom *g, dirac_op **out) {
     dirac_op *op = (dirac_op *)calloc(1, sizeof(dirac_op));
@@ -90,6 +118,7 @@ int op_alloc(dirac_kind kind, const dirac_geom *g, dirac_op **out) {
         op_free(op);
         return rc;
     }
+    recall_tuning(op);
     *out = op;
     return DIRAC_OK;
 }
@@ -178,6 +207,73 @@ int dirac_op_copy_w(const dirac_op *op, void *w_out, void *stream) {
 void dirac_op_destroy(dirac_op *op) { op_destroy(op); }
 
 size_t dirac_vec_bytes(const dirac_op *op) { return op ? op->vec_bytes : 0; }
+
+int dirac_op_set_launch(dirac_op *op, int vr, int minb) {
+    if (!op) return DIRAC_ERR_INVALID_ARG;
+    if (vr == 0) {
+        op->vr = op->minb = 0;
+        return DIRAC_OK;
+    }
+    if (!variant_compiled(op->nc, vr, minb) || op->nv % vr) return DIRAC_ERR_INVALID_ARG;
+    op->vr = vr;
+    op->minb = minb;
+    return DIRAC_OK;
+}
+
+int dirac_op_get_launch(const dirac_op *op, int *vr, int *minb) {
+    if (!op || !vr || !minb) return DIRAC_ERR_INVALID_ARG;
+    launch_variant(op, *vr, *minb);
+    return DIRAC_OK;
+}
+
+int dirac_op_autotune(dirac_op *op, double m0, void *stream, double *best_ms) {
+    if (!op) return DIRAC_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = DIRAC_OK;
+    if (!op->stage_out) rc = alloc(&op->stage_out, op->vec_bytes);
+    if (rc) return rc;
+    rc = cuda_check(cudaMemsetAsync(op->scratch, 0, op->vec_bytes, s), "autotune memset");
+    if (rc) return rc;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const int vrs[3] = {1, 2, 4}, minbs[5] = {1, 2, 3, 4, 6};
+    float best = 1e30f;
+    int bvr = 0, bmb = 0;
+    const int saved_vr = op->vr, saved_mb = op->minb;
+    for (int a = 0; a < 3 && !rc; ++a)
+        for (int b = 0; b < 5 && !rc; ++b) {
+            if (!variant_compiled(op->nc, vrs[a], minbs[b]) || op->nv % vrs[a]) continue;
+            op->vr = vrs[a];
+            op->minb = minbs[b];
+            for (int w = 0; w < 2 && !rc; ++w) rc = op_apply(op, op->scratch, op->stage_out, m0, +1, s);
+            const int reps = 5;
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < reps && !rc; ++r) rc = op_apply(op, op->scratch, op->stage_out, m0, +1, s);
+            cudaEventRecord(e1, s);
+            if (!rc) rc = cuda_check(cudaEventSynchronize(e1), "autotune sync");
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= reps;
+            if (!rc && ms < best) {
+                best = ms;
+                bvr = vrs[a];
+                bmb = minbs[b];
+            }
+        }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc || !bvr) {
+        op->vr = saved_vr;
+        op->minb = saved_mb;
+        return rc ? rc : DIRAC_ERR_INVALID_ARG;
+    }
+    op->vr = bvr;
+    op->minb = bmb;
+    remember_tuning(op);
+    if (best_ms) *best_ms = best;
+    return DIRAC_OK;
+}
 
 static int apply_checked(const dirac_op *op, const void *in, void *out, double m0, int sgn, void *stream) {
     if (!op) return DIRAC_ERR_INVALID_ARG;

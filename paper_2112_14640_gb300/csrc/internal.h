@@ -32,6 +32,7 @@ struct dirac_op {
     void *solver_ws;       // solver workspace (lazy), solver_ws_bytes long
     size_t solver_ws_bytes;
     dirac_op *inner[4];    // lower-precision twins for mixed solves (lazy)
+    int vr, minb;          // stencil launch variant (RHS per thread, min blocks/SM); 0 = default
 };
 
 namespace dgb {
@@ -85,6 +86,39 @@ int dispatch_vr(int vr, F &&f) {
     case 4: return f(std::integral_constant<int, 4>{});
     }
     return DIRAC_ERR_INVALID_ARG;
+}
+
+// Stencil launch variants: VR right-hand sides per thread and a register cap
+// through __launch_bounds__(128, MINB).  Every (VR, MINB) pair below is
+// compiled for N_c = 3; other N_c have MINB = 1 only.
+constexpr int kStencilBlock = 128;
+inline bool variant_compiled(int nc, int vr, int minb) {
+    if (vr != 1 && vr != 2 && vr != 4) return false;
+    if (minb == 1) return true;
+    return nc == 3 && (minb == 2 || minb == 3 || minb == 4 || minb == 6);
+}
+
+template <typename F>
+int dispatch_minb(int nc, int minb, F &&f) {
+    if (nc != 3 || minb == 1) return f(std::integral_constant<int, 1>{});
+    switch (minb) {
+    case 2: return f(std::integral_constant<int, 2>{});
+    case 3: return f(std::integral_constant<int, 3>{});
+    case 4: return f(std::integral_constant<int, 4>{});
+    case 6: return f(std::integral_constant<int, 6>{});
+    }
+    return DIRAC_ERR_INVALID_ARG;
+}
+
+// (vr, minb) an operator launches with: its tuned choice or the default.
+inline void launch_variant(const dirac_op *op, int &vr, int &minb) {
+    if (op->vr) {
+        vr = op->vr;
+        minb = op->minb ? op->minb : 1;
+        return;
+    }
+    vr = pick_vr(op->prec, op->nv);
+    minb = 1;
 }
 
 inline unsigned grid_for(long long threads, int block) {

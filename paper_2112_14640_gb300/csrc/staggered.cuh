@@ -1,4 +1,4 @@
-// staggered.cu -- multi-RHS Susskind (staggered) Dirac operator, Eq. (def_stag):
+// staggered.cuh -- multi-RHS Susskind (staggered) Dirac operator, Eq. (def_stag):
 //   (D_S phi)(n) = m0 phi(n) + 1/2 sum_mu eta_mu(n) [U_mu(n) phi(n+mu) - U_mu(n-mu)^dag phi(n-mu)]
 // with eta_1 = 1, eta_2 = (-1)^x, eta_3 = (-1)^(x+y), eta_4 = (-1)^(x+y+z) in
 // the paper's 1-based coordinates (App. D starts the toggles at x = 1, which
@@ -8,6 +8,7 @@
 //
 // Thread <-> (site, VR consecutive right-hand sides), colour-vector
 // accumulator in registers, one write per output element.
+#pragma once
 #include "internal.h"
 
 namespace dgb {
@@ -34,8 +35,8 @@ __device__ __forceinline__ void stag_hop(cx<A> (&acc)[NC][VR], const E *__restri
         }
 }
 
-template <int NC, int VR, typename E>
-__global__ void __launch_bounds__(128) staggered_kernel(const E *__restrict__ U, const E *__restrict__ in,
+template <int NC, int VR, typename E, int MINB>
+__global__ void __launch_bounds__(kStencilBlock, MINB) staggered_kernel(const E *__restrict__ U, const E *__restrict__ in,
                                                         E *__restrict__ out, Lat g, typename Acc<E>::T mass,
                                                         typename Acc<E>::T half_sgn) {
     using A = typename Acc<E>::T;
@@ -81,20 +82,22 @@ __global__ void __launch_bounds__(128) staggered_kernel(const E *__restrict__ U,
     }
 }
 
-int launch_staggered(const dirac_op *op, const void *in, void *out, double m0, int sgn, cudaStream_t s) {
-    const int vr = pick_vr(op->prec, op->nv);
-    return dispatch_prec(op->prec, [&](auto tag) {
-        using E = std::remove_pointer_t<decltype(tag)>;
-        using A = typename Acc<E>::T;
-        return dispatch_nc(op->nc, [&](auto ncc) {
-            constexpr int NC = decltype(ncc)::value;
-            return dispatch_vr(vr, [&](auto vrc) {
-                constexpr int VR = decltype(vrc)::value;
-                const long long threads = op->V * (op->nv / VR);
-                const int block = 128;
-                staggered_kernel<NC, VR, E><<<grid_for(threads, block), block, 0, s>>>(
-                    (const E *)op->links, (const E *)in, (E *)out, op->lat, (A)m0, (A)(0.5 * sgn));
-                return launch_check("staggered_kernel");
+template <typename E>
+int launch_staggered_t(const dirac_op *op, const void *in, void *out, double m0, int sgn, cudaStream_t s) {
+    int vr, minb;
+    launch_variant(op, vr, minb);
+    using A = typename Acc<E>::T;
+    return dispatch_nc(op->nc, [&](auto ncc) {
+        constexpr int NC = decltype(ncc)::value;
+        return dispatch_vr(vr, [&](auto vrc) {
+            constexpr int VR = decltype(vrc)::value;
+            return dispatch_minb(NC, minb, [&](auto mbc) {
+            constexpr int MINB = decltype(mbc)::value;
+            const long long threads = op->V * (op->nv / VR);
+            const int block = kStencilBlock;
+            staggered_kernel<NC, VR, E, MINB><<<grid_for(threads, block), block, 0, s>>>(
+                (const E *)op->links, (const E *)in, (E *)out, op->lat, (A)m0, (A)(0.5 * sgn));
+            return launch_check("staggered_kernel");
             });
         });
     });

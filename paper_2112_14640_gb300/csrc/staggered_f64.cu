@@ -1,0 +1,6 @@
+// staggered_f64.cu -- F64 instantiations of the staggered stencil (see staggered.cuh).
+#include "staggered.cuh"
+
+namespace dgb {
+template int launch_staggered_t<double>(const dirac_op *, const void *, void *, double, int, cudaStream_t);
+}  // namespace dgb

@@ -1,4 +1,4 @@
-// wilson.cu -- multi-RHS Wilson Dirac operator, Eq. (app_wils) at r = 1,
+// wilson.cuh -- multi-RHS Wilson Dirac operator, Eq. (app_wils) at r = 1,
 // c_SW = 0:
 //   (D_W psi)(n) = (4 + m0) psi(n)
 //       - 1/2 sum_mu { (1 - gamma_mu) U_mu(n) psi(n+mu) + (1 + gamma_mu) U_mu(n-mu)^dag psi(n-mu) }
@@ -12,6 +12,7 @@
 // (colour, spin) component are one 16-byte load and neighbouring threads read
 // neighbouring bytes.  Every thread accumulates its whole output in
 // registers and writes it once (the paper's write-once "site" accumulator).
+#pragma once
 #include "internal.h"
 
 namespace dgb {
@@ -107,8 +108,8 @@ __device__ __forceinline__ void wilson_dir(cx<A> (&acc)[NC][4][VR], const E *__r
                                  g.nv, sgn);
 }
 
-template <int NC, int VR, typename E>
-__global__ void __launch_bounds__(128) wilson_kernel(const E *__restrict__ U, const E *__restrict__ in,
+template <int NC, int VR, typename E, int MINB>
+__global__ void __launch_bounds__(kStencilBlock, MINB) wilson_kernel(const E *__restrict__ U, const E *__restrict__ in,
                                                      E *__restrict__ out, Lat g, typename Acc<E>::T diag,
                                                      typename Acc<E>::T sgn) {
     using A = typename Acc<E>::T;
@@ -150,20 +151,22 @@ __global__ void __launch_bounds__(128) wilson_kernel(const E *__restrict__ U, co
         }
 }
 
-int launch_wilson(const dirac_op *op, const void *in, void *out, double m0, int sgn, cudaStream_t s) {
-    const int vr = pick_vr(op->prec, op->nv);
-    return dispatch_prec(op->prec, [&](auto tag) {
-        using E = std::remove_pointer_t<decltype(tag)>;
-        using A = typename Acc<E>::T;
-        return dispatch_nc(op->nc, [&](auto ncc) {
-            constexpr int NC = decltype(ncc)::value;
-            return dispatch_vr(vr, [&](auto vrc) {
-                constexpr int VR = decltype(vrc)::value;
-                const long long threads = op->V * (op->nv / VR);
-                const int block = 128;
-                wilson_kernel<NC, VR, E><<<grid_for(threads, block), block, 0, s>>>(
-                    (const E *)op->links, (const E *)in, (E *)out, op->lat, (A)(4.0 + m0), (A)sgn);
-                return launch_check("wilson_kernel");
+template <typename E>
+int launch_wilson_t(const dirac_op *op, const void *in, void *out, double m0, int sgn, cudaStream_t s) {
+    int vr, minb;
+    launch_variant(op, vr, minb);
+    using A = typename Acc<E>::T;
+    return dispatch_nc(op->nc, [&](auto ncc) {
+        constexpr int NC = decltype(ncc)::value;
+        return dispatch_vr(vr, [&](auto vrc) {
+            constexpr int VR = decltype(vrc)::value;
+            return dispatch_minb(NC, minb, [&](auto mbc) {
+            constexpr int MINB = decltype(mbc)::value;
+            const long long threads = op->V * (op->nv / VR);
+            const int block = kStencilBlock;
+            wilson_kernel<NC, VR, E, MINB><<<grid_for(threads, block), block, 0, s>>>(
+                (const E *)op->links, (const E *)in, (E *)out, op->lat, (A)(4.0 + m0), (A)sgn);
+            return launch_check("wilson_kernel");
             });
         });
     });

@@ -1,0 +1,6 @@
+// wilson_f16.cu -- F16 instantiations of the wilson stencil (see wilson.cuh).
+#include "wilson.cuh"
+
+namespace dgb {
+template int launch_wilson_t<__half>(const dirac_op *, const void *, void *, double, int, cudaStream_t);
+}  // namespace dgb

@@ -62,6 +62,9 @@ SIGNATURES = {
     "dirac_apply_dagger": (_I, [_P, _P, _P, _D, _P]),
     "dirac_apply_normal": (_I, [_P, _P, _P, _D, _P]),
     "dirac_apply_host": (_I, [_P, _P, _P, _D, _I, _P]),
+    "dirac_op_set_launch": (_I, [_P, _I, _I]),
+    "dirac_op_get_launch": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "dirac_op_autotune": (_I, [_P, _D, _P, ctypes.POINTER(_D)]),
     "dirac_vec_bytes": (_SZ, [_P]),
     "dirac_vec_norm2": (_I, [_P, _P, _P, _P]),
     "dirac_vec_dot": (_I, [_P, _P, _P, _P, _P]),
@@ -191,6 +194,21 @@ class DiracOp:
         if v.dtype in (torch.bfloat16, torch.float16):
             return torch.view_as_complex(v.float().contiguous())
         return v
+
+    def set_launch(self, vr, minb=1):
+        """Pick the stencil launch variant (vr RHS per thread, minb blocks/SM register cap)."""
+        _check(lib().dirac_op_set_launch(self._h, int(vr), int(minb)), "dirac_op_set_launch")
+
+    def get_launch(self):
+        vr, mb = ctypes.c_int(), ctypes.c_int()
+        _check(lib().dirac_op_get_launch(self._h, ctypes.byref(vr), ctypes.byref(mb)), "dirac_op_get_launch")
+        return vr.value, mb.value
+
+    def autotune(self, m0=0.0, stream=None):
+        """Time every compiled launch variant and keep the fastest; returns ms per apply."""
+        ms = ctypes.c_double()
+        _check(lib().dirac_op_autotune(self._h, float(m0), _stream(stream), ctypes.byref(ms)), "dirac_op_autotune")
+        return ms.value
 
     def vec_bytes(self):
         return int(lib().dirac_vec_bytes(self._h))
