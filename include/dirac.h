@@ -51,6 +51,7 @@ enum {
     DIRAC_ERR_OOM = -5,             /* a library-owned allocation failed */
     DIRAC_ERR_CUDA = -6,            /* a CUDA call or launch failed; see stderr */
     DIRAC_ERR_DEVICE_TIMEOUT = -7,  /* a bounded device-side wait ran out */
+    DIRAC_ERR_CAPACITY = -8,        /* request exceeds a fixed static capacity */
     DIRAC_NOT_CONVERGED = 1,        /* maxit reached */
     DIRAC_STAGNATED = 2,            /* updated and recomputed residual differ > 1% (Sec. 9) */
     DIRAC_BREAKDOWN = 3,            /* BiCGstab rho or omega vanished */
@@ -151,6 +152,30 @@ int dirac_vec_gamma5(const dirac_op *op, void *v, void *stream);
 /* Convert a vector between precisions (same shape): src in src_prec, dst in dst_prec. */
 int dirac_vec_convert(const dirac_op *op, const void *src, dirac_prec src_prec, void *dst,
                       dirac_prec dst_prec, void *stream);
+
+/* Per-RHS squared 2-norms of a [rows][nv] complex vector in precision prec,
+ * written to out_dev (nv doubles), for callers that cannot allocate device
+ * memory: code running where cudaMalloc is unavailable or forbidden, such as
+ * inside CUDA stream capture of a graph they do not own, in a host callback,
+ * under a custom allocator that must not be bypassed, or in a real-time loop
+ * that forbids allocation.  It needs no operator handle and allocates nothing:
+ * the partial sums live in a fixed device array inside the library
+ * (DIRAC_NOALLOC_MAX_BLOCKS x 64 doubles = 256 KiB, held by every GPU that
+ * loads the library until the process exits).  The paper has no counterpart;
+ * the result equals dirac_vec_norm2's up to FP64 rounding (the two may split
+ * the sum over a different number of blocks).
+ *   v        device pointer, 16-byte aligned, rows*nv complex numbers
+ *   rows     >= 1 (any size; the reduction is a grid-stride loop)
+ *   nv       1..64, else DIRAC_ERR_CAPACITY
+ * The first call on each device looks up the array's device address (with
+ * that device current), so make that first call before any stream capture.
+ * All calls share the one array: calls whose work overlaps on the GPU (other
+ * streams, other host threads) race and must be serialised by the caller.
+ * Nothing needs clearing between calls: every partial sum read is written
+ * earlier in the same call. */
+#define DIRAC_NOALLOC_MAX_BLOCKS 512
+int dirac_vec_norm2_noalloc(const void *v, dirac_prec prec, long long rows, int nv, double *out_dev,
+                            void *stream);
 
 /* ------------------------------------------------------------- solvers (Sec. 9) */
 typedef enum { DIRAC_CG_NORMAL = 0, DIRAC_BICGSTAB = 1 } dirac_solver;

@@ -203,4 +203,56 @@ int blas_convert(const dirac_op *op, const void *src, dirac_prec sp, void *dst, 
     });
 }
 
+// ------------------------------------------------------------------------
+// Allocation-free variant of the norm^2 reduction (dirac_vec_norm2_noalloc):
+// the per-block partial sums go to a file-scope device array instead of the
+// operator's buffer.  Host code must not pass the symbol itself to a kernel
+// (in host code it names a host-side shadow, not device memory): its device
+// address is looked up once per device with cudaGetSymbolAddress.
+static __device__ __align__(256) double g_noalloc_partial[DIRAC_NOALLOC_MAX_BLOCKS * 64];
+
+static double *noalloc_partial_ptr(int *rc) {
+    static double *addr[128] = {nullptr};
+    int dev = 0;
+    *rc = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
+    if (*rc) return nullptr;
+    if (dev < 0 || dev >= 128) {
+        *rc = DIRAC_ERR_CAPACITY;
+        return nullptr;
+    }
+    if (!addr[dev]) {
+        double *p = nullptr;
+        *rc = cuda_check(cudaGetSymbolAddress((void **)&p, g_noalloc_partial), "cudaGetSymbolAddress");
+        if (*rc) return nullptr;
+        addr[dev] = p;
+    }
+    return addr[dev];
+}
+
 }  // namespace dgb
+
+extern "C" int dirac_vec_norm2_noalloc(const void *v, dirac_prec prec, long long rows, int nv, double *out_dev,
+                                       void *stream) {
+    using namespace dgb;
+    if (!v || !out_dev || rows < 1) return DIRAC_ERR_INVALID_ARG;
+    if ((uintptr_t)v & 15) return DIRAC_ERR_ALIGNMENT;
+    if (prec < DIRAC_F64 || prec > DIRAC_F16) return DIRAC_ERR_UNSUPPORTED_PREC;
+    if (nv < 1 || nv > 64) {
+        fprintf(stderr, "libdirac: dirac_vec_norm2_noalloc: nv = %d exceeds the static capacity of 64\n", nv);
+        return DIRAC_ERR_CAPACITY;
+    }
+    int rc = DIRAC_OK;
+    double *partial = noalloc_partial_ptr(&rc);
+    if (rc) return rc;
+    const int tb = red_block(nv);
+    const int R = tb / nv;
+    long long want = (rows + R - 1) / R;
+    const int blocks = (int)(want < DIRAC_NOALLOC_MAX_BLOCKS ? want : DIRAC_NOALLOC_MAX_BLOCKS);
+    cudaStream_t s = (cudaStream_t)stream;
+    return dispatch_prec(prec, [&](auto tag) {
+        using E = std::remove_pointer_t<decltype(tag)>;
+        norm2_kernel<E><<<blocks, tb, tb * sizeof(double), s>>>((const E *)v, rows, nv, partial);
+        finalize_kernel<1><<<1, 64, 0, s>>>(partial, blocks, nv, out_dev);
+        return launch_check("norm2_kernel (noalloc)");
+    });
+}

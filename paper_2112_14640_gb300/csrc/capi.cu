@@ -361,6 +361,7 @@ const char *dirac_error_string(int code) {
     case DIRAC_ERR_OOM: return "device allocation failed";
     case DIRAC_ERR_CUDA: return "CUDA error";
     case DIRAC_ERR_DEVICE_TIMEOUT: return "bounded device wait timed out";
+    case DIRAC_ERR_CAPACITY: return "request exceeds a fixed static capacity";
     case DIRAC_NOT_CONVERGED: return "solver reached maxit";
     case DIRAC_STAGNATED: return "solver stagnated (updated vs recomputed residual differ by >1%)";
     case DIRAC_BREAKDOWN: return "solver breakdown";

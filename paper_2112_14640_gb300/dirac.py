@@ -71,6 +71,7 @@ SIGNATURES = {
     "dirac_vec_axpy": (_I, [_P, _P, _P, _P, _P]),
     "dirac_vec_gamma5": (_I, [_P, _P, _P]),
     "dirac_vec_convert": (_I, [_P, _P, _I, _P, _I, _P]),
+    "dirac_vec_norm2_noalloc": (_I, [_P, _I, ctypes.c_longlong, _I, _P, _P]),
     "dirac_solve": (_I, [_P, _P, _P, _D, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats), _P]),
     "dirac_error_string": (ctypes.c_char_p, [_I]),
     "dirac_flops_per_site": (ctypes.c_long, [_I, _I]),
