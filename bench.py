@@ -242,10 +242,13 @@ def main():
     kinds = tuple(names[o] for o in args.ops.split(","))
     sources = {k: I.source(DIMS, NC, NV, 4321 + k, staggered=(k == D.STAGGERED)) for k in kinds}
     ops, xs, ys = {}, {}, {}
+    launch = {}
     for k in kinds:
         ops[k] = D.DiracOp(k, U, NV, BC, D.F32)
         xs[k] = ops[k].to_prec(torch.from_numpy(sources[k]).cuda())
         ys[k] = ops[k].new_vector(zero=False)
+        ops[k].autotune(MASS[k])          # untimed setup: pick the launch variant
+        launch[D.KIND_NAMES[k]] = ops[k].get_launch()
     V = int(np.prod(DIMS))
     flop = {k: D.flops_per_site(k, NC) * V * NV for k in kinds}
     step_flop = sum(flop.values())
@@ -327,7 +330,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_dict(),
             "gpu_launches": K * len(kinds), "roofline": roof, "rooflines": rooflines, "per_op": per_op,
-            "clocks": clk, "peaks_source": pk["source"]}
+            "clocks": clk, "peaks_source": pk["source"], "launch_variants": launch}
 
     if not args.ncu:
         # end to end through the C ABI from pinned host memory, copies included

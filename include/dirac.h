@@ -178,7 +178,11 @@ int dirac_vec_norm2_noalloc(const void *v, dirac_prec prec, long long rows, int 
                             void *stream);
 
 /* ------------------------------------------------------------- solvers (Sec. 9) */
-typedef enum { DIRAC_CG_NORMAL = 0, DIRAC_BICGSTAB = 1 } dirac_solver;
+typedef enum {
+    DIRAC_CG_NORMAL = 0,   /* CG on D^dag D x = D^dag b (Sec. 9, A = D^dag D) */
+    DIRAC_BICGSTAB = 1,    /* BiCGstab on D x = b (Sec. 9) */
+    DIRAC_CG_HPD = 2       /* CG on D^dag D x = b, b given directly (pseudofermion solves) */
+} dirac_solver;
 
 typedef struct {
     dirac_solver solver;   /* CG on D^dag D x = D^dag b, or BiCGstab on D x = b */
@@ -208,6 +212,22 @@ typedef struct {
  * per-iteration residual norms on the host).  stats may be NULL. */
 int dirac_solve(const dirac_op *op, const void *b, void *x, double m0,
                 const dirac_solve_params *params, dirac_solve_stats *stats, void *stream);
+
+/* ------------------------------------------------------------ fermion force
+ * Derivative of S = sum_v Re phi_v^dag (D_W^dag D_W)^-1 phi_v with respect to
+ * the links (the paper has no force; derived from Eq. app_wils).  Inputs:
+ * psi = (D^dag D)^-1 phi and chi = D psi, Wilson-type vectors of op (F64 or
+ * F32).  Output: [site][mu][a][b] complex in op precision.
+ *   mode DIRAC_FORCE_TA:   F_mu(n) = P_TA(U B - C U^dag), traceless
+ *                          anti-hermitian, with dS/deps = Re sum tr[X F] for
+ *                          U -> exp(eps X) U, X in su(Nc);
+ *   mode DIRAC_FORCE_GRAD: G with dS = Re sum conj(G) dU for an arbitrary
+ *                          complex change dU of the caller's (unphased) links,
+ * where B_mu(n) = sum psi(n+mu) [(1-gamma_mu) chi(n)]^dag and
+ * C_mu(n) = sum psi(n) [(1+gamma_mu) chi(n+mu)]^dag, summed over spin and RHS. */
+enum { DIRAC_FORCE_TA = 0, DIRAC_FORCE_GRAD = 1 };
+int dirac_force_wilson(const dirac_op *op, const void *psi, const void *chi, void *force_out, int mode,
+                       void *stream);
 
 /* ------------------------------------------------------------- utilities */
 const char *dirac_error_string(int code);

@@ -420,6 +420,73 @@ def lanczos_cond(alphas, betas):
     return np.array(res)
 
 
+# --------------------------------------------------------------- force
+# The paper has no force; this is derived for S = sum_v phi_v^dag (D_W^dag D_W)^-1 phi_v.
+# With psi = (D^dag D)^-1 phi and chi = D psi, dS = -2 Re <chi, dD psi>.  Only
+# the two hops through U_mu(n) depend on it:
+#   forward  at n:     -1/2 (1 - gamma_mu) U_mu(n) psi(n+mu)
+#   backward at n+mu:  -1/2 (1 + gamma_mu) U_mu(n)^dag psi(n)
+# so with the colour matrices (spin and RHS summed)
+#   B_mu(n) = sum psi(n+mu) [(1 - gamma_mu) chi(n)]^dag,
+#   C_mu(n) = sum psi(n) [(1 + gamma_mu) chi(n+mu)]^dag
+# one finds dS = Re sum tr[dU_mu(n) (B_mu(n) + C_mu(n)^dag)].  For U -> exp(eps X) U,
+# X in su(N): dS/deps = Re sum tr[X M] with M = U B - C U^dag, and only the
+# traceless anti-hermitian part F = P_TA(M) contributes.
+
+def _proj(chi, mu, sign):
+    """(1 + sign*gamma_mu) applied in spinor space to a Wilson-type vector."""
+    g = gamma(mu)
+    return chi + sign * np.einsum("st,...ctv->...csv", g, chi)
+
+
+def _shift(v, mu, step):
+    """v(n + step*mu), periodic (axes of the vector: t, z, y, x first)."""
+    ax = {0: 3, 1: 2, 2: 1, 3: 0}[mu]
+    return np.roll(v, -step, axis=ax)
+
+
+def wilson_force_terms(op, psi, chi):
+    """(B, C) per link, each of shape (Nt, Nz, Ny, Nx, 4, Nc, Nc)."""
+    sh = psi.shape[:4] + (4, psi.shape[4], psi.shape[4])
+    B = np.empty(sh, np.complex128)
+    C = np.empty(sh, np.complex128)
+    for mu in range(4):
+        B[..., mu, :, :] = np.einsum("...asv,...bsv->...ab", _shift(psi, mu, 1), np.conj(_proj(chi, mu, -1)))
+        C[..., mu, :, :] = np.einsum("...asv,...bsv->...ab", psi, np.conj(_proj(_shift(chi, mu, 1), mu, +1)))
+    return B, C
+
+
+def project_ta(M):
+    """Traceless anti-hermitian part of each colour matrix."""
+    A = 0.5 * (M - np.conj(np.swapaxes(M, -1, -2)))
+    n = M.shape[-1]
+    tr = np.trace(A, axis1=-2, axis2=-1) / n
+    return A - tr[..., None, None] * np.eye(n)
+
+
+def wilson_force(op, psi, chi):
+    """F_mu(n) = P_TA(U B - C U^dag) with the operator's phased links."""
+    B, C = wilson_force_terms(op, psi, chi)
+    U = op.Up
+    M = U @ B - C @ np.conj(np.swapaxes(U, -1, -2))
+    return project_ta(M)
+
+
+def wilson_action_gradient(op, psi, chi):
+    """dS/dU in the convention dS = Re sum conj(G) dU for the unphased links:
+    G = bc-phase * (B^dag + C)."""
+    B, C = wilson_force_terms(op, psi, chi)
+    G = np.conj(np.swapaxes(B, -1, -2)) + C
+    ph = phase_links(np.ones(op.Up.shape, np.complex128), op.bc)
+    return G * ph
+
+
+def pseudofermion_action(op, phi, m0=None, tol=1e-13, maxit=20000):
+    """S = sum_v Re phi_v^dag (D^dag D)^-1 phi_v and the solution psi."""
+    psi, info = cg(lambda v: op.apply_normal(v, m0), phi, None, tol, maxit, 50)
+    return float(np.sum(np.real(np.conj(phi) * psi))), psi
+
+
 # ------------------------------------------------------------ App. E counts
 
 def flops_per_site(kind, nc):

@@ -143,6 +143,31 @@ __global__ void convert_kernel(const S *__restrict__ src, D *__restrict__ dst, l
     if (i < count) dst[i] = from_acc<D, typename Acc<S>::T>(to_acc<S>(src[i]));
 }
 
+// Deterministic pseudo-random fill in [-1, 1) (a 32-bit integer hash of the
+// element index), used to give timing runs realistic, non-zero operands.
+template <typename E>
+__global__ void fill_hash_kernel(E *__restrict__ v, long long count, unsigned seed) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    unsigned h = (unsigned)i * 2654435761u ^ seed;
+    h ^= h >> 16;
+    h *= 2246822519u;
+    h ^= h >> 13;
+    h *= 3266489917u;
+    h ^= h >> 16;
+    const float f = (float)(h >> 8) * (1.0f / 8388608.0f) - 1.0f;
+    v[i] = from_acc<E, typename Acc<E>::T>((typename Acc<E>::T)f);
+}
+
+int blas_fill_hash(const dirac_op *op, dirac_prec p, void *v, unsigned seed, cudaStream_t s) {
+    return dispatch_prec(p, [&](auto tag) {
+        using E = std::remove_pointer_t<decltype(tag)>;
+        const long long n = op->rows * op->nv * 2;
+        fill_hash_kernel<E><<<grid_for(n, 256), 256, 0, s>>>((E *)v, n, seed);
+        return launch_check("fill_hash_kernel");
+    });
+}
+
 static inline int red_grid(const dirac_op *op) { return op->red_blocks; }
 
 int blas_norm2(const dirac_op *op, dirac_prec p, const void *v, double *out, cudaStream_t s) {

@@ -232,35 +232,45 @@ int dirac_op_autotune(dirac_op *op, double m0, void *stream, double *best_ms) {
     int rc = DIRAC_OK;
     if (!op->stage_out) rc = alloc(&op->stage_out, op->vec_bytes);
     if (rc) return rc;
-    rc = cuda_check(cudaMemsetAsync(op->scratch, 0, op->vec_bytes, s), "autotune memset");
+    // realistic operands (power draw, and hence clocks, depend on the data)
+    rc = blas_fill_hash(op, op->prec, op->scratch, 12345u, s);
     if (rc) return rc;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     const int vrs[3] = {1, 2, 4}, minbs[5] = {1, 2, 3, 4, 6};
+    float times[3][5];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 5; ++b) times[a][b] = 1e30f;
+    const int saved_vr = op->vr, saved_mb = op->minb;
+    // three interleaved rounds, best time per variant, so that a clock or
+    // neighbour transient does not decide the choice
+    for (int round = 0; round < 3 && !rc; ++round)
+        for (int a = 0; a < 3 && !rc; ++a)
+            for (int b = 0; b < 5 && !rc; ++b) {
+                if (!variant_compiled(op->nc, vrs[a], minbs[b]) || op->nv % vrs[a]) continue;
+                op->vr = vrs[a];
+                op->minb = minbs[b];
+                rc = op_apply(op, op->scratch, op->stage_out, m0, +1, s);
+                const int reps = 5;
+                cudaEventRecord(e0, s);
+                for (int r = 0; r < reps && !rc; ++r) rc = op_apply(op, op->scratch, op->stage_out, m0, +1, s);
+                cudaEventRecord(e1, s);
+                if (!rc) rc = cuda_check(cudaEventSynchronize(e1), "autotune sync");
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ms /= reps;
+                if (ms < times[a][b]) times[a][b] = ms;
+            }
     float best = 1e30f;
     int bvr = 0, bmb = 0;
-    const int saved_vr = op->vr, saved_mb = op->minb;
-    for (int a = 0; a < 3 && !rc; ++a)
-        for (int b = 0; b < 5 && !rc; ++b) {
-            if (!variant_compiled(op->nc, vrs[a], minbs[b]) || op->nv % vrs[a]) continue;
-            op->vr = vrs[a];
-            op->minb = minbs[b];
-            for (int w = 0; w < 2 && !rc; ++w) rc = op_apply(op, op->scratch, op->stage_out, m0, +1, s);
-            const int reps = 5;
-            cudaEventRecord(e0, s);
-            for (int r = 0; r < reps && !rc; ++r) rc = op_apply(op, op->scratch, op->stage_out, m0, +1, s);
-            cudaEventRecord(e1, s);
-            if (!rc) rc = cuda_check(cudaEventSynchronize(e1), "autotune sync");
-            float ms = 0;
-            cudaEventElapsedTime(&ms, e0, e1);
-            ms /= reps;
-            if (!rc && ms < best) {
-                best = ms;
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 5; ++b)
+            if (times[a][b] < best) {
+                best = times[a][b];
                 bvr = vrs[a];
                 bmb = minbs[b];
             }
-        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc || !bvr) {

@@ -144,6 +144,7 @@ int blas_axpy(const dirac_op *op, dirac_prec p, const double *alpha, const void 
 int blas_axpby(const dirac_op *op, dirac_prec p, void *z, const void *x, const double *a_coef, double as,
                const void *y, const double *b_coef, double bs, double *norm_out, cudaStream_t s);
 int blas_gamma5(const dirac_op *op, dirac_prec p, void *v, cudaStream_t s);
+int blas_fill_hash(const dirac_op *op, dirac_prec p, void *v, unsigned seed, cudaStream_t s);
 int blas_convert(const dirac_op *op, const void *src, dirac_prec sp, void *dst, dirac_prec dp, cudaStream_t s);
 
 // operator handle helpers (capi.cu)

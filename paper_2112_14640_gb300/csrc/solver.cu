@@ -392,11 +392,11 @@ static int mixed_solve(const dirac_op *op, const void *b, void *x, double m0, co
     TRY(get_ws(lo, wl));
     const int nv = op->nv;
     const dirac_prec ph = op->prec, pl = lo->prec;
-    const bool cg = prm->solver == DIRAC_CG_NORMAL;
+    const bool cg = prm->solver != DIRAC_BICGSTAB;
     void *rhs = wh.v[5], *r = wh.v[6], *tmp = wh.v[7];
     void *rl = wl.v[5], *el = wl.v[6];
     // rhs = D^dag b (CG on normal equations) or b
-    if (cg) TRY(op_apply(op, b, rhs, m0, -1, s));
+    if (prm->solver == DIRAC_CG_NORMAL) TRY(op_apply(op, b, rhs, m0, -1, s));
     else TRY(blas_axpby(op, ph, rhs, b, nullptr, 1.0, nullptr, nullptr, 0.0, nullptr, s));
     double nb[kNS], rr[kNS], act[kNS];
     TRY(blas_norm2(op, ph, rhs, wh.nb, s));
@@ -465,6 +465,8 @@ static int plain_solve(const dirac_op *op, const void *b, void *x, double m0, co
         void *rhs = w.v[5];
         TRY(op_apply(op, b, rhs, m0, -1, s));
         TRY(cg_core(op, rhs, x, m0, prm->tol, prm->maxit, every, co, s));
+    } else if (prm->solver == DIRAC_CG_HPD) {
+        TRY(cg_core(op, b, x, m0, prm->tol, prm->maxit, every, co, s));
     } else {
         TRY(bicgstab_core(op, b, x, m0, prm->tol, prm->maxit, every, co, s));
     }
@@ -492,10 +494,11 @@ int solve(const dirac_op *op, const void *b, void *x, double m0, const dirac_sol
     if (prm->inner_prec == op->prec) rc = plain_solve(op, b, x, m0, prm, &st, s);
     else rc = mixed_solve(op, b, x, m0, prm, &st, s);
     if (rc) return rc;
-    // true residual ||b - D x|| / ||b|| in the operator precision
+    // true residual ||b - D x|| / ||b|| (||b - D^dag D x|| / ||b|| for CG_HPD)
     Ws w;
     TRY(get_ws(op, w));
-    TRY(op_apply(op, x, w.v[7], m0, +1, s));
+    if (prm->solver == DIRAC_CG_HPD) TRY(op_apply_normal(op, x, w.v[7], m0, s));
+    else TRY(op_apply(op, x, w.v[7], m0, +1, s));
     TRY(blas_axpby(op, op->prec, w.v[6], b, nullptr, 1.0, w.v[7], nullptr, -1.0, w.rr, s));
     TRY(blas_norm2(op, op->prec, b, w.nb, s));
     double rr[kNS], nb[kNS];
@@ -513,7 +516,8 @@ extern "C" int dirac_solve(const dirac_op *op, const void *b, void *x, double m0
                            dirac_solve_stats *stats, void *stream) {
     if (!op || !params || !b || !x) return DIRAC_ERR_INVALID_ARG;
     if (((uintptr_t)b & 15) || ((uintptr_t)x & 15)) return DIRAC_ERR_ALIGNMENT;
-    if (params->solver != DIRAC_CG_NORMAL && params->solver != DIRAC_BICGSTAB) return DIRAC_ERR_INVALID_ARG;
+    if (params->solver != DIRAC_CG_NORMAL && params->solver != DIRAC_BICGSTAB && params->solver != DIRAC_CG_HPD)
+        return DIRAC_ERR_INVALID_ARG;
     if (params->inner_prec < DIRAC_F64 || params->inner_prec > DIRAC_F16) return DIRAC_ERR_UNSUPPORTED_PREC;
     if (!(params->tol > 0) || params->maxit < 1) return DIRAC_ERR_INVALID_ARG;
     return dgb::solve(op, b, x, m0, params, stats, (cudaStream_t)stream);

@@ -21,7 +21,8 @@ from . import build as _build
 
 WILSON, BRILLOUIN, STAGGERED = 0, 1, 2
 F64, F32, BF16, F16 = 0, 1, 2, 3
-CG_NORMAL, BICGSTAB = 0, 1
+CG_NORMAL, BICGSTAB, CG_HPD = 0, 1, 2
+FORCE_TA, FORCE_GRAD = 0, 1
 PREC_NAMES = {F64: "f64", F32: "f32", BF16: "bf16", F16: "f16"}
 KIND_NAMES = {WILSON: "wilson", BRILLOUIN: "brillouin", STAGGERED: "staggered"}
 _TORCH_DTYPE = {F64: torch.complex128, F32: torch.complex64, BF16: torch.bfloat16, F16: torch.float16}
@@ -73,6 +74,7 @@ SIGNATURES = {
     "dirac_vec_convert": (_I, [_P, _P, _I, _P, _I, _P]),
     "dirac_vec_norm2_noalloc": (_I, [_P, _I, ctypes.c_longlong, _I, _P, _P]),
     "dirac_solve": (_I, [_P, _P, _P, _D, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats), _P]),
+    "dirac_force_wilson": (_I, [_P, _P, _P, _P, _I, _P]),
     "dirac_error_string": (ctypes.c_char_p, [_I]),
     "dirac_flops_per_site": (ctypes.c_long, [_I, _I]),
     "dirac_version": (_I, []),
@@ -281,6 +283,15 @@ class DiracOp:
         _check(lib().dirac_vec_convert(self._h, _ptr(src.contiguous()), int(src_prec), _ptr(dst), int(dst_prec),
                                        _stream(stream)), "dirac_vec_convert")
         return dst
+
+    def force(self, psi, chi, mode=FORCE_TA, stream=None):
+        """Link derivative of S = sum Re phi^dag (D^dag D)^-1 phi (Wilson only):
+        (Nt, Nz, Ny, Nx, 4, Nc, Nc) complex, from psi = (D^dag D)^-1 phi, chi = D psi."""
+        nx, ny, nz, nt = self.dims
+        out = torch.empty((nt, nz, ny, nx, 4, self.nc, self.nc), dtype=_TORCH_DTYPE[self.prec], device=self.device)
+        _check(lib().dirac_force_wilson(self._h, self._vec(psi, "psi"), self._vec(chi, "chi"), _ptr(out), int(mode),
+                                        _stream(stream)), "dirac_force_wilson")
+        return out
 
     # ---------------------------------------------------------------- solve
     def solve(self, b, x=None, m0=0.0, solver=CG_NORMAL, tol=1e-10, maxit=10000, inner_prec=None,

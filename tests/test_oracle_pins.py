@@ -360,3 +360,54 @@ def test_flop_counts_app_e():
     assert O.flops_per_site(O.WILSON, 3) == 1368
     assert O.flops_per_site(O.BRILLOUIN, 3) == 30168
     assert O.flops_per_site(O.STAGGERED, 3) == 582
+
+
+# ------------------------------------------------------------- fermion force
+
+def _expm_ah(X):
+    """exp of anti-hermitian matrices via eigendecomposition of the Hermitian -iX."""
+    w, v = np.linalg.eigh(-1j * X)
+    return np.einsum("...ij,...j,...kj->...ik", v, np.exp(1j * w), v.conj())
+
+
+@pytest.mark.parametrize("bc", [(1, 1, 1, 1), (1, 1, 1, -1)])
+def test_force_matches_finite_differences(bc):
+    """dS/deps along U -> exp(eps X) U equals Re sum tr[X F] (central differences,
+    eps = 1e-4, FP64 solves to 1e-13) for random su(3) directions X."""
+    dims = (4, 2, 2, 4)
+    m0 = 0.3
+    U = I.gauge_field(dims, 3, 0.4, seed=101)
+    phi = I.source(dims, 3, 2, seed=102)
+    op = O.Operator(O.WILSON, U, bc, m0)
+    S0, psi = O.pseudofermion_action(op, phi)
+    F = O.wilson_force(op, psi, op.apply(psi))
+    assert np.allclose(F, -np.conj(np.swapaxes(F, -1, -2)), atol=1e-14)
+    assert np.abs(np.trace(F, axis1=-2, axis2=-1)).max() < 1e-13
+    eps = 1e-4
+    for seed in range(4):
+        X = I.su_n_direction(dims, 3, seed=200 + seed)
+        Sp, _ = O.pseudofermion_action(O.Operator(O.WILSON, _expm_ah(eps * X) @ U, bc, m0), phi)
+        Sm, _ = O.pseudofermion_action(O.Operator(O.WILSON, _expm_ah(-eps * X) @ U, bc, m0), phi)
+        fd = (Sp - Sm) / (2 * eps)
+        an = np.sum(np.real(np.einsum("...ab,...ba->...", X, F)))
+        assert abs(fd - an) < 1e-6 * max(abs(an), 1.0), (seed, fd, an)
+
+
+def test_action_gradient_matches_finite_differences():
+    """The complex gradient G (dS = Re sum conj(G) dU) against central differences
+    along an arbitrary complex perturbation dU (off the group manifold too)."""
+    dims = (2, 2, 2, 4)
+    m0, bc = 0.4, (1, 1, 1, -1)
+    U = I.gauge_field(dims, 3, 0.4, seed=111)
+    phi = I.source(dims, 3, 1, seed=112)
+    op = O.Operator(O.WILSON, U, bc, m0)
+    S0, psi = O.pseudofermion_action(op, phi)
+    G = O.wilson_action_gradient(op, psi, op.apply(psi))
+    rng = np.random.default_rng(5)
+    dU = rng.standard_normal(U.shape) + 1j * rng.standard_normal(U.shape)
+    eps = 1e-5
+    Sp, _ = O.pseudofermion_action(O.Operator(O.WILSON, U + eps * dU, bc, m0), phi)
+    Sm, _ = O.pseudofermion_action(O.Operator(O.WILSON, U - eps * dU, bc, m0), phi)
+    fd = (Sp - Sm) / (2 * eps)
+    an = float(np.sum(np.real(np.conj(G) * dU)))
+    assert abs(fd - an) < 1e-6 * abs(an)
