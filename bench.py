@@ -54,6 +54,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-sweep", action="store_true")
     p.add_argument("--solve", action="store_true", help="add the config-3 mixed-precision solver comparison")
+    p.add_argument("--batch", action="store_true", help="add the config-4 batched-solve measurement")
     p.add_argument("--ncu", action="store_true", help="short run for profiler launch lists (no extras)")
     p.add_argument("--ops", default="wilson,brillouin,staggered",
                    help="profiling only: subset of operators to create and time")
@@ -242,12 +243,35 @@ def main():
     kinds = tuple(names[o] for o in args.ops.split(","))
     sources = {k: I.source(DIMS, NC, NV, 4321 + k, staggered=(k == D.STAGGERED)) for k in kinds}
     ops, xs, ys = {}, {}, {}
-    launch = {}
+    launch, layout_ms = {}, {}
+    stream0 = torch.cuda.current_stream()
+
+    def quick_ms(op, x, y, m0, reps=20):
+        for _ in range(3):
+            op.apply(x, y, m0=m0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream0)
+        for _ in range(reps):
+            op.apply(x, y, m0=m0)
+        e1.record(stream0)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps
+
     for k in kinds:
-        ops[k] = D.DiracOp(k, U, NV, BC, D.F32)
-        xs[k] = ops[k].to_prec(torch.from_numpy(sources[k]).cuda())
-        ys[k] = ops[k].new_vector(zero=False)
-        ops[k].autotune(MASS[k])          # untimed setup: pick the launch variant
+        # untimed setup: for each vector layout pick the launch variant, then
+        # keep the faster layout for the timed step
+        cand = {}
+        for lay in (D.SITE_OUTER, D.SITE_INNER):
+            op = D.DiracOp(k, U, NV, BC, D.F32, layout=lay)
+            x = op.to_prec(op.from_site_outer(torch.from_numpy(sources[k]).cuda()))
+            y = op.new_vector(zero=False)
+            op.autotune(MASS[k])
+            cand[lay] = (quick_ms(op, x, y, MASS[k]), op, x, y)
+        best = min(cand, key=lambda l: cand[l][0])
+        layout_ms[D.KIND_NAMES[k]] = {"site_outer_ms": cand[D.SITE_OUTER][0], "site_inner_ms": cand[D.SITE_INNER][0],
+                                      "chosen": "site_inner" if best == D.SITE_INNER else "site_outer"}
+        _, ops[k], xs[k], ys[k] = cand[best]
+        cand[1 - best][1].close()
         launch[D.KIND_NAMES[k]] = ops[k].get_launch()
     V = int(np.prod(DIMS))
     flop = {k: D.flops_per_site(k, NC) * V * NV for k in kinds}
@@ -330,7 +354,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_dict(),
             "gpu_launches": K * len(kinds), "roofline": roof, "rooflines": rooflines, "per_op": per_op,
-            "clocks": clk, "peaks_source": pk["source"], "launch_variants": launch}
+            "clocks": clk, "peaks_source": pk["source"], "launch_variants": launch, "layouts": layout_ms}
 
     if not args.ncu:
         # end to end through the C ABI from pinned host memory, copies included
@@ -353,7 +377,8 @@ def main():
         for nv in (1, 4, 12, 24):
             row = {}
             for k in kinds:
-                op = D.DiracOp(k, U, nv, BC, D.F32)
+                op = D.DiracOp(k, U, nv, BC, D.F32, layout=ops[k].layout)
+                op.autotune(MASS[k])
                 x = op.new_vector()
                 x.real.normal_()
                 y = op.new_vector(zero=False)
@@ -375,6 +400,8 @@ def main():
 
     if args.solve:
         line["solve"] = solver_comparison(D, I, torch)
+    if args.batch:
+        line["batch"] = batch_measurement(D, I, torch)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.ncu:
         rate, sample = oracle_rate(6.0, U_np, sources)
@@ -386,24 +413,93 @@ def main():
         torch.distributed.destroy_process_group()
 
 
+def batch_measurement(D, I, torch, nsolves=64, seed=2026):
+    """64 independent Wilson/staggered CG solves (FP32, tol 1e-6) of random
+    lattice size in {8^4, 12^4, 16^3x32, 24^3x48} and N_v ~ U{1..24} as one
+    graph-captured batch: solves/s and per-solve latency p50/p99 from the
+    device completion stamps."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    sizes = [(8, 8, 8, 8), (12, 12, 12, 12), (16, 16, 16, 32), (24, 24, 24, 48)]
+    ops, bs, m0s, desc = [], [], [], []
+    fields = {}
+    for i in range(nsolves):
+        kind = D.WILSON if rng.integers(2) == 0 else D.STAGGERED
+        dims = sizes[rng.integers(len(sizes))]
+        nv = int(rng.integers(1, 25))
+        if dims not in fields:
+            fields[dims] = torch.from_numpy(I.gauge_field(dims, NC, 0.4, 500 + len(fields))).cuda()
+        op = D.DiracOp(kind, fields[dims], nv, BC, D.F32)
+        op.autotune(MASS[kind])
+        ops.append(op)
+        bs.append(op.to_prec(torch.from_numpy(I.source(dims, NC, nv, 600 + i, staggered=(kind == D.STAGGERED))).cuda()))
+        m0s.append(0.1 if kind == D.WILSON else 0.05)
+        desc.append((D.KIND_NAMES[kind], "x".join(map(str, dims)), nv))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    xs, stats, rc = D.solve_batched(ops, bs, m0s=m0s, solver=D.CG_NORMAL, tol=1e-6, maxit=20000)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    lat = sorted(s["seconds"] for s in stats)
+    res = {"nsolves": nsolves, "rc": rc, "wall_s": wall, "solves_per_s": nsolves / wall,
+           "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
+           "iters_total": int(sum(s["iters"] for s in stats)),
+           "all_converged": all(s["status"] == 0 for s in stats),
+           "rhs_total": int(sum(d[2] for d in desc))}
+    for op in ops:
+        op.close()
+    return res
+
+
+def tune_mass(D, op32, b32, kind, target=1e6, iters=600):
+    """Bare mass giving cond(D^dag D) ~ target, from Lanczos estimates of a
+    short FP32 CG (App. F "cond").  Staggered: cond ~ lambda_max / m^2.
+    Wilson: bisection on m0 for lambda_min = lambda_max / target."""
+    def est(m):
+        _, st = op32.solve(b32, m0=m, solver=D.CG_HPD, tol=1e-30, maxit=iters, recompute_every=100000)
+        return min(st["lambda_min"]), max(st["lambda_max"])
+    if kind == D.STAGGERED:
+        lo, hi = est(0.05)
+        return (hi / target) ** 0.5, {"lambda_max": hi}
+    lo_m, hi_m = -2.5, 0.5
+    for _ in range(10):
+        m = 0.5 * (lo_m + hi_m)
+        lmin, lmax = est(m)
+        if lmin * target > lmax:
+            hi_m = m     # too well conditioned: move toward the critical mass
+        else:
+            lo_m = m
+    m = hi_m
+    lmin, lmax = est(m)
+    return m, {"lambda_min": lmin, "lambda_max": lmax, "cond_est": lmax / max(lmin, 1e-300)}
+
+
 def solver_comparison(D, I, torch):
-    """Time to 1e-10 of defect-correction CG on D^dag D (32^3x64, Nv=12):
-    FP64 outer with FP32 inner vs BF16/FP16 inner."""
+    """Time to an FP64 residual of 1e-10 of mixed-precision CG on D^dag D
+    (32^3x64, Nc=3, Nv=12, eps=0.6, mass tuned to cond ~1e6): the FP32
+    sloppy iteration (the baseline) against BF16 and FP16 sloppy iterations,
+    reliable updates in FP64."""
     dims = (32, 32, 32, 64)
     out = {}
     U = torch.from_numpy(I.gauge_field(dims, NC, 0.6, 99)).cuda()
-    for kind, m0 in ((D.WILSON, -0.5), (D.STAGGERED, 0.01)):
+    for kind in (D.STAGGERED, D.WILSON):
         op = D.DiracOp(kind, U, NV, BC, D.F64)
-        b = op.to_prec(torch.from_numpy(I.source(dims, NC, NV, 5, staggered=(kind == D.STAGGERED))).cuda())
-        row = {}
+        op32 = D.DiracOp(kind, U, NV, BC, D.F32)
+        src = torch.from_numpy(I.source(dims, NC, NV, 5, staggered=(kind == D.STAGGERED))).cuda()
+        m0, info = tune_mass(D, op32, op32.to_prec(src), kind)
+        op32.close()
+        b = op.to_prec(src)
+        row = {"m0": m0, "tuning": info}
         for inner in (D.F32, D.BF16, D.F16):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            x, st = op.solve(b, m0=m0, tol=1e-10, maxit=200000, inner_prec=inner)
+            x, st = op.solve(b, m0=m0, solver=D.CG_NORMAL, tol=1e-10, maxit=100000, inner_prec=inner)
             torch.cuda.synchronize()
             row[D.PREC_NAMES[inner]] = {"seconds": time.perf_counter() - t0, "iters": st["iters"],
-                                        "outer": st["outer_iters"], "status": st["status"],
-                                        "max_true_relres": max(st["true_relres"]), "max_relres": max(st["relres"])}
+                                        "updates": st["outer_iters"], "status": st["status"],
+                                        "max_relres": max(st["relres"]), "max_true_relres": max(st["true_relres"]),
+                                        "cond_lanczos": max(st["lambda_max"]) / max(min(st["lambda_min"]), 1e-300)}
+            del x
         out[D.KIND_NAMES[kind]] = row
         op.close()
     return out

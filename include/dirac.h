@@ -74,7 +74,20 @@ typedef struct {
     int nv;
     int bc[4];
     dirac_prec prec;
+    int layout;        /* vector layout, DIRAC_LAYOUT_* below (0 = the paper's) */
 } dirac_geom;
+
+/* Vector layouts (the RHS index v is innermost in both, so the BLAS-1 calls
+ * treat every vector as a [rows][N_v] array):
+ *   SITE_OUTER  Wilson-type [site][colour][spin][v], staggered [site][colour][v]
+ *               -- the paper's NvNsNc / NvNc orders (Sec. 2);
+ *   SITE_INNER  Wilson-type [colour][spin][site][v], staggered [colour][site][v]
+ *               -- the site index moved inside the internal dofs, so that the
+ *               threads of a warp, which cover consecutive sites, read one
+ *               contiguous run per (colour, spin) component.
+ * The gauge field handed to dirac_op_create is always [site][mu][a][b]; the
+ * operator stores its own copy in the order that matches the layout. */
+enum { DIRAC_LAYOUT_SITE_OUTER = 0, DIRAC_LAYOUT_SITE_INNER = 1 };
 
 typedef struct dirac_op dirac_op;   /* opaque */
 
@@ -92,7 +105,8 @@ int dirac_op_create(dirac_kind kind, const dirac_geom *geom, const void *U,
 int dirac_op_update_links(dirac_op *op, const void *U, dirac_prec u_prec, void *stream);
 
 /* Copy the operator's stored W links (Brillouin only) into w_out, layout
- * [site][80][a][b] in geom->prec, directions s = (sx,sy,sz,st) in {-1,0,1}^4
+ * [site][80][a][b] (SITE_OUTER) or [80][a][b][site] (SITE_INNER) in
+ * geom->prec, directions s = (sx,sy,sz,st) in {-1,0,1}^4
  * numbered d = (st+1)*27+(sz+1)*9+(sy+1)*3+(sx+1) with the centre d = 40
  * left out (index d for d < 40, d-1 for d > 40). */
 int dirac_op_copy_w(const dirac_op *op, void *w_out, void *stream);
@@ -189,12 +203,25 @@ typedef struct {
     double tol;            /* relative residual: ||r_N||/||D^dag b|| (CG) or ||b-Dx||/||b|| */
     int maxit;             /* total iteration limit (inner iterations for mixed solves) */
     dirac_prec inner_prec; /* == op precision: plain Krylov solve in that precision;
-                              lower precision: defect correction (Sec. 9 "mp" solvers)
-                              with the outer residual, norms and update in the
-                              operator's precision and inner solves in inner_prec */
-    double inner_tol;      /* relative tolerance of each inner solve (0 = default) */
+                              lower precision: mixed-precision solve (Sec. 9 "mp"
+                              solvers) with residual, norms, convergence test and
+                              solution in the operator's precision and the Krylov
+                              iterations in inner_prec */
+    double inner_tol;      /* restarted mode: relative tolerance of each inner solve (0 = default) */
     int recompute_every;   /* 0 = paper default: 50 for F64 solves, 20 otherwise */
+    int mixed_mode;        /* DIRAC_MIXED_RELIABLE (CG only) or DIRAC_MIXED_RESTART */
+    double delta;          /* reliable updates: recompute when the sloppy residual fell by
+                              this factor since the last update (0 = default 0.1) */
 } dirac_solve_params;
+
+/* Mixed-precision strategies.  RESTART: defect correction, the paper's "mp"
+ * driver (Sec. 9): r = b - A x in the operator precision, an inner solve of
+ * A e = r/|r| from zero in inner_prec, x += |r| e, repeat.  RELIABLE (CG):
+ * one Krylov iteration in inner_prec on the scaled residual, with the
+ * solution and the true residual refreshed in the operator precision each
+ * time the iterated residual has dropped by delta; the search direction is
+ * kept across refreshes.  BiCGstab always uses RESTART. */
+enum { DIRAC_MIXED_RELIABLE = 0, DIRAC_MIXED_RESTART = 1 };
 
 typedef struct {
     int iters;                 /* Krylov iterations (summed over inner solves) */
@@ -205,6 +232,8 @@ typedef struct {
     double relres[64];         /* final recomputed residual, per RHS */
     double true_relres[64];    /* ||b - D x|| / ||b|| per RHS */
     double seconds;            /* wall time of the call */
+    double lambda_min[64];     /* CG only: Lanczos estimates of the extreme eigenvalues */
+    double lambda_max[64];     /* of D^dag D from the CG coefficients (App. F "cond"); 0 otherwise */
 } dirac_solve_stats;
 
 /* Solve for N_v right-hand sides b (operator precision); x holds the initial
@@ -212,6 +241,23 @@ typedef struct {
  * per-iteration residual norms on the host).  stats may be NULL. */
 int dirac_solve(const dirac_op *op, const void *b, void *x, double m0,
                 const dirac_solve_params *params, dirac_solve_stats *stats, void *stream);
+
+/* Many independent solves at once (the paper's solvers, Sec. 9, grown into a
+ * batch): solve i is CG on D_i^dag D_i x_i = D_i^dag b_i (DIRAC_CG_NORMAL) or
+ * D_i^dag D_i x_i = b_i (DIRAC_CG_HPD) with operator ops[i] (distinct
+ * handles: each solve uses its operator's workspace; any lattice, N_v and
+ * kind), mass m0[i] (host array) and the shared tolerance and iteration
+ * limit of params (inner_prec must equal every operator's precision).
+ * Coefficients and convergence masks stay on the device; segments of
+ * recompute_every (default 20) iterations followed by a true-residual
+ * recompute run for all solves as one CUDA graph, replayed until every solve
+ * has converged.  stats (host array of nsolves, may be NULL) receive per-solve
+ * iterations (segment granularity), final residuals and the device-timed
+ * seconds from the batch start to that solve's completion.  Blocks until done.
+ * Returns 0 when all converged, DIRAC_NOT_CONVERGED otherwise. */
+int dirac_solve_batched(int nsolves, dirac_op *const *ops, const void *const *b, void *const *x,
+                        const double *m0, const dirac_solve_params *params, dirac_solve_stats *stats,
+                        void *stream);
 
 /* ------------------------------------------------------------ fermion force
  * Derivative of S = sum_v Re phi_v^dag (D_W^dag D_W)^-1 phi_v with respect to

@@ -118,17 +118,18 @@ __global__ void axpby_kernel(E *z, const E *x, const E *y, const double *__restr
 }
 
 template <typename E>
-__global__ void gamma5_kernel(E *__restrict__ v, Lat g, int nc, int staggered) {
+__global__ void gamma5_kernel(E *__restrict__ v, Lat g, int nc, int staggered, int layout) {
     const long long rows = staggered ? g.V * nc : g.V * nc * 4;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= rows * g.nv) return;
-    const long long row = i / g.nv;
+    const long long row = i / g.nv;   // (site, cs) site-outer or (cs, site) site-inner
     bool neg;
     if (staggered) {
-        const Coord c = site_coords(g, row / nc);
+        const Coord c = site_coords(g, layout == 0 ? row / nc : row % g.V);
         neg = (c.x + c.y + c.z + c.t) & 1;        // epsilon(n) = (-1)^(x+y+z+t)
     } else {
-        neg = (row % 4) >= 2;                    // gamma5 = diag(1, 1, -1, -1)
+        const long long spin = layout == 0 ? row % 4 : (row / g.V) % 4;
+        neg = spin >= 2;                          // gamma5 = diag(1, 1, -1, -1)
     }
     if (neg) {
         using A = typename Acc<E>::T;
@@ -211,7 +212,8 @@ int blas_gamma5(const dirac_op *op, dirac_prec p, void *v, cudaStream_t s) {
     return dispatch_prec(p, [&](auto tag) {
         using E = std::remove_pointer_t<decltype(tag)>;
         const long long n = op->rows * op->nv;
-        gamma5_kernel<E><<<grid_for(n, 256), 256, 0, s>>>((E *)v, op->lat, op->nc, op->kind == DIRAC_STAGGERED);
+        gamma5_kernel<E><<<grid_for(n, 256), 256, 0, s>>>((E *)v, op->lat, op->nc, op->kind == DIRAC_STAGGERED,
+                                                          op->geom.layout);
         return launch_check("gamma5_kernel");
     });
 }

@@ -21,8 +21,8 @@
 
 namespace dgb {
 
-template <int NC, int VR, typename E, int MINB>
-__global__ void __launch_bounds__(kStencilBlock, MINB) brillouin_kernel(const E *__restrict__ W, const E *__restrict__ in,
+template <int NC, int VR, typename E, int MINB, int LAYOUT>
+__global__ void __launch_bounds__(kStencilBlock, (MINB > 1 ? MINB : 0)) brillouin_kernel(const E *__restrict__ W, const E *__restrict__ in,
                                                         E *__restrict__ out, Lat g, typename Acc<E>::T centre,
                                                         typename Acc<E>::T sgn) {
     using A = typename Acc<E>::T;
@@ -32,7 +32,8 @@ __global__ void __launch_bounds__(kStencilBlock, MINB) brillouin_kernel(const E 
     const long long n = tid / nchunk;
     const int j = (int)(tid - n * nchunk);
     const Coord c = site_coords(g, n);
-    const long long site_cx = (long long)NC * 4 * g.nv;
+    using L = Layout<LAYOUT>;
+    const long long cs = L::cs_stride(g), ws = L::mat_stride(g);
 
     cx<A> acc[NC][4][VR];
 #pragma unroll
@@ -46,7 +47,6 @@ __global__ void __launch_bounds__(kStencilBlock, MINB) brillouin_kernel(const E 
     const int ys[3] = {c.y == 0 ? g.ny - 1 : c.y - 1, c.y, c.y == g.ny - 1 ? 0 : c.y + 1};
     const int zs[3] = {c.z == 0 ? g.nz - 1 : c.z - 1, c.z, c.z == g.nz - 1 ? 0 : c.z + 1};
     const int ts[3] = {c.t == 0 ? g.nt - 1 : c.t - 1, c.t, c.t == g.nt - 1 ? 0 : c.t + 1};
-    const E *wsite = W + 2 * (n * 80 * NC * NC);
 
     for (int it = 0; it < 3; ++it) {
         for (int iz = 0; iz < 3; ++iz) {
@@ -70,14 +70,14 @@ __global__ void __launch_bounds__(kStencilBlock, MINB) brillouin_kernel(const E 
                     const A ml = -l;
 
                     cx<A> Wm[NC][NC];
-                    load_mat<NC, E, A>(wsite + 2 * (dirp * NC * NC), Wm);
+                    load_mat_s<NC, E, A>(W + 2 * L::template mat<NC>(g, n, 80, dirp), ws, Wm);
                     const long long m = tzy * g.nx + xs[ix];
-                    const E *pm = in + 2 * (m * site_cx + (long long)j * VR);
+                    const E *pm = in + 2 * (L::vec(g, m, NC * 4, 0) + (long long)j * VR);
 #pragma unroll
                     for (int kc = 0; kc < NC; ++kc) {
                         cx<A> p[4][VR];
 #pragma unroll
-                        for (int s = 0; s < 4; ++s) load_cx<E, VR, A>(pm + 2 * (long long)((kc * 4 + s) * g.nv), p[s]);
+                        for (int s = 0; s < 4; ++s) load_cx<E, VR, A>(pm + 2 * (kc * 4 + s) * cs, p[s]);
 #pragma unroll
                         for (int v = 0; v < VR; ++v) {
                             cx<A> f0 = ml * p[0][v], f1 = ml * p[1][v], f2 = ml * p[2][v], f3 = ml * p[3][v];
@@ -103,13 +103,13 @@ __global__ void __launch_bounds__(kStencilBlock, MINB) brillouin_kernel(const E 
         }
     }
 
-    const long long base = 2 * (n * site_cx + (long long)j * VR);
+    const long long base = 2 * (L::vec(g, n, NC * 4, 0) + (long long)j * VR);
 #pragma unroll
     for (int a = 0; a < NC; ++a)
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
             cx<A> p[VR], o[VR];
-            const long long off = base + 2LL * (a * 4 + s) * g.nv;
+            const long long off = base + 2LL * (a * 4 + s) * cs;
             load_cx<E, VR, A>(in + off, p);
 #pragma unroll
             for (int v = 0; v < VR; ++v) {
@@ -129,14 +129,17 @@ int launch_brillouin_t(const dirac_op *op, const void *in, void *out, double m0,
         constexpr int NC = decltype(ncc)::value;
         return dispatch_vr(vr, [&](auto vrc) {
             constexpr int VR = decltype(vrc)::value;
-            return dispatch_minb(NC, minb, [&](auto mbc) {
+            return dispatch_minb<NC>(minb, [&](auto mbc) {
             constexpr int MINB = decltype(mbc)::value;
-            const long long threads = op->V * (op->nv / VR);
-            const int block = kStencilBlock;
-            // m0 - lambda_0 / 2 = m0 + 240/128
-            brillouin_kernel<NC, VR, E, MINB><<<grid_for(threads, block), block, 0, s>>>(
-                (const E *)op->w, (const E *)in, (E *)out, op->lat, (A)(m0 + 240.0 / 128.0), (A)sgn);
-            return launch_check("brillouin_kernel");
+            return dispatch_layout(op->geom.layout, [&](auto lyc) {
+                constexpr int LAYOUT = decltype(lyc)::value;
+                const long long threads = op->V * (op->nv / VR);
+                const int block = kStencilBlock;
+                // m0 - lambda_0 / 2 = m0 + 240/128
+                brillouin_kernel<NC, VR, E, MINB, LAYOUT><<<grid_for(threads, block), block, 0, s>>>(
+                    (const E *)op->w, (const E *)in, (E *)out, op->lat, (A)(m0 + 240.0 / 128.0), (A)sgn);
+                return launch_check("brillouin_kernel");
+            });
             });
         });
     });

@@ -55,6 +55,7 @@ static int validate_geom(dirac_kind kind, const dirac_geom *g) {
     if (g->nc < 1 || g->nc > 4) return DIRAC_ERR_UNSUPPORTED_NC;
     if (g->nv < 1 || g->nv > 64) return DIRAC_ERR_INVALID_ARG;
     if (g->prec < DIRAC_F64 || g->prec > DIRAC_F16) return DIRAC_ERR_UNSUPPORTED_PREC;
+    if (g->layout != DIRAC_LAYOUT_SITE_OUTER && g->layout != DIRAC_LAYOUT_SITE_INNER) return DIRAC_ERR_INVALID_ARG;
     return DIRAC_OK;
 }
 
@@ -74,7 +75,7 @@ static std::mutex g_tune_mu;
 static std::map<TuneKey, std::pair<int, int>> g_tune;
 
 static TuneKey tune_key(const dirac_op *op) {
-    return TuneKey{(int)op->kind, (int)op->prec, op->nc, op->nv, op->V};
+    return TuneKey{(int)op->kind * 2 + op->geom.layout, (int)op->prec, op->nc, op->nv, op->V};
 }
 
 static void remember_tuning(const dirac_op *op) {
@@ -238,16 +239,16 @@ int dirac_op_autotune(dirac_op *op, double m0, void *stream, double *best_ms) {
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int vrs[3] = {1, 2, 4}, minbs[5] = {1, 2, 3, 4, 6};
-    float times[3][5];
+    const int vrs[3] = {1, 2, 4}, minbs[4] = {1, 3, 4, 6};
+    float times[3][4];
     for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 5; ++b) times[a][b] = 1e30f;
+        for (int b = 0; b < 4; ++b) times[a][b] = 1e30f;
     const int saved_vr = op->vr, saved_mb = op->minb;
     // three interleaved rounds, best time per variant, so that a clock or
     // neighbour transient does not decide the choice
     for (int round = 0; round < 3 && !rc; ++round)
         for (int a = 0; a < 3 && !rc; ++a)
-            for (int b = 0; b < 5 && !rc; ++b) {
+            for (int b = 0; b < 4 && !rc; ++b) {
                 if (!variant_compiled(op->nc, vrs[a], minbs[b]) || op->nv % vrs[a]) continue;
                 op->vr = vrs[a];
                 op->minb = minbs[b];
@@ -265,7 +266,7 @@ int dirac_op_autotune(dirac_op *op, double m0, void *stream, double *best_ms) {
     float best = 1e30f;
     int bvr = 0, bmb = 0;
     for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 5; ++b)
+        for (int b = 0; b < 4; ++b)
             if (times[a][b] < best) {
                 best = times[a][b];
                 bvr = vrs[a];

@@ -187,6 +187,44 @@ __device__ __forceinline__ long long neighbour(const Lat &g, long long n, const 
     return (coord == 0) ? n + (long long)(extent - 1) * stride : n - stride;
 }
 
+// ------------------------------------------------------------- layouts
+// Index arithmetic of the two vector layouts (in complex numbers).  ncs is the
+// number of internal components per site (N_c*4 or N_c), cs one of them.
+//   OUTER: ((site * ncs + cs) * nv + v)      INNER: ((cs * V + site) * nv + v)
+// Links / W matrices, element e of matrix k (k = mu or dir):
+//   OUTER: ((site * nk + k) * NC*NC + e)     INNER: ((k * NC*NC + e) * V + site)
+template <int LAYOUT>
+struct Layout {
+    static __host__ __device__ __forceinline__ long long vec(const Lat &g, long long site, int ncs, int cs) {
+        if constexpr (LAYOUT == 0) return (site * ncs + cs) * (long long)g.nv;
+        else return ((long long)cs * g.V + site) * g.nv;
+    }
+    // distance (in complex numbers) between consecutive components cs of one site
+    static __host__ __device__ __forceinline__ long long cs_stride(const Lat &g) {
+        if constexpr (LAYOUT == 0) return g.nv;
+        else return g.V * g.nv;
+    }
+    template <int NC>
+    static __host__ __device__ __forceinline__ long long mat(const Lat &g, long long site, int nk, int k) {
+        if constexpr (LAYOUT == 0) return (site * nk + k) * (long long)(NC * NC);
+        else return (long long)k * NC * NC * g.V + site;
+    }
+    // distance between consecutive matrix elements
+    static __host__ __device__ __forceinline__ long long mat_stride(const Lat &g) {
+        if constexpr (LAYOUT == 0) return 1;
+        else return g.V;
+    }
+};
+
+// NC x NC matrix whose elements are `stride` complex numbers apart.
+template <int NC, typename E, typename A>
+__device__ __forceinline__ void load_mat_s(const E *__restrict__ p, long long stride, cx<A> (&M)[NC][NC]) {
+#pragma unroll
+    for (int a = 0; a < NC; ++a)
+#pragma unroll
+        for (int b = 0; b < NC; ++b) M[a][b] = ld1<E, A>(p + 2 * stride * (a * NC + b));
+}
+
 // Element type for each storage precision.
 template <int P> struct Elem;
 template <> struct Elem<DIRAC_F64> { using T = double; };

@@ -46,9 +46,10 @@ __device__ __forceinline__ void apply_proj(int mu, A a, const cx<A> p[4], cx<A> 
     }
 }
 
-template <int NC, typename E>
+template <int NC, typename E, int LAYOUT>
 __global__ void force_kernel(const E *__restrict__ U, const E *__restrict__ psi, const E *__restrict__ chi,
                              E *__restrict__ out, Lat g, int bc0, int bc1, int bc2, int bc3, int mode) {
+    using L = Layout<LAYOUT>;
     using A = typename Acc<E>::T;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= g.V * 4) return;
@@ -56,7 +57,7 @@ __global__ void force_kernel(const E *__restrict__ U, const E *__restrict__ psi,
     const int mu = (int)(tid % 4);
     const Coord c = site_coords(g, n);
     const long long m = neighbour(g, n, c, mu, +1);
-    const long long site_cx = (long long)NC * 4 * g.nv;
+    const long long csd = L::cs_stride(g);
     cx<A> B[NC][NC], C[NC][NC];
     for (int a = 0; a < NC; ++a)
         for (int b = 0; b < NC; ++b) B[a][b] = C[a][b] = cx<A>{0, 0};
@@ -65,8 +66,8 @@ __global__ void force_kernel(const E *__restrict__ U, const E *__restrict__ psi,
         for (int a = 0; a < NC; ++a) {
             cx<A> cn[4], cm[4];
             for (int s = 0; s < 4; ++s) {
-                const long long on = 2 * (n * site_cx + (long long)(a * 4 + s) * g.nv + v);
-                const long long om = 2 * (m * site_cx + (long long)(a * 4 + s) * g.nv + v);
+                const long long on = 2 * (L::vec(g, n, NC * 4, 0) + (long long)(a * 4 + s) * csd + v);
+                const long long om = 2 * (L::vec(g, m, NC * 4, 0) + (long long)(a * 4 + s) * csd + v);
                 pn[a][s] = ld1<E, A>(psi + on);
                 pm[a][s] = ld1<E, A>(psi + om);
                 cn[s] = ld1<E, A>(chi + on);
@@ -97,14 +98,14 @@ __global__ void force_kernel(const E *__restrict__ U, const E *__restrict__ psi,
         return;
     }
     // M = U B - C U^dag, U = phased link
-    cx<A> L[NC][NC], M[NC][NC];
-    load_mat<NC, E, A>(U + 2 * (tid * NC * NC), L);
+    cx<A> Lk[NC][NC], M[NC][NC];
+    load_mat_s<NC, E, A>(U + 2 * L::template mat<NC>(g, n, 4, mu), L::mat_stride(g), Lk);
     for (int a = 0; a < NC; ++a)
         for (int b = 0; b < NC; ++b) {
             cx<A> acc = {0, 0};
             for (int k = 0; k < NC; ++k) {
-                cmac(acc, L[a][k], B[k][b]);
-                cmac(acc, C[a][k], cx<A>{-L[b][k].re, L[b][k].im});   // - C U^dag
+                cmac(acc, Lk[a][k], B[k][b]);
+                cmac(acc, C[a][k], cx<A>{-Lk[b][k].re, Lk[b][k].im});   // - C U^dag
             }
             M[a][b] = acc;
         }
@@ -139,11 +140,14 @@ extern "C" int dirac_force_wilson(const dirac_op *op, const void *psi, const voi
         } else {
             return dispatch_nc(op->nc, [&](auto ncc) {
                 constexpr int NC = decltype(ncc)::value;
-                const long long threads = op->V * 4;
-                force_kernel<NC, E><<<grid_for(threads, 128), 128, 0, s>>>(
-                    (const E *)op->links, (const E *)psi, (const E *)chi, (E *)force_out, op->lat, op->geom.bc[0],
-                    op->geom.bc[1], op->geom.bc[2], op->geom.bc[3], mode);
-                return launch_check("force_kernel");
+                return dispatch_layout(op->geom.layout, [&](auto lyc) {
+                    constexpr int LAYOUT = decltype(lyc)::value;
+                    const long long threads = op->V * 4;
+                    force_kernel<NC, E, LAYOUT><<<grid_for(threads, 128), 128, 0, s>>>(
+                        (const E *)op->links, (const E *)psi, (const E *)chi, (E *)force_out, op->lat,
+                        op->geom.bc[0], op->geom.bc[1], op->geom.bc[2], op->geom.bc[3], mode);
+                    return launch_check("force_kernel");
+                });
             });
         }
     });

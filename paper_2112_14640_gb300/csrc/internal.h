@@ -40,6 +40,7 @@ namespace dgb {
 inline int cuda_check(cudaError_t e, const char *what) {
     if (e != cudaSuccess) {
         fprintf(stderr, "libdirac: %s: %s\n", what, cudaGetErrorString(e));
+        cudaGetLastError();   // clear a non-sticky error so it is not blamed on a later call
         return DIRAC_ERR_CUDA;
     }
     return DIRAC_OK;
@@ -89,20 +90,33 @@ int dispatch_vr(int vr, F &&f) {
 }
 
 // Stencil launch variants: VR right-hand sides per thread and a register cap
-// through __launch_bounds__(128, MINB).  Every (VR, MINB) pair below is
+// through __launch_bounds__(128, MINB).  MINB = 1 compiles with the plain
+// __launch_bounds__(128) (the compiler's own register heuristic, which differs
+// from an explicit minimum of one block).  Every (VR, MINB) pair below is
 // compiled for N_c = 3; other N_c have MINB = 1 only.
 constexpr int kStencilBlock = 128;
 inline bool variant_compiled(int nc, int vr, int minb) {
     if (vr != 1 && vr != 2 && vr != 4) return false;
     if (minb == 1) return true;
-    return nc == 3 && (minb == 2 || minb == 3 || minb == 4 || minb == 6);
+    return nc == 3 && (minb == 3 || minb == 4 || minb == 6);
 }
 
 template <typename F>
-int dispatch_minb(int nc, int minb, F &&f) {
-    if (nc != 3 || minb == 1) return f(std::integral_constant<int, 1>{});
+int dispatch_layout(int layout, F &&f) {
+    switch (layout) {
+    case DIRAC_LAYOUT_SITE_OUTER: return f(std::integral_constant<int, 0>{});
+    case DIRAC_LAYOUT_SITE_INNER: return f(std::integral_constant<int, 1>{});
+    }
+    return DIRAC_ERR_INVALID_ARG;
+}
+
+template <int NC, typename F>
+int dispatch_minb(int minb, F &&f) {
+    if constexpr (NC != 3) {
+        return f(std::integral_constant<int, 1>{});
+    }
+    if (minb == 1) return f(std::integral_constant<int, 1>{});
     switch (minb) {
-    case 2: return f(std::integral_constant<int, 2>{});
     case 3: return f(std::integral_constant<int, 3>{});
     case 4: return f(std::integral_constant<int, 4>{});
     case 6: return f(std::integral_constant<int, 6>{});

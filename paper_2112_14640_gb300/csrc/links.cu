@@ -22,7 +22,8 @@ __device__ __forceinline__ cx<double> ld_u(const UE *U, long long idx) {
 }
 
 template <typename UE, typename E>
-__global__ void phase_links_kernel(const UE *__restrict__ U, E *__restrict__ out, Lat g, Phases ph, int nc) {
+__global__ void phase_links_kernel(const UE *__restrict__ U, E *__restrict__ out, Lat g, Phases ph, int nc,
+                                   int layout) {
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;   // (site, mu)
     if (tid >= g.V * 4) return;
     const long long n = tid / 4;
@@ -34,8 +35,10 @@ __global__ void phase_links_kernel(const UE *__restrict__ U, E *__restrict__ out
     const int per = nc * nc;
     for (int e = 0; e < per; ++e) {
         cx<double> u = ld_u(U, tid * per + e);
-        out[2 * (tid * per + e)] = from_acc<E, double>(f * u.re);
-        out[2 * (tid * per + e) + 1] = from_acc<E, double>(f * u.im);
+        // [site][mu][a][b] (site-outer) or [mu][a][b][site] (site-inner)
+        const long long o = layout == 0 ? tid * per + e : ((long long)mu * per + e) * g.V + n;
+        out[2 * o] = from_acc<E, double>(f * u.re);
+        out[2 * o + 1] = from_acc<E, double>(f * u.im);
     }
 }
 
@@ -59,7 +62,8 @@ __device__ __forceinline__ void signed_link(const UE *__restrict__ U, const Lat 
 }
 
 template <int NC, typename UE, typename E>
-__global__ void __launch_bounds__(96) build_w_kernel(const UE *__restrict__ U, E *__restrict__ W, Lat g, Phases ph) {
+__global__ void __launch_bounds__(96) build_w_kernel(const UE *__restrict__ U, E *__restrict__ W, Lat g, Phases ph,
+                                                     int layout) {
     __shared__ cx<double> Ws[81][NC * NC];
     const long long n = blockIdx.x;
     const int dir = threadIdx.x;
@@ -107,10 +111,11 @@ __global__ void __launch_bounds__(96) build_w_kernel(const UE *__restrict__ U, E
     }
     if (dir < 81 && dir != 40) {
         const int dirp = dir < 40 ? dir : dir - 1;
-        E *o = W + 2 * ((n * 80 + dirp) * NC * NC);
         for (int e = 0; e < NC * NC; ++e) {
-            o[2 * e] = from_acc<E, double>(Ws[dir][e].re);
-            o[2 * e + 1] = from_acc<E, double>(Ws[dir][e].im);
+            // [site][dir][a][b] (site-outer) or [dir][a][b][site] (site-inner)
+            const long long o = layout == 0 ? (n * 80 + dirp) * NC * NC + e : ((long long)dirp * NC * NC + e) * g.V + n;
+            W[2 * o] = from_acc<E, double>(Ws[dir][e].re);
+            W[2 * o + 1] = from_acc<E, double>(Ws[dir][e].im);
         }
     }
 }
@@ -135,7 +140,8 @@ int launch_phase_links(dirac_op *op, const void *U, dirac_prec u_prec, cudaStrea
             using E = std::remove_pointer_t<decltype(tag)>;
             const long long threads = op->V * 4;
             phase_links_kernel<UE, E><<<grid_for(threads, 128), 128, 0, s>>>((const UE *)U, (E *)op->links,
-                                                                            op->lat, phases_of(op), op->nc);
+                                                                            op->lat, phases_of(op), op->nc,
+                                                                            op->geom.layout);
             return launch_check("phase_links_kernel");
         });
     });
@@ -149,7 +155,7 @@ int launch_build_w(dirac_op *op, const void *U, dirac_prec u_prec, cudaStream_t 
             return dispatch_nc(op->nc, [&](auto ncc) {
                 constexpr int NC = decltype(ncc)::value;
                 build_w_kernel<NC, UE, E><<<(unsigned)op->V, 96, 0, s>>>((const UE *)U, (E *)op->w, op->lat,
-                                                                       phases_of(op));
+                                                                       phases_of(op), op->geom.layout);
                 return launch_check("build_w_kernel");
             });
         });

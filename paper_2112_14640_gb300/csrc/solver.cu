@@ -20,6 +20,7 @@
 #include <string.h>
 
 #include <chrono>
+#include <vector>
 
 #include "internal.h"
 
@@ -51,6 +52,18 @@ static int get_ws(const dirac_op *op, Ws &w) {
     double **arr[] = {&w.rr, &w.rr_new, &w.pq, &w.alpha, &w.beta, &w.act, &w.nb, &w.c1,
                       &w.c2, &w.c3, &w.omega, &w.rho, &w.rho_new, &w.tt};
     for (size_t i = 0; i < sizeof(arr) / sizeof(arr[0]); ++i) *arr[i] = d + i * kNS * 2;
+    return DIRAC_OK;
+}
+
+// The operator's solver workspace: the first nvecs vectors and the scalar
+// area (arrays of 2*64 doubles in the order rr, rr_new, pq, alpha, beta, act,
+// nb, ...), for drivers in other translation units.
+int solver_ws(const dirac_op *op, void **vecs, int nvecs, double **scal) {
+    Ws w;
+    int rc = get_ws(op, w);
+    if (rc) return rc;
+    for (int i = 0; i < nvecs && i < kWsVecs; ++i) vecs[i] = w.v[i];
+    *scal = w.rr;
     return DIRAC_OK;
 }
 
@@ -135,12 +148,13 @@ __global__ void bicg_omega_kernel(int nv, const double *ts, const double *tt, co
     rho[2 * v + 1] = rho_new[2 * v + 1];
 }
 
-// c[2v] = act ? scale * f(x[v]) : 0 with f = 1/sqrt or sqrt
-__global__ void coef_from_norm_kernel(int nv, const double *rr, const double *act, double *c, int inverse) {
+// c[2v] = act ? f(|x|) : 0 with f(r) = scale / r (inverse) or r / scale
+__global__ void coef_from_norm_kernel(int nv, const double *rr, const double *act, double *c, int inverse,
+                                      double scale = 1.0) {
     const int v = threadIdx.x;
     if (v >= nv) return;
     double r = sqrt(rr[v]);
-    double val = (act[v] != 0.0 && r > 0.0) ? (inverse ? 1.0 / r : r) : 0.0;
+    double val = (act[v] != 0.0 && r > 0.0) ? (inverse ? scale / r : r / scale) : 0.0;
     c[2 * v] = val;
     c[2 * v + 1] = 0.0;
 }
@@ -167,6 +181,67 @@ struct CoreOut {
     double relres[kNS];
 };
 
+// Per-RHS CG coefficient history for the Lanczos estimate of the extreme
+// eigenvalues of A (the "cond" module of App. F): alpha_j = rr_j / <p_j, A p_j>,
+// beta_j = rr_{j+1} / rr_j.
+struct Lanczos {
+    std::vector<double> alpha[kNS], beta[kNS];
+    void add(int nv, const double *act, const double *rr, const double *pq, const double *rn) {
+        for (int v = 0; v < nv; ++v) {
+            if (act[v] == 0.0 || pq[2 * v] <= 0.0 || rr[v] <= 0.0) continue;
+            alpha[v].push_back(rr[v] / pq[2 * v]);
+            beta[v].push_back(rn[v] / rr[v]);
+        }
+    }
+};
+
+// number of eigenvalues below x of the symmetric tridiagonal (d, e) (Sturm count)
+static int sturm_count(const std::vector<double> &d, const std::vector<double> &e, double x) {
+    int cnt = 0;
+    double q = 1.0;
+    for (size_t i = 0; i < d.size(); ++i) {
+        const double off = i ? e[i - 1] * e[i - 1] : 0.0;
+        q = (d[i] - x) - (i ? off / q : 0.0);
+        if (q == 0.0) q = -1e-300;
+        if (q < 0) ++cnt;
+    }
+    return cnt;
+}
+
+// smallest and largest eigenvalue of the Lanczos matrix built from the CG
+// coefficients: diagonal 1/alpha_j + beta_{j-1}/alpha_{j-1}, off-diagonal
+// sqrt(beta_j)/alpha_j; bisection on the Gershgorin interval.
+static void lanczos_extremes(const std::vector<double> &al, const std::vector<double> &be, double &lmin,
+                             double &lmax) {
+    const size_t k = al.size();
+    lmin = lmax = 0.0;
+    if (k == 0) return;
+    std::vector<double> d(k), e(k > 1 ? k - 1 : 0);
+    for (size_t j = 0; j < k; ++j) {
+        d[j] = 1.0 / al[j] + (j ? be[j - 1] / al[j - 1] : 0.0);
+        if (j + 1 < k) e[j] = sqrt(be[j]) / al[j];
+    }
+    double lo = 1e300, hi = -1e300;
+    for (size_t j = 0; j < k; ++j) {
+        const double r = (j ? fabs(e[j - 1]) : 0.0) + (j + 1 < k ? fabs(e[j]) : 0.0);
+        lo = fmin(lo, d[j] - r);
+        hi = fmax(hi, d[j] + r);
+    }
+    double a = lo, b = hi;
+    for (int it = 0; it < 200 && b - a > 1e-15 * fmax(fabs(a), fabs(b)); ++it) {
+        const double m = 0.5 * (a + b);
+        if (sturm_count(d, e, m) >= 1) b = m; else a = m;
+    }
+    lmin = 0.5 * (a + b);
+    a = lo;
+    b = hi;
+    for (int it = 0; it < 200 && b - a > 1e-15 * fmax(fabs(a), fabs(b)); ++it) {
+        const double m = 0.5 * (a + b);
+        if (sturm_count(d, e, m) >= (int)k) b = m; else a = m;
+    }
+    lmax = 0.5 * (a + b);
+}
+
 // A = D^dag D (normal = true) applied through the operator scratch.
 static int apply_A(const dirac_op *op, const void *in, void *out, double m0, cudaStream_t s) {
     return op_apply_normal(op, in, out, m0, s);
@@ -174,7 +249,7 @@ static int apply_A(const dirac_op *op, const void *in, void *out, double m0, cud
 
 // CG on A x = rhs (A = D^dag D), x in/out.  Uses ws vectors 0..2.
 static int cg_core(const dirac_op *op, const void *rhs, void *x, double m0, double tol, int maxit, int every,
-                   CoreOut &out, cudaStream_t s) {
+                   CoreOut &out, cudaStream_t s, Lanczos *lan = nullptr) {
     Ws w;
     TRY(get_ws(op, w));
     const int nv = op->nv;
@@ -206,8 +281,13 @@ static int cg_core(const dirac_op *op, const void *rhs, void *x, double m0, doub
         cg_alpha_kernel<<<1, kNS, 0, s>>>(nv, w.rr, w.pq, w.act, w.alpha);
         TRY(blas_axpby(op, p, x, x, nullptr, 1.0, pv, w.alpha, 1.0, nullptr, s));
         TRY(blas_axpby(op, p, r, r, nullptr, 1.0, q, w.alpha, -1.0, w.rr_new, s));
-        double rn[kNS];
+        double rn[kNS], pq[2 * kNS], rro[kNS];
+        if (lan) {
+            TRY(cuda_check(cudaMemcpyAsync(pq, w.pq, 2 * nv * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H"));
+            TRY(cuda_check(cudaMemcpyAsync(rro, w.rr, nv * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H"));
+        }
         TRY(to_host(rn, w.rr_new, nv, s));
+        if (lan) lan->add(nv, act, rro, pq, rn);
         bool all_pass = true, finite = true;
         for (int v = 0; v < nv; ++v) {
             if (!isfinite(rn[v])) finite = false;
@@ -373,6 +453,196 @@ static int bicgstab_core(const dirac_op *op, const void *b, void *x, double m0, 
     return DIRAC_OK;
 }
 
+// previous sloppy |r|^2 expressed in the new scaling (ratio = 0 restarts p)
+__global__ void scale_rr_kernel(int nv, const double *ratio, double *rr) {
+    const int v = threadIdx.x;
+    if (v >= nv) return;
+    rr[v] *= ratio[2 * v] * ratio[2 * v];
+}
+
+__global__ void inverse_kernel(int nv, const double *c, double *inv) {
+    const int v = threadIdx.x;
+    if (v >= nv) return;
+    inv[2 * v] = c[2 * v] != 0.0 ? 1.0 / c[2 * v] : 0.0;
+    inv[2 * v + 1] = 0.0;
+}
+
+// Mixed-precision CG on A x = rhs (A = D^dag D) with reliable updates: the
+// Krylov iteration runs in the precision of `lo` on the residual scaled to
+// unit norm per RHS; whenever the sloppy residual has dropped by `delta`
+// since the last update (or looks converged, or at maxit) the accumulated
+// correction is added to x and r = rhs - A x is recomputed in the precision
+// of `hi`, rescaled, and the iteration continues with its search direction
+// (rescaled) instead of restarting.  Converged RHS are frozen.
+// Workspace: hi vectors 0..1, lo vectors 0..3.
+static int cg_reliable(const dirac_op *hi, const dirac_op *lo, const void *rhs, void *x, double m0, double tol,
+                       int maxit, double delta, CoreOut &out, Lanczos *lan, cudaStream_t s) {
+    Ws wh, wl;
+    TRY(get_ws(hi, wh));
+    TRY(get_ws(lo, wl));
+    const int nv = hi->nv;
+    const dirac_prec ph = hi->prec, pl = lo->prec;
+    void *rh = wh.v[0], *th = wh.v[1];
+    void *rs = wl.v[0], *ps = wl.v[1], *qs = wl.v[2], *ys = wl.v[3];
+    double *sig = wh.c1, *ratio = wh.c3, *inv = wh.omega;
+    double nb[kNS], rrt[kNS], act[kNS], rmax[kNS], prev_true[kNS], best[kNS], best_true[kNS];
+    int slow[kNS], since_best[kNS];
+    // sloppy iterations without a new residual minimum that force an update
+    // (CG residual norms are not monotone, so this is only a safety net)
+    const int kStall = 100;
+    TRY(blas_norm2(hi, ph, rhs, wh.nb, s));
+    TRY(to_host(nb, wh.nb, nv, s));
+    // true residual and first scaling
+    TRY(apply_A(hi, x, th, m0, s));
+    TRY(blas_axpby(hi, ph, rh, rhs, nullptr, 1.0, th, nullptr, -1.0, wh.rr, s));
+    TRY(to_host(rrt, wh.rr, nv, s));
+    int nact = 0;
+    for (int v = 0; v < nv; ++v) {
+        const bool conv = nb[v] == 0.0 || sqrt(rrt[v]) < tol * sqrt(nb[v]);
+        act[v] = conv ? 0.0 : 1.0;
+        out.status_rhs[v] = conv ? DIRAC_OK : DIRAC_NOT_CONVERGED;
+        out.relres[v] = nb[v] > 0 ? sqrt(rrt[v] / nb[v]) : 0.0;
+        prev_true[v] = best_true[v] = sqrt(rrt[v]);
+        slow[v] = 0;
+        nact += !conv;
+    }
+    TRY(to_dev(wh.act, act, nv, s));
+    TRY(to_dev(wl.act, act, nv, s));
+    // sloppy vectors carry the residual scaled to unit rms per component (not
+    // unit norm): FP16 would otherwise hold most components near its
+    // subnormal range on large lattices
+    const double unit = sqrt((double)hi->rows);
+    coef_from_norm_kernel<<<1, kNS, 0, s>>>(nv, wh.rr, wh.act, sig, 1, unit);
+    TRY(blas_axpby(hi, ph, th, rh, sig, 1.0, nullptr, nullptr, 0.0, nullptr, s));
+    TRY(blas_convert(hi, th, ph, rs, pl, s));
+    TRY(blas_axpby(lo, pl, ps, rs, nullptr, 1.0, nullptr, nullptr, 0.0, nullptr, s));
+    TRY(cuda_check(cudaMemsetAsync(ys, 0, lo->vec_bytes, s), "memset"));
+    TRY(blas_norm2(lo, pl, rs, wl.rr, s));
+    double rr0[kNS];
+    TRY(to_host(rr0, wl.rr, nv, s));
+    for (int v = 0; v < nv; ++v) {
+        rmax[v] = best[v] = sqrt(rr0[v]);
+        since_best[v] = 0;
+    }
+    double sig_h[kNS];
+    for (int v = 0; v < nv; ++v) sig_h[v] = (act[v] != 0.0 && rrt[v] > 0) ? unit / sqrt(rrt[v]) : 0.0;
+    out.status = DIRAC_OK;
+    int it = 0;
+    while (nact > 0) {
+        ++it;
+        TRY(apply_A(lo, ps, qs, m0, s));
+        TRY(blas_dot(lo, pl, ps, qs, wl.pq, s));
+        cg_alpha_kernel<<<1, kNS, 0, s>>>(nv, wl.rr, wl.pq, wl.act, wl.alpha);
+        TRY(blas_axpby(lo, pl, ys, ys, nullptr, 1.0, ps, wl.alpha, 1.0, nullptr, s));
+        TRY(blas_axpby(lo, pl, rs, rs, nullptr, 1.0, qs, wl.alpha, -1.0, wl.rr_new, s));
+        double rn[kNS], pq[2 * kNS], rro[kNS];
+        if (lan) {
+            TRY(cuda_check(cudaMemcpyAsync(pq, wl.pq, 2 * nv * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H"));
+            TRY(cuda_check(cudaMemcpyAsync(rro, wl.rr, nv * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H"));
+        }
+        TRY(to_host(rn, wl.rr_new, nv, s));
+        if (lan) lan->add(nv, act, rro, pq, rn);
+        bool trigger = it >= maxit, finite = true;
+        bool stalled[kNS];
+        for (int v = 0; v < nv; ++v) {
+            stalled[v] = false;
+            if (!isfinite(rn[v])) finite = false;
+            if (act[v] == 0.0) continue;
+            const double r = sqrt(rn[v]);
+            if (r < best[v]) {
+                best[v] = r;
+                since_best[v] = 0;
+            } else if (++since_best[v] >= kStall) {
+                trigger = true;   // the sloppy recurrence stopped improving: refresh it
+            }
+            if (r < delta * rmax[v] || r < tol * sqrt(nb[v]) * sig_h[v]) trigger = true;
+        }
+        if (!finite) {
+            out.status = DIRAC_NONFINITE;
+            break;
+        }
+        if (trigger) {
+            out.recomputes++;
+            // x += y / sigma, then the true residual in the high precision
+            inverse_kernel<<<1, kNS, 0, s>>>(nv, sig, inv);
+            TRY(blas_convert(lo, ys, pl, th, ph, s));
+            TRY(blas_axpby(hi, ph, x, x, nullptr, 1.0, th, inv, 1.0, nullptr, s));
+            TRY(apply_A(hi, x, th, m0, s));
+            TRY(blas_axpby(hi, ph, rh, rhs, nullptr, 1.0, th, nullptr, -1.0, wh.rr, s));
+            TRY(to_host(rrt, wh.rr, nv, s));
+            nact = 0;
+            bool stagnated = false;
+            for (int v = 0; v < nv; ++v) {
+                out.relres[v] = nb[v] > 0 ? sqrt(rrt[v] / nb[v]) : 0.0;
+                if (act[v] == 0.0) continue;
+                if (!isfinite(rrt[v])) {
+                    out.status = DIRAC_NONFINITE;
+                    return DIRAC_OK;
+                }
+                if (sqrt(rrt[v]) < tol * sqrt(nb[v])) {
+                    act[v] = 0.0;
+                    out.status_rhs[v] = DIRAC_OK;
+                    continue;
+                }
+                // the true residual grew across the segment: the sloppy search
+                // direction is no longer useful, restart it below
+                stalled[v] = stalled[v] || sqrt(rrt[v]) > prev_true[v];
+                // give up when 30 updates in a row failed to halve the best true residual
+                if (sqrt(rrt[v]) < 0.5 * best_true[v]) {
+                    best_true[v] = sqrt(rrt[v]);
+                    slow[v] = 0;
+                } else if (++slow[v] >= 30) {
+                    stagnated = true;
+                }
+                prev_true[v] = sqrt(rrt[v]);
+                ++nact;
+            }
+            TRY(to_dev(wh.act, act, nv, s));
+            TRY(to_dev(wl.act, act, nv, s));
+            if (nact == 0) break;
+            if (stagnated) {
+                out.status = DIRAC_STAGNATED;
+                for (int v = 0; v < nv; ++v)
+                    if (act[v] != 0.0) out.status_rhs[v] = DIRAC_STAGNATED;
+                break;
+            }
+            if (it >= maxit) {
+                out.status = DIRAC_NOT_CONVERGED;
+                break;
+            }
+            // rescale: r_s = sigma_new r, p_s *= sigma_new / sigma_old (0 = restart a
+            // stalled direction), y_s = 0
+            double rat[2 * kNS];
+            for (int v = 0; v < nv; ++v) {
+                const double sn = (act[v] != 0.0 && rrt[v] > 0) ? unit / sqrt(rrt[v]) : 0.0;
+                rat[2 * v] = (stalled[v] || sig_h[v] == 0.0) ? 0.0 : sn / sig_h[v];
+                rat[2 * v + 1] = 0.0;
+            }
+            TRY(to_dev(ratio, rat, 2 * nv, s));
+            coef_from_norm_kernel<<<1, kNS, 0, s>>>(nv, wh.rr, wh.act, sig, 1, unit);
+            scale_rr_kernel<<<1, kNS, 0, s>>>(nv, ratio, wl.rr);
+            TRY(blas_axpby(hi, ph, th, rh, sig, 1.0, nullptr, nullptr, 0.0, nullptr, s));
+            TRY(blas_convert(hi, th, ph, rs, pl, s));
+            TRY(blas_axpby(lo, pl, ps, ps, ratio, 1.0, nullptr, nullptr, 0.0, nullptr, s));
+            TRY(cuda_check(cudaMemsetAsync(ys, 0, lo->vec_bytes, s), "memset"));
+            TRY(blas_norm2(lo, pl, rs, wl.rr_new, s));
+            TRY(to_host(rn, wl.rr_new, nv, s));
+            for (int v = 0; v < nv; ++v) {
+                rmax[v] = best[v] = sqrt(rn[v]);
+                since_best[v] = 0;
+                sig_h[v] = (act[v] != 0.0 && rrt[v] > 0) ? unit / sqrt(rrt[v]) : 0.0;
+            }
+        } else {
+            for (int v = 0; v < nv; ++v) rmax[v] = fmax(rmax[v], sqrt(rn[v]));
+        }
+        cg_beta_kernel<<<1, kNS, 0, s>>>(nv, wl.rr_new, wl.rr, wl.act, wl.beta);
+        TRY(blas_axpby(lo, pl, ps, rs, nullptr, 1.0, ps, wl.beta, 1.0, nullptr, s));
+    }
+    out.iters = it;
+    TRY(launch_check("reliable-update kernels"));
+    return DIRAC_OK;
+}
+
 static double default_inner_tol(dirac_prec p) {
     switch (p) {
     case DIRAC_F32: return 1e-5;
@@ -433,7 +703,8 @@ static int mixed_solve(const dirac_op *op, const void *b, void *x, double m0, co
         if (total >= prm->maxit) break;
         TRY(to_dev(wh.act, act, nv, s));
         // inner right-hand side r / |r| in low precision
-        coef_from_norm_kernel<<<1, kNS, 0, s>>>(nv, wh.rr, wh.act, wh.c1, 1);
+        const double unit = sqrt((double)op->rows);   // unit rms per component (see cg_reliable)
+        coef_from_norm_kernel<<<1, kNS, 0, s>>>(nv, wh.rr, wh.act, wh.c1, 1, unit);
         TRY(blas_axpby(op, ph, tmp, r, wh.c1, 1.0, nullptr, nullptr, 0.0, nullptr, s));
         TRY(blas_convert(op, tmp, ph, rl, pl, s));
         TRY(cuda_check(cudaMemsetAsync(el, 0, lo->vec_bytes, s), "memset"));
@@ -445,7 +716,7 @@ static int mixed_solve(const dirac_op *op, const void *b, void *x, double m0, co
         st->recomputes += co.recomputes;
         // x += |r| e
         TRY(blas_convert(op, el, pl, tmp, ph, s));
-        coef_from_norm_kernel<<<1, kNS, 0, s>>>(nv, wh.rr, wh.act, wh.c1, 0);
+        coef_from_norm_kernel<<<1, kNS, 0, s>>>(nv, wh.rr, wh.act, wh.c1, 0, unit);
         TRY(blas_axpby(op, ph, x, x, nullptr, 1.0, tmp, wh.c1, 1.0, nullptr, s));
         ++outer;
         if (co.iters == 0) break;   // inner solver made no progress
@@ -455,18 +726,54 @@ static int mixed_solve(const dirac_op *op, const void *b, void *x, double m0, co
     return DIRAC_OK;
 }
 
+static void lanczos_stats(const Lanczos &lan, int nv, dirac_solve_stats *st) {
+    for (int v = 0; v < nv; ++v) lanczos_extremes(lan.alpha[v], lan.beta[v], st->lambda_min[v], st->lambda_max[v]);
+}
+
+static int reliable_solve(const dirac_op *op, const void *b, void *x, double m0, const dirac_solve_params *prm,
+                          dirac_solve_stats *st, cudaStream_t s) {
+    dirac_op *lo = nullptr;
+    TRY(op_inner(op, prm->inner_prec, &lo, s));
+    Ws w;
+    TRY(get_ws(op, w));
+    void *rhs = w.v[5];
+    if (prm->solver == DIRAC_CG_NORMAL) TRY(op_apply(op, b, rhs, m0, -1, s));
+    else TRY(blas_axpby(op, op->prec, rhs, b, nullptr, 1.0, nullptr, nullptr, 0.0, nullptr, s));
+    CoreOut co;
+    Lanczos lan;
+    const double delta = prm->delta > 0 ? prm->delta : 0.1;
+    TRY(cg_reliable(op, lo, rhs, x, m0, prm->tol, prm->maxit, delta, co, &lan, s));
+    st->iters = co.iters;
+    st->outer_iters = co.recomputes;
+    st->recomputes = co.recomputes;
+    st->status = co.status;
+    bool all = true;
+    for (int v = 0; v < op->nv; ++v) {
+        st->status_per_rhs[v] = co.status_rhs[v];
+        st->relres[v] = co.relres[v];
+        all &= co.status_rhs[v] == DIRAC_OK;
+    }
+    if (all) st->status = DIRAC_OK;
+    else if (st->status == DIRAC_OK) st->status = DIRAC_NOT_CONVERGED;
+    lanczos_stats(lan, op->nv, st);
+    return DIRAC_OK;
+}
+
 static int plain_solve(const dirac_op *op, const void *b, void *x, double m0, const dirac_solve_params *prm,
                        dirac_solve_stats *st, cudaStream_t s) {
     Ws w;
     TRY(get_ws(op, w));
     const int every = prm->recompute_every > 0 ? prm->recompute_every : (op->prec == DIRAC_F64 ? 50 : 20);
     CoreOut co;
+    Lanczos lan;
     if (prm->solver == DIRAC_CG_NORMAL) {
         void *rhs = w.v[5];
         TRY(op_apply(op, b, rhs, m0, -1, s));
-        TRY(cg_core(op, rhs, x, m0, prm->tol, prm->maxit, every, co, s));
+        TRY(cg_core(op, rhs, x, m0, prm->tol, prm->maxit, every, co, s, &lan));
+        lanczos_stats(lan, op->nv, st);
     } else if (prm->solver == DIRAC_CG_HPD) {
-        TRY(cg_core(op, b, x, m0, prm->tol, prm->maxit, every, co, s));
+        TRY(cg_core(op, b, x, m0, prm->tol, prm->maxit, every, co, s, &lan));
+        lanczos_stats(lan, op->nv, st);
     } else {
         TRY(bicgstab_core(op, b, x, m0, prm->tol, prm->maxit, every, co, s));
     }
@@ -492,6 +799,8 @@ int solve(const dirac_op *op, const void *b, void *x, double m0, const dirac_sol
     memset(&st, 0, sizeof(st));
     int rc;
     if (prm->inner_prec == op->prec) rc = plain_solve(op, b, x, m0, prm, &st, s);
+    else if (prm->solver != DIRAC_BICGSTAB && prm->mixed_mode == DIRAC_MIXED_RELIABLE)
+        rc = reliable_solve(op, b, x, m0, prm, &st, s);
     else rc = mixed_solve(op, b, x, m0, prm, &st, s);
     if (rc) return rc;
     // true residual ||b - D x|| / ||b|| (||b - D^dag D x|| / ||b|| for CG_HPD)
@@ -520,5 +829,8 @@ extern "C" int dirac_solve(const dirac_op *op, const void *b, void *x, double m0
         return DIRAC_ERR_INVALID_ARG;
     if (params->inner_prec < DIRAC_F64 || params->inner_prec > DIRAC_F16) return DIRAC_ERR_UNSUPPORTED_PREC;
     if (!(params->tol > 0) || params->maxit < 1) return DIRAC_ERR_INVALID_ARG;
+    if (params->mixed_mode != DIRAC_MIXED_RELIABLE && params->mixed_mode != DIRAC_MIXED_RESTART)
+        return DIRAC_ERR_INVALID_ARG;
+    if (params->delta < 0 || params->delta >= 1) return DIRAC_ERR_INVALID_ARG;
     return dgb::solve(op, b, x, m0, params, stats, (cudaStream_t)stream);
 }

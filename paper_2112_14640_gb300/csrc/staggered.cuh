@@ -14,13 +14,13 @@
 namespace dgb {
 
 template <int NC, int VR, bool DAG, typename E, typename A>
-__device__ __forceinline__ void stag_hop(cx<A> (&acc)[NC][VR], const E *__restrict__ link,
-                                         const E *__restrict__ phi, int nv, A f) {
+__device__ __forceinline__ void stag_hop(cx<A> (&acc)[NC][VR], const E *__restrict__ link, long long lstride,
+                                         const E *__restrict__ phi, long long cs_stride, A f) {
     cx<A> L[NC][NC];
-    load_mat<NC, E, A>(link, L);
+    load_mat_s<NC, E, A>(link, lstride, L);
     cx<A> p[NC][VR];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) load_cx<E, VR, A>(phi + 2 * (long long)c * nv, p[c]);
+    for (int c = 0; c < NC; ++c) load_cx<E, VR, A>(phi + 2 * c * cs_stride, p[c]);
 #pragma unroll
     for (int c = 0; c < NC; ++c)
 #pragma unroll
@@ -35,8 +35,8 @@ __device__ __forceinline__ void stag_hop(cx<A> (&acc)[NC][VR], const E *__restri
         }
 }
 
-template <int NC, int VR, typename E, int MINB>
-__global__ void __launch_bounds__(kStencilBlock, MINB) staggered_kernel(const E *__restrict__ U, const E *__restrict__ in,
+template <int NC, int VR, typename E, int MINB, int LAYOUT>
+__global__ void __launch_bounds__(kStencilBlock, (MINB > 1 ? MINB : 0)) staggered_kernel(const E *__restrict__ U, const E *__restrict__ in,
                                                         E *__restrict__ out, Lat g, typename Acc<E>::T mass,
                                                         typename Acc<E>::T half_sgn) {
     using A = typename Acc<E>::T;
@@ -46,7 +46,8 @@ __global__ void __launch_bounds__(kStencilBlock, MINB) staggered_kernel(const E 
     const long long n = tid / nchunk;
     const int j = (int)(tid - n * nchunk);
     const Coord c = site_coords(g, n);
-    const long long site_cx = (long long)NC * g.nv;
+    using L = Layout<LAYOUT>;
+    const long long cs = L::cs_stride(g), ls = L::mat_stride(g);
 
     cx<A> acc[NC][VR];
 #pragma unroll
@@ -61,17 +62,17 @@ __global__ void __launch_bounds__(kStencilBlock, MINB) staggered_kernel(const E 
         const A eta = (e[mu] & 1) ? (A)-1 : (A)1;
         const long long fw = neighbour(g, n, c, mu, +1);
         const long long bw = neighbour(g, n, c, mu, -1);
-        stag_hop<NC, VR, false>(acc, U + 2 * ((n * 4 + mu) * NC * NC), in + 2 * (fw * site_cx + (long long)j * VR),
-                                g.nv, eta);
-        stag_hop<NC, VR, true>(acc, U + 2 * ((bw * 4 + mu) * NC * NC), in + 2 * (bw * site_cx + (long long)j * VR),
-                               g.nv, -eta);
+        stag_hop<NC, VR, false>(acc, U + 2 * L::template mat<NC>(g, n, 4, mu), ls,
+                                in + 2 * (L::vec(g, fw, NC, 0) + (long long)j * VR), cs, eta);
+        stag_hop<NC, VR, true>(acc, U + 2 * L::template mat<NC>(g, bw, 4, mu), ls,
+                               in + 2 * (L::vec(g, bw, NC, 0) + (long long)j * VR), cs, -eta);
     }
 
-    const long long base = 2 * (n * site_cx + (long long)j * VR);
+    const long long base = 2 * (L::vec(g, n, NC, 0) + (long long)j * VR);
 #pragma unroll
     for (int a = 0; a < NC; ++a) {
         cx<A> p[VR], o[VR];
-        const long long off = base + 2LL * a * g.nv;
+        const long long off = base + 2LL * a * cs;
         load_cx<E, VR, A>(in + off, p);
 #pragma unroll
         for (int v = 0; v < VR; ++v) {
@@ -91,13 +92,16 @@ int launch_staggered_t(const dirac_op *op, const void *in, void *out, double m0,
         constexpr int NC = decltype(ncc)::value;
         return dispatch_vr(vr, [&](auto vrc) {
             constexpr int VR = decltype(vrc)::value;
-            return dispatch_minb(NC, minb, [&](auto mbc) {
+            return dispatch_minb<NC>(minb, [&](auto mbc) {
             constexpr int MINB = decltype(mbc)::value;
-            const long long threads = op->V * (op->nv / VR);
-            const int block = kStencilBlock;
-            staggered_kernel<NC, VR, E, MINB><<<grid_for(threads, block), block, 0, s>>>(
-                (const E *)op->links, (const E *)in, (E *)out, op->lat, (A)m0, (A)(0.5 * sgn));
-            return launch_check("staggered_kernel");
+            return dispatch_layout(op->geom.layout, [&](auto lyc) {
+                constexpr int LAYOUT = decltype(lyc)::value;
+                const long long threads = op->V * (op->nv / VR);
+                const int block = kStencilBlock;
+                staggered_kernel<NC, VR, E, MINB, LAYOUT><<<grid_for(threads, block), block, 0, s>>>(
+                    (const E *)op->links, (const E *)in, (E *)out, op->lat, (A)m0, (A)(0.5 * sgn));
+                return launch_check("staggered_kernel");
+            });
             });
         });
     });

@@ -58,18 +58,20 @@ __device__ __forceinline__ void reconstruct(cx<A> &o0, cx<A> &o1, cx<A> &o2, cx<
     }
 }
 
-// One hop: acc += (1 + a gamma_MU) (x) L psi(m), L = link or link^dag.
+// One hop: acc += (1 + a gamma_MU) (x) L psi(m), L = link or link^dag.  The
+// link elements are lstride complex numbers apart, the spinor components
+// cs_stride apart (both depend on the layout).
 template <int MU, bool DAG, int NC, int VR, typename E, typename A>
-__device__ __forceinline__ void wilson_hop(cx<A> (&acc)[NC][4][VR], const E *__restrict__ link,
-                                           const E *__restrict__ psi, int nv, A a) {
+__device__ __forceinline__ void wilson_hop(cx<A> (&acc)[NC][4][VR], const E *__restrict__ link, long long lstride,
+                                           const E *__restrict__ psi, long long cs_stride, A a) {
     cx<A> L[NC][NC];
-    load_mat<NC, E, A>(link, L);
+    load_mat_s<NC, E, A>(link, lstride, L);
     cx<A> h[NC][2][VR];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
         cx<A> p[4][VR];
 #pragma unroll
-        for (int s = 0; s < 4; ++s) load_cx<E, VR, A>(psi + 2 * (long long)((c * 4 + s) * nv), p[s]);
+        for (int s = 0; s < 4; ++s) load_cx<E, VR, A>(psi + 2 * (c * 4 + s) * cs_stride, p[s]);
 #pragma unroll
         for (int v = 0; v < VR; ++v) project<MU, A>(p[0][v], p[1][v], p[2][v], p[3][v], a, h[c][0][v], h[c][1][v]);
     }
@@ -93,23 +95,24 @@ __device__ __forceinline__ void wilson_hop(cx<A> (&acc)[NC][4][VR], const E *__r
     }
 }
 
-template <int MU, int NC, int VR, typename E, typename A>
+template <int MU, int NC, int VR, int LAYOUT, typename E, typename A>
 __device__ __forceinline__ void wilson_dir(cx<A> (&acc)[NC][4][VR], const E *__restrict__ U,
                                            const E *__restrict__ in, const Lat &g, long long n, const Coord &c,
                                            int j, A sgn) {
+    using L = Layout<LAYOUT>;
     const long long fw = neighbour(g, n, c, MU, +1);
     const long long bw = neighbour(g, n, c, MU, -1);
-    const long long site_cx = (long long)NC * 4 * g.nv;
+    const long long cs = L::cs_stride(g), ls = L::mat_stride(g);
     // forward: (1 - sgn gamma) U_mu(n) psi(n+mu)
-    wilson_hop<MU, false, NC, VR>(acc, U + 2 * ((n * 4 + MU) * NC * NC), in + 2 * (fw * site_cx + (long long)j * VR),
-                                  g.nv, -sgn);
+    wilson_hop<MU, false, NC, VR>(acc, U + 2 * L::template mat<NC>(g, n, 4, MU), ls,
+                                  in + 2 * (L::vec(g, fw, NC * 4, 0) + (long long)j * VR), cs, -sgn);
     // backward: (1 + sgn gamma) U_mu(n-mu)^dag psi(n-mu)
-    wilson_hop<MU, true, NC, VR>(acc, U + 2 * ((bw * 4 + MU) * NC * NC), in + 2 * (bw * site_cx + (long long)j * VR),
-                                 g.nv, sgn);
+    wilson_hop<MU, true, NC, VR>(acc, U + 2 * L::template mat<NC>(g, bw, 4, MU), ls,
+                                 in + 2 * (L::vec(g, bw, NC * 4, 0) + (long long)j * VR), cs, sgn);
 }
 
-template <int NC, int VR, typename E, int MINB>
-__global__ void __launch_bounds__(kStencilBlock, MINB) wilson_kernel(const E *__restrict__ U, const E *__restrict__ in,
+template <int NC, int VR, typename E, int MINB, int LAYOUT>
+__global__ void __launch_bounds__(kStencilBlock, (MINB > 1 ? MINB : 0)) wilson_kernel(const E *__restrict__ U, const E *__restrict__ in,
                                                      E *__restrict__ out, Lat g, typename Acc<E>::T diag,
                                                      typename Acc<E>::T sgn) {
     using A = typename Acc<E>::T;
@@ -128,19 +131,20 @@ __global__ void __launch_bounds__(kStencilBlock, MINB) wilson_kernel(const E *__
 #pragma unroll
             for (int v = 0; v < VR; ++v) acc[a][s][v] = cx<A>{0, 0};
 
-    wilson_dir<0, NC, VR, E, A>(acc, U, in, g, n, c, j, sgn);
-    wilson_dir<1, NC, VR, E, A>(acc, U, in, g, n, c, j, sgn);
-    wilson_dir<2, NC, VR, E, A>(acc, U, in, g, n, c, j, sgn);
-    wilson_dir<3, NC, VR, E, A>(acc, U, in, g, n, c, j, sgn);
+    wilson_dir<0, NC, VR, LAYOUT, E, A>(acc, U, in, g, n, c, j, sgn);
+    wilson_dir<1, NC, VR, LAYOUT, E, A>(acc, U, in, g, n, c, j, sgn);
+    wilson_dir<2, NC, VR, LAYOUT, E, A>(acc, U, in, g, n, c, j, sgn);
+    wilson_dir<3, NC, VR, LAYOUT, E, A>(acc, U, in, g, n, c, j, sgn);
 
-    const long long base = 2 * (n * (long long)NC * 4 * g.nv + (long long)j * VR);
+    const long long base = 2 * (Layout<LAYOUT>::vec(g, n, NC * 4, 0) + (long long)j * VR);
+    const long long cs = Layout<LAYOUT>::cs_stride(g);
     const A mhalf = (A)-0.5;
 #pragma unroll
     for (int a = 0; a < NC; ++a)
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
             cx<A> p[VR], o[VR];
-            const long long off = base + 2LL * (a * 4 + s) * g.nv;
+            const long long off = base + 2LL * (a * 4 + s) * cs;
             load_cx<E, VR, A>(in + off, p);
 #pragma unroll
             for (int v = 0; v < VR; ++v) {
@@ -160,13 +164,16 @@ int launch_wilson_t(const dirac_op *op, const void *in, void *out, double m0, in
         constexpr int NC = decltype(ncc)::value;
         return dispatch_vr(vr, [&](auto vrc) {
             constexpr int VR = decltype(vrc)::value;
-            return dispatch_minb(NC, minb, [&](auto mbc) {
+            return dispatch_minb<NC>(minb, [&](auto mbc) {
             constexpr int MINB = decltype(mbc)::value;
-            const long long threads = op->V * (op->nv / VR);
-            const int block = kStencilBlock;
-            wilson_kernel<NC, VR, E, MINB><<<grid_for(threads, block), block, 0, s>>>(
-                (const E *)op->links, (const E *)in, (E *)out, op->lat, (A)(4.0 + m0), (A)sgn);
-            return launch_check("wilson_kernel");
+            return dispatch_layout(op->geom.layout, [&](auto lyc) {
+                constexpr int LAYOUT = decltype(lyc)::value;
+                const long long threads = op->V * (op->nv / VR);
+                const int block = kStencilBlock;
+                wilson_kernel<NC, VR, E, MINB, LAYOUT><<<grid_for(threads, block), block, 0, s>>>(
+                    (const E *)op->links, (const E *)in, (E *)out, op->lat, (A)(4.0 + m0), (A)sgn);
+                return launch_check("wilson_kernel");
+            });
             });
         });
     });

