@@ -451,7 +451,7 @@ def batch_measurement(D, I, torch, nsolves=64, seed=2026):
     return res
 
 
-def tune_mass(D, op32, b32, kind, target=1e6, iters=600):
+def tune_mass(D, op32, b32, kind, target=1e6, iters=600, torch_mod=None):
     """Bare mass giving cond(D^dag D) ~ target, from Lanczos estimates of a
     short FP32 CG (App. F "cond").  Staggered: cond ~ lambda_max / m^2.
     Wilson: bisection on m0 for lambda_min = lambda_max / target."""
@@ -461,17 +461,26 @@ def tune_mass(D, op32, b32, kind, target=1e6, iters=600):
     if kind == D.STAGGERED:
         lo, hi = est(0.05)
         return (hi / target) ** 0.5, {"lambda_max": hi}
-    lo_m, hi_m = -2.5, 0.5
-    for _ in range(10):
-        m = 0.5 * (lo_m + hi_m)
-        lmin, lmax = est(m)
-        if lmin * target > lmax:
-            hi_m = m     # too well conditioned: move toward the critical mass
-        else:
-            lo_m = m
-    m = hi_m
-    lmin, lmax = est(m)
-    return m, {"lambda_min": lmin, "lambda_max": lmax, "cond_est": lmax / max(lmin, 1e-300)}
+    # Wilson: a coarse scan of m0 on a 16^3x32 field of the same roughness,
+    # each point solved to 1e-8 so that the Lanczos extremes have converged,
+    # then log-interpolation of cond(m0) to the target
+    small = (16, 16, 16, 32)
+    import numpy as np
+    from paper_2112_14640_gb300 import inputs as I
+    Us = torch_mod.from_numpy(I.gauge_field(small, NC, 0.6, 98)).cuda()
+    ops = D.DiracOp(kind, Us, NV, BC, D.F32)
+    bs = ops.to_prec(torch_mod.from_numpy(I.source(small, NC, NV, 6)).cuda())
+    scan = []
+    for m in (0.0, -0.4, -0.7, -0.9, -1.05, -1.2, -1.3, -1.4, -1.5, -1.6):
+        _, st = ops.solve(bs, m0=m, solver=D.CG_HPD, tol=1e-8, maxit=20000)
+        c = max(st["lambda_max"]) / max(min(st["lambda_min"]), 1e-300)
+        scan.append((m, c, st["iters"]))
+        if c > 10 * target:
+            break
+    ops.close()
+    ms, cs = np.array([a for a, _, _ in scan]), np.log(np.array([b for _, b, _ in scan]))
+    m = float(np.interp(np.log(target), cs, ms)) if cs.max() >= np.log(target) else float(ms[-1])
+    return m, {"scan_16x16x16x32": [(round(a, 3), float(b), int(k)) for a, b, k in scan]}
 
 
 def solver_comparison(D, I, torch):
@@ -486,16 +495,19 @@ def solver_comparison(D, I, torch):
         op = D.DiracOp(kind, U, NV, BC, D.F64)
         op32 = D.DiracOp(kind, U, NV, BC, D.F32)
         src = torch.from_numpy(I.source(dims, NC, NV, 5, staggered=(kind == D.STAGGERED))).cuda()
-        m0, info = tune_mass(D, op32, op32.to_prec(src), kind)
+        m0, info = tune_mass(D, op32, op32.to_prec(src), kind, torch_mod=torch)
         op32.close()
         b = op.to_prec(src)
         row = {"m0": m0, "tuning": info}
-        for inner in (D.F32, D.BF16, D.F16):
+        for inner, links in ((D.F32, D.LINKS_NATIVE), (D.F16, D.LINKS_F32), (D.BF16, D.LINKS_F32),
+                             (D.F16, D.LINKS_NATIVE), (D.BF16, D.LINKS_NATIVE)):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            x, st = op.solve(b, m0=m0, solver=D.CG_NORMAL, tol=1e-10, maxit=100000, inner_prec=inner)
+            x, st = op.solve(b, m0=m0, solver=D.CG_NORMAL, tol=1e-10, maxit=40000, inner_prec=inner,
+                             sloppy_links=links)
             torch.cuda.synchronize()
-            row[D.PREC_NAMES[inner]] = {"seconds": time.perf_counter() - t0, "iters": st["iters"],
+            name = D.PREC_NAMES[inner] + ("+f32links" if links == D.LINKS_F32 else "")
+            row[name] = {"seconds": time.perf_counter() - t0, "iters": st["iters"],
                                         "updates": st["outer_iters"], "status": st["status"],
                                         "max_relres": max(st["relres"]), "max_true_relres": max(st["true_relres"]),
                                         "cond_lanczos": max(st["lambda_max"]) / max(min(st["lambda_min"]), 1e-300)}

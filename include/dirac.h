@@ -75,7 +75,11 @@ typedef struct {
     int bc[4];
     dirac_prec prec;
     int layout;        /* vector layout, DIRAC_LAYOUT_* below (0 = the paper's) */
+    int link_storage;  /* DIRAC_LINKS_NATIVE: links (and W) in prec; DIRAC_LINKS_F32: FP32
+                          links with 16-bit vectors (prec BF16/F16 only) */
 } dirac_geom;
+
+enum { DIRAC_LINKS_NATIVE = 0, DIRAC_LINKS_F32 = 1 };
 
 /* Vector layouts (the RHS index v is innermost in both, so the BLAS-1 calls
  * treat every vector as a [rows][N_v] array):
@@ -134,13 +138,15 @@ int dirac_apply_host(const dirac_op *op, const void *host_in, void *host_out, do
                      int dagger, void *stream);
 
 /* ----------------------------------------------------- launch tuning
- * A stencil launch variant is (vr, minb): vr = right-hand sides per thread
- * (1, 2 or 4, dividing N_v) and minb = minimum resident blocks per SM the
- * kernel was compiled for (1 = no register cap; 2, 3, 4, 6 compiled for
- * N_c = 3 only).  vr = 0 restores the default choice.  Errors:
- * DIRAC_ERR_INVALID_ARG for a variant that is not compiled or does not divide N_v. */
-int dirac_op_set_launch(dirac_op *op, int vr, int minb);
-int dirac_op_get_launch(const dirac_op *op, int *vr, int *minb);
+ * A stencil launch variant is (vr, minb, block): vr = right-hand sides per
+ * thread (1, 2 or 4, dividing N_v); minb = register class, the cap of minb
+ * resident 128-thread blocks per SM (1 = the compiler's choice; 3, 4, 6
+ * compiled for N_c = 3 only); block = threads per block, a multiple of 32 up
+ * to 128 minb (0 = 128).  vr = 0 restores the default choice.  Errors:
+ * DIRAC_ERR_INVALID_ARG for a variant that is not compiled, a vr that does
+ * not divide N_v or a block size out of range. */
+int dirac_op_set_launch(dirac_op *op, int vr, int minb, int block);
+int dirac_op_get_launch(const dirac_op *op, int *vr, int *minb, int *block);
 /* Time every compiled variant of D (bare mass m0) on operator-owned buffers
  * and keep the fastest for this operator; the choice is also remembered for
  * operators created later in this process with the same kind, precision,
@@ -210,6 +216,8 @@ typedef struct {
     double inner_tol;      /* restarted mode: relative tolerance of each inner solve (0 = default) */
     int recompute_every;   /* 0 = paper default: 50 for F64 solves, 20 otherwise */
     int mixed_mode;        /* DIRAC_MIXED_RELIABLE (CG only) or DIRAC_MIXED_RESTART */
+    int sloppy_links;      /* link storage of the inner operator: DIRAC_LINKS_NATIVE or
+                              DIRAC_LINKS_F32 (16-bit inner vectors with FP32 links) */
     double delta;          /* reliable updates: recompute when the sloppy residual fell by
                               this factor since the last update (0 = default 0.1) */
 } dirac_solve_params;

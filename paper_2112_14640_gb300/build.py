@@ -35,6 +35,11 @@ def build(force=False, verbose=False, jobs=None, extra=()):
     nvcc = _nvcc()
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     hdr_time = max(os.path.getmtime(h) for h in _headers())
+    # objects of translation units that no longer exist
+    live = {os.path.basename(s)[:-3] + ".o" for s in srcs}
+    for o in glob.glob(os.path.join(OUT, "*.o")):
+        if os.path.basename(o) not in live:
+            os.remove(o)
     objs, todo = [], []
     for s in srcs:
         o = os.path.join(OUT, os.path.basename(s)[:-3] + ".o")

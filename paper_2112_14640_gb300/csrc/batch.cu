@@ -21,6 +21,7 @@
 namespace dgb {
 
 int solver_ws(const dirac_op *op, void **vecs, int nvecs, double **scal);
+int batch_apply_A_pq(const dirac_op *op, const void *p, void *q, double *pq, double m0, cudaStream_t s);
 
 __device__ __forceinline__ unsigned long long globaltimer() {
     unsigned long long t;
@@ -32,10 +33,11 @@ __global__ void stamp_kernel(unsigned long long *t) {
     if (threadIdx.x == 0 && blockIdx.x == 0) *t = globaltimer();
 }
 
+// pq holds N_v real values |D p|^2
 __global__ void batch_alpha_kernel(int nv, const double *rr, const double *pq, const double *act, double *alpha) {
     const int v = threadIdx.x;
     if (v >= nv) return;
-    const double p = pq[2 * v];
+    const double p = pq[v];
     const double a = (act[v] != 0.0 && p > 0.0) ? rr[v] / p : 0.0;
     alpha[2 * v] = a;
     alpha[2 * v + 1] = 0.0;
@@ -190,13 +192,11 @@ extern "C" int dirac_solve_batched(int nsolves, dirac_op *const *ops, const void
             double *act = sc + 5 * 128, *nb = sc + 6 * 128;
             TRYB(cuda_check(cudaStreamWaitEvent(s, fork, 0), "wait fork"));
             for (int k = 0; k < K; ++k) {
-                TRYB(op_apply_normal(op, pv, q, m0[i], s));
-                TRYB(blas_dot(op, p, pv, q, pq, s));
+                TRYB(batch_apply_A_pq(op, pv, q, pq, m0[i], s));
                 batch_alpha_kernel<<<1, 64, 0, s>>>(nv, rr, pq, act, alpha);
-                TRYB(blas_axpby(op, p, x[i], x[i], nullptr, 1.0, pv, alpha, 1.0, nullptr, s));
                 TRYB(blas_axpby(op, p, r, r, nullptr, 1.0, q, alpha, -1.0, rr_new, s));
                 batch_beta_kernel<<<1, 64, 0, s>>>(nv, rr_new, rr, act, beta);
-                TRYB(blas_axpby(op, p, pv, r, nullptr, 1.0, pv, beta, 1.0, nullptr, s));
+                TRYB(blas_update_xp(op, p, x[i], pv, r, alpha, beta, s));   // x += alpha p; p = r + beta p
             }
             // recompute the true residual, freeze converged RHS, stamp completion
             TRYB(op_apply_normal(op, x[i], q, m0[i], s));

@@ -13,26 +13,36 @@ namespace dgb {
 
 constexpr int kRedThreads = 256;
 
-// threads per block that are a multiple of nv (one column per thread)
-inline int red_block(int nv) { return nv * (kRedThreads / nv); }
+// Complex numbers per thread and per access: one 16-byte load when N_v allows.
+inline int blas_group(dirac_prec p, int nv) { return pick_vr(p, nv); }
 
-template <int NOUT>
-__device__ __forceinline__ void block_reduce_store(double (*vals)[NOUT], double *sh, int r, int v, int R, int nv,
-                                                   double *partial_block) {
-    // sh holds R*nv*NOUT doubles
+// Threads per block: a multiple of the number of column groups nv/G.
+inline int red_block(int ngroups) { return ngroups * (kRedThreads / ngroups); }
+
+// Reduce the per-thread column sums vals[G][NOUT] over the R row-threads of the
+// block (fixed pairwise tree) and store the block's partial sums for its nv
+// columns: partial_block[v][NOUT].
+template <int G, int NOUT>
+__device__ __forceinline__ void block_reduce_store(const double (&vals)[G][NOUT], double *sh, int r, int vg, int R,
+                                                   int ng, double *partial_block) {
+    constexpr int W = G * NOUT;
 #pragma unroll
-    for (int q = 0; q < NOUT; ++q) sh[(r * nv + v) * NOUT + q] = (*vals)[q];
+    for (int i = 0; i < G; ++i)
+#pragma unroll
+        for (int q = 0; q < NOUT; ++q) sh[(r * ng + vg) * W + i * NOUT + q] = vals[i][q];
     __syncthreads();
     for (int off = 1; off < R; off *= 2) {
         if ((r % (2 * off)) == 0 && r + off < R) {
 #pragma unroll
-            for (int q = 0; q < NOUT; ++q) sh[(r * nv + v) * NOUT + q] += sh[((r + off) * nv + v) * NOUT + q];
+            for (int w = 0; w < W; ++w) sh[(r * ng + vg) * W + w] += sh[((r + off) * ng + vg) * W + w];
         }
         __syncthreads();
     }
     if (r == 0) {
 #pragma unroll
-        for (int q = 0; q < NOUT; ++q) partial_block[v * NOUT + q] = sh[v * NOUT + q];
+        for (int i = 0; i < G; ++i)
+#pragma unroll
+            for (int q = 0; q < NOUT; ++q) partial_block[(vg * G + i) * NOUT + q] = sh[vg * W + i * NOUT + q];
     }
 }
 
@@ -51,70 +61,175 @@ __global__ void finalize_kernel(const double *__restrict__ partial, int nblocks,
     for (int q = 0; q < NOUT; ++q) out[v * NOUT + q] = acc[q];
 }
 
-template <typename E>
-__global__ void norm2_kernel(const E *__restrict__ x, long long rows, int nv, double *__restrict__ partial) {
-    extern __shared__ double sh[];
-    const int R = blockDim.x / nv;
-    const int r = threadIdx.x / nv, v = threadIdx.x % nv;
-    double acc[1] = {0.0};
-    for (long long row = (long long)blockIdx.x * R + r; row < rows; row += (long long)gridDim.x * R) {
-        const long long e = 2 * (row * nv + v);
-        const double re = (double)to_acc<E>(x[e]), im = (double)to_acc<E>(x[e + 1]);
-        acc[0] = fma(re, re, acc[0]);
-        acc[0] = fma(im, im, acc[0]);
-    }
-    block_reduce_store<1>(&acc, sh, r, v, R, nv, partial + (long long)blockIdx.x * nv);
+// partial[b][v][2] -> out[v] = the real part only, summed in block order
+__global__ void finalize_re_kernel(const double *__restrict__ partial, int nblocks, int nv, double *__restrict__ out) {
+    const int v = threadIdx.x;
+    if (v >= nv) return;
+    double acc = 0.0;
+    for (int b = 0; b < nblocks; ++b) acc += partial[((long long)b * nv + v) * 2];
+    out[v] = acc;
 }
 
-template <typename E>
+// thread (r, vg) of a block walks the rows r0 = block*R + r, stride grid*R and
+// owns columns vg*G .. vg*G+G-1
+#define BLAS_THREAD_SETUP                                   \
+    const int ng = nv / G;                                  \
+    const int R = blockDim.x / ng;                          \
+    const int r = threadIdx.x / ng, vg = threadIdx.x % ng;  \
+    const bool live = r < R;
+
+template <typename E, int G>
+__global__ void norm2_kernel(const E *__restrict__ x, long long rows, int nv, double *__restrict__ partial) {
+    extern __shared__ double sh[];
+    using A = typename Acc<E>::T;
+    BLAS_THREAD_SETUP
+    double acc[G][1] = {};
+    if (live)
+        for (long long row = (long long)blockIdx.x * R + r; row < rows; row += (long long)gridDim.x * R) {
+            cx<A> a[G];
+            load_cx<E, G, A>(x + 2 * (row * nv + vg * G), a);
+#pragma unroll
+            for (int i = 0; i < G; ++i) {
+                acc[i][0] = fma((double)a[i].re, (double)a[i].re, acc[i][0]);
+                acc[i][0] = fma((double)a[i].im, (double)a[i].im, acc[i][0]);
+            }
+        }
+    block_reduce_store<G, 1>(acc, sh, r, vg, R, ng, partial + (long long)blockIdx.x * nv);
+}
+
+template <typename E, int G>
 __global__ void dot_kernel(const E *__restrict__ x, const E *__restrict__ y, long long rows, int nv,
                            double *__restrict__ partial) {
     extern __shared__ double sh[];
-    const int R = blockDim.x / nv;
-    const int r = threadIdx.x / nv, v = threadIdx.x % nv;
-    double acc[2] = {0.0, 0.0};
-    for (long long row = (long long)blockIdx.x * R + r; row < rows; row += (long long)gridDim.x * R) {
-        const long long e = 2 * (row * nv + v);
-        const double xr = (double)to_acc<E>(x[e]), xi = (double)to_acc<E>(x[e + 1]);
-        const double yr = (double)to_acc<E>(y[e]), yi = (double)to_acc<E>(y[e + 1]);
-        // conj(x) * y
-        acc[0] = fma(xr, yr, acc[0]);
-        acc[0] = fma(xi, yi, acc[0]);
-        acc[1] = fma(xr, yi, acc[1]);
-        acc[1] = fma(-xi, yr, acc[1]);
-    }
-    block_reduce_store<2>(&acc, sh, r, v, R, nv, partial + 2LL * blockIdx.x * nv);
+    using A = typename Acc<E>::T;
+    BLAS_THREAD_SETUP
+    double acc[G][2] = {};
+    if (live)
+        for (long long row = (long long)blockIdx.x * R + r; row < rows; row += (long long)gridDim.x * R) {
+            cx<A> a[G], b[G];
+            load_cx<E, G, A>(x + 2 * (row * nv + vg * G), a);
+            load_cx<E, G, A>(y + 2 * (row * nv + vg * G), b);
+#pragma unroll
+            for (int i = 0; i < G; ++i) {   // conj(x) * y
+                acc[i][0] = fma((double)a[i].re, (double)b[i].re, acc[i][0]);
+                acc[i][0] = fma((double)a[i].im, (double)b[i].im, acc[i][0]);
+                acc[i][1] = fma((double)a[i].re, (double)b[i].im, acc[i][1]);
+                acc[i][1] = fma(-(double)a[i].im, (double)b[i].re, acc[i][1]);
+            }
+        }
+    block_reduce_store<G, 2>(acc, sh, r, vg, R, ng, partial + 2LL * blockIdx.x * nv);
+}
+
+template <typename A>
+__device__ __forceinline__ cx<A> coef(const double *c, double scale, int v) {
+    return c ? cx<A>{(A)(scale * c[2 * v]), (A)(scale * c[2 * v + 1])} : cx<A>{(A)scale, (A)0};
 }
 
 // z = a x + b y per column; a, b = scale * coef[v] (complex pairs) or scale
 // alone when coef is null; x or y may be null (term dropped); z may alias x
 // or y.  With partial != null also reduces |z|^2 per column.
-template <typename E>
+template <typename E, int G>
 __global__ void axpby_kernel(E *z, const E *x, const E *y, const double *__restrict__ ac, double as,
                              const double *__restrict__ bc, double bs, long long rows, int nv, double *partial) {
     extern __shared__ double sh[];
     using A = typename Acc<E>::T;
-    const int R = blockDim.x / nv;
-    const int r = threadIdx.x / nv, v = threadIdx.x % nv;
-    const double ar = ac ? as * ac[2 * v] : as, ai = ac ? as * ac[2 * v + 1] : 0.0;
-    const double br = bc ? bs * bc[2 * v] : bs, bi = bc ? bs * bc[2 * v + 1] : 0.0;
-    const cx<A> a = {(A)ar, (A)ai}, b = {(A)br, (A)bi};
-    double acc[1] = {0.0};
-    for (long long row = (long long)blockIdx.x * R + r; row < rows; row += (long long)gridDim.x * R) {
-        const long long e = 2 * (row * nv + v);
-        cx<A> out = {0, 0};
-        if (x) cmac(out, a, cx<A>{(A)to_acc<E>(x[e]), (A)to_acc<E>(x[e + 1])});
-        if (y) cmac(out, b, cx<A>{(A)to_acc<E>(y[e]), (A)to_acc<E>(y[e + 1])});
-        const E zr = from_acc<E, A>(out.re), zi = from_acc<E, A>(out.im);
-        z[e] = zr;
-        z[e + 1] = zi;
-        if (partial) {
-            const double dr = (double)to_acc<E>(zr), di = (double)to_acc<E>(zi);
-            acc[0] = fma(dr, dr, acc[0]);
-            acc[0] = fma(di, di, acc[0]);
-        }
+    BLAS_THREAD_SETUP
+    cx<A> a[G], b[G];
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+        a[i] = coef<A>(ac, as, vg * G + i);
+        b[i] = coef<A>(bc, bs, vg * G + i);
     }
-    if (partial) block_reduce_store<1>(&acc, sh, r, v, R, nv, partial + (long long)blockIdx.x * nv);
+    double acc[G][1] = {};
+    if (live)
+        for (long long row = (long long)blockIdx.x * R + r; row < rows; row += (long long)gridDim.x * R) {
+            const long long e = 2 * (row * nv + vg * G);
+            cx<A> out[G], t[G];
+#pragma unroll
+            for (int i = 0; i < G; ++i) out[i] = cx<A>{0, 0};
+            if (x) {
+                load_cx<E, G, A>(x + e, t);
+#pragma unroll
+                for (int i = 0; i < G; ++i) cmac(out[i], a[i], t[i]);
+            }
+            if (y) {
+                load_cx<E, G, A>(y + e, t);
+#pragma unroll
+                for (int i = 0; i < G; ++i) cmac(out[i], b[i], t[i]);
+            }
+            store_cx<E, G, A>(z + e, out);
+            if (partial) {
+                // the norm of the value as stored: round the registers through
+                // the storage type (z may alias x or y, so it is not re-read)
+#pragma unroll
+                for (int i = 0; i < G; ++i) {
+                    const double re = (double)to_acc<E>(from_acc<E, A>(out[i].re));
+                    const double im = (double)to_acc<E>(from_acc<E, A>(out[i].im));
+                    acc[i][0] = fma(re, re, acc[i][0]);
+                    acc[i][0] = fma(im, im, acc[i][0]);
+                }
+            }
+        }
+    if (partial) block_reduce_store<G, 1>(acc, sh, r, vg, R, ng, partial + (long long)blockIdx.x * nv);
+}
+
+// The two Krylov updates that use the old search direction, in one pass:
+// x += a p, then p = r + b p.
+template <typename E, int G>
+__global__ void update_xp_kernel(E *x, E *p, const E *__restrict__ r_, const double *__restrict__ ac,
+                                 const double *__restrict__ bc, long long rows, int nv) {
+    using A = typename Acc<E>::T;
+    BLAS_THREAD_SETUP
+    if (!live) return;
+    cx<A> a[G], b[G];
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+        a[i] = coef<A>(ac, 1.0, vg * G + i);
+        b[i] = coef<A>(bc, 1.0, vg * G + i);
+    }
+    for (long long row = (long long)blockIdx.x * R + r; row < rows; row += (long long)gridDim.x * R) {
+        const long long e = 2 * (row * nv + vg * G);
+        cx<A> xv[G], pv[G], rv[G];
+        load_cx<E, G, A>(x + e, xv);
+        load_cx<E, G, A>(p + e, pv);
+        load_cx<E, G, A>(r_ + e, rv);
+#pragma unroll
+        for (int i = 0; i < G; ++i) {
+            cmac(xv[i], a[i], pv[i]);
+            cx<A> np = rv[i];
+            cmac(np, b[i], pv[i]);
+            pv[i] = np;
+        }
+        store_cx<E, G, A>(x + e, xv);
+        store_cx<E, G, A>(p + e, pv);
+    }
+}
+
+#undef BLAS_THREAD_SETUP
+
+template <typename F>
+static int dispatch_group(int g, F &&f) {
+    switch (g) {
+    case 1: return f(std::integral_constant<int, 1>{});
+    case 2: return f(std::integral_constant<int, 2>{});
+    case 4: return f(std::integral_constant<int, 4>{});
+    }
+    return DIRAC_ERR_INVALID_ARG;
+}
+
+// launch geometry shared by the reduction kernels: threads per block, shared bytes
+struct RedLaunch {
+    int G, tb;
+    size_t sh;
+};
+static RedLaunch red_launch(dirac_prec p, int nv, int nout) {
+    RedLaunch L;
+    L.G = blas_group(p, nv);
+    const int ng = nv / L.G;
+    L.tb = red_block(ng);
+    // one extra row of slots absorbs the threads beyond R (tb is a multiple of ng)
+    L.sh = (size_t)(L.tb + ng) * L.G * nout * sizeof(double);
+    return L;
 }
 
 template <typename E>
@@ -171,24 +286,50 @@ int blas_fill_hash(const dirac_op *op, dirac_prec p, void *v, unsigned seed, cud
 
 static inline int red_grid(const dirac_op *op) { return op->red_blocks; }
 
+template <typename E>
+static int launch_norm2(const E *v, long long rows, int nv, dirac_prec p, double *partial, int blocks, double *out,
+                        cudaStream_t s) {
+    const RedLaunch L = red_launch(p, nv, 1);
+    return dispatch_group(L.G, [&](auto gc) {
+        constexpr int G = decltype(gc)::value;
+        norm2_kernel<E, G><<<blocks, L.tb, L.sh, s>>>(v, rows, nv, partial);
+        finalize_kernel<1><<<1, 64, 0, s>>>(partial, blocks, nv, out);
+        return launch_check("norm2_kernel");
+    });
+}
+
 int blas_norm2(const dirac_op *op, dirac_prec p, const void *v, double *out, cudaStream_t s) {
     return dispatch_prec(p, [&](auto tag) {
         using E = std::remove_pointer_t<decltype(tag)>;
-        const int tb = red_block(op->nv);
-        norm2_kernel<E><<<red_grid(op), tb, tb * sizeof(double), s>>>((const E *)v, op->rows, op->nv, op->red_partial);
-        finalize_kernel<1><<<1, 64, 0, s>>>(op->red_partial, red_grid(op), op->nv, out);
-        return launch_check("norm2_kernel");
+        return launch_norm2<E>((const E *)v, op->rows, op->nv, p, op->red_partial, red_grid(op), out, s);
     });
 }
 
 int blas_dot(const dirac_op *op, dirac_prec p, const void *u, const void *v, double *out, cudaStream_t s) {
     return dispatch_prec(p, [&](auto tag) {
         using E = std::remove_pointer_t<decltype(tag)>;
-        const int tb = red_block(op->nv);
-        dot_kernel<E><<<red_grid(op), tb, 2 * tb * sizeof(double), s>>>((const E *)u, (const E *)v, op->rows, op->nv,
-                                                                       op->red_partial);
-        finalize_kernel<2><<<1, 64, 0, s>>>(op->red_partial, red_grid(op), op->nv, out);
-        return launch_check("dot_kernel");
+        const RedLaunch L = red_launch(p, op->nv, 2);
+        return dispatch_group(L.G, [&](auto gc) {
+            constexpr int G = decltype(gc)::value;
+            dot_kernel<E, G><<<red_grid(op), L.tb, L.sh, s>>>((const E *)u, (const E *)v, op->rows, op->nv,
+                                                              op->red_partial);
+            finalize_kernel<2><<<1, 64, 0, s>>>(op->red_partial, red_grid(op), op->nv, out);
+            return launch_check("dot_kernel");
+        });
+    });
+}
+
+int blas_dot_re(const dirac_op *op, dirac_prec p, const void *u, const void *v, double *out, cudaStream_t s) {
+    return dispatch_prec(p, [&](auto tag) {
+        using E = std::remove_pointer_t<decltype(tag)>;
+        const RedLaunch L = red_launch(p, op->nv, 2);
+        return dispatch_group(L.G, [&](auto gc) {
+            constexpr int G = decltype(gc)::value;
+            dot_kernel<E, G><<<red_grid(op), L.tb, L.sh, s>>>((const E *)u, (const E *)v, op->rows, op->nv,
+                                                              op->red_partial);
+            finalize_re_kernel<<<1, 64, 0, s>>>(op->red_partial, red_grid(op), op->nv, out);
+            return launch_check("dot_kernel");
+        });
     });
 }
 
@@ -196,16 +337,34 @@ int blas_axpby(const dirac_op *op, dirac_prec p, void *z, const void *x, const d
                const double *b, double bs, double *norm_out, cudaStream_t s) {
     return dispatch_prec(p, [&](auto tag) {
         using E = std::remove_pointer_t<decltype(tag)>;
-        const int tb = red_block(op->nv);
-        axpby_kernel<E><<<red_grid(op), tb, tb * sizeof(double), s>>>(
-            (E *)z, (const E *)x, (const E *)y, a, as, b, bs, op->rows, op->nv, norm_out ? op->red_partial : nullptr);
-        if (norm_out) finalize_kernel<1><<<1, 64, 0, s>>>(op->red_partial, red_grid(op), op->nv, norm_out);
-        return launch_check("axpby_kernel");
+        const RedLaunch L = red_launch(p, op->nv, 1);
+        return dispatch_group(L.G, [&](auto gc) {
+            constexpr int G = decltype(gc)::value;
+            axpby_kernel<E, G><<<red_grid(op), L.tb, L.sh, s>>>((E *)z, (const E *)x, (const E *)y, a, as, b, bs,
+                                                                op->rows, op->nv,
+                                                                norm_out ? op->red_partial : nullptr);
+            if (norm_out) finalize_kernel<1><<<1, 64, 0, s>>>(op->red_partial, red_grid(op), op->nv, norm_out);
+            return launch_check("axpby_kernel");
+        });
     });
 }
 
 int blas_axpy(const dirac_op *op, dirac_prec p, const double *alpha, const void *x, void *y, cudaStream_t s) {
     return blas_axpby(op, p, y, x, alpha, 1.0, y, nullptr, 1.0, nullptr, s);
+}
+
+int blas_update_xp(const dirac_op *op, dirac_prec p, void *x, void *pv, const void *r, const double *a,
+                   const double *b, cudaStream_t s) {
+    return dispatch_prec(p, [&](auto tag) {
+        using E = std::remove_pointer_t<decltype(tag)>;
+        const RedLaunch L = red_launch(p, op->nv, 1);
+        return dispatch_group(L.G, [&](auto gc) {
+            constexpr int G = decltype(gc)::value;
+            update_xp_kernel<E, G><<<red_grid(op), L.tb, 0, s>>>((E *)x, (E *)pv, (const E *)r, a, b, op->rows,
+                                                                 op->nv);
+            return launch_check("update_xp_kernel");
+        });
+    });
 }
 
 int blas_gamma5(const dirac_op *op, dirac_prec p, void *v, cudaStream_t s) {
@@ -271,15 +430,13 @@ extern "C" int dirac_vec_norm2_noalloc(const void *v, dirac_prec prec, long long
     int rc = DIRAC_OK;
     double *partial = noalloc_partial_ptr(&rc);
     if (rc) return rc;
-    const int tb = red_block(nv);
-    const int R = tb / nv;
+    const RedLaunch L = red_launch(prec, nv, 1);
+    const int R = L.tb / (nv / L.G);
     long long want = (rows + R - 1) / R;
     const int blocks = (int)(want < DIRAC_NOALLOC_MAX_BLOCKS ? want : DIRAC_NOALLOC_MAX_BLOCKS);
     cudaStream_t s = (cudaStream_t)stream;
     return dispatch_prec(prec, [&](auto tag) {
         using E = std::remove_pointer_t<decltype(tag)>;
-        norm2_kernel<E><<<blocks, tb, tb * sizeof(double), s>>>((const E *)v, rows, nv, partial);
-        finalize_kernel<1><<<1, 64, 0, s>>>(partial, blocks, nv, out_dev);
-        return launch_check("norm2_kernel (noalloc)");
+        return launch_norm2<E>((const E *)v, rows, nv, prec, partial, blocks, out_dev, s);
     });
 }

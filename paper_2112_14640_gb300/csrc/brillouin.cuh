@@ -21,8 +21,8 @@
 
 namespace dgb {
 
-template <int NC, int VR, typename E, int MINB, int LAYOUT>
-__global__ void __launch_bounds__(kStencilBlock, (MINB > 1 ? MINB : 0)) brillouin_kernel(const E *__restrict__ W, const E *__restrict__ in,
+template <int NC, int VR, typename E, int MINB, int LAYOUT, typename EL>
+__global__ void __launch_bounds__(stencil_max_threads(MINB), (MINB > 1 ? 1 : 0)) brillouin_kernel(const EL *__restrict__ W, const E *__restrict__ in,
                                                         E *__restrict__ out, Lat g, typename Acc<E>::T centre,
                                                         typename Acc<E>::T sgn) {
     using A = typename Acc<E>::T;
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(kStencilBlock, (MINB > 1 ? MINB : 0)) brilloui
                     const A ml = -l;
 
                     cx<A> Wm[NC][NC];
-                    load_mat_s<NC, E, A>(W + 2 * L::template mat<NC>(g, n, 80, dirp), ws, Wm);
+                    load_mat_s<NC, EL, A>(W + 2 * L::template mat<NC>(g, n, 80, dirp), ws, Wm);
                     const long long m = tzy * g.nx + xs[ix];
                     const E *pm = in + 2 * (L::vec(g, m, NC * 4, 0) + (long long)j * VR);
 #pragma unroll
@@ -120,10 +120,10 @@ __global__ void __launch_bounds__(kStencilBlock, (MINB > 1 ? MINB : 0)) brilloui
         }
 }
 
-template <typename E>
-int launch_brillouin_t(const dirac_op *op, const void *in, void *out, double m0, int sgn, cudaStream_t s) {
-    int vr, minb;
-    launch_variant(op, vr, minb);
+template <typename E, int LAYOUT, typename EL>
+int launch_brillouin_v(const dirac_op *op, const void *in, void *out, double m0, int sgn, cudaStream_t s) {
+    int vr, minb, block;
+    launch_variant(op, vr, minb, block);
     using A = typename Acc<E>::T;
     return dispatch_nc(op->nc, [&](auto ncc) {
         constexpr int NC = decltype(ncc)::value;
@@ -131,15 +131,15 @@ int launch_brillouin_t(const dirac_op *op, const void *in, void *out, double m0,
             constexpr int VR = decltype(vrc)::value;
             return dispatch_minb<NC>(minb, [&](auto mbc) {
             constexpr int MINB = decltype(mbc)::value;
-            return dispatch_layout(op->geom.layout, [&](auto lyc) {
-                constexpr int LAYOUT = decltype(lyc)::value;
+            {
                 const long long threads = op->V * (op->nv / VR);
-                const int block = kStencilBlock;
                 // m0 - lambda_0 / 2 = m0 + 240/128
-                brillouin_kernel<NC, VR, E, MINB, LAYOUT><<<grid_for(threads, block), block, 0, s>>>(
-                    (const E *)op->w, (const E *)in, (E *)out, op->lat, (A)(m0 + 240.0 / 128.0), (A)sgn);
+                {
+                brillouin_kernel<NC, VR, E, MINB, LAYOUT, EL><<<grid_for(threads, block), block, 0, s>>>(
+                    (const EL *)op->w, (const E *)in, (E *)out, op->lat, (A)(m0 + 240.0 / 128.0), (A)sgn);
                 return launch_check("brillouin_kernel");
-            });
+                }
+            }
             });
         });
     });

@@ -1,0 +1,6 @@
+// brillouin_bf16_l0.cu -- one instantiation of the brillouin stencil (bf16 vectors, layout 0, bf16 links); see brillouin.cuh.
+#include "brillouin.cuh"
+
+namespace dgb {
+template int launch_brillouin_v<__nv_bfloat16, 0, __nv_bfloat16>(const dirac_op *, const void *, void *, double, int, cudaStream_t);
+}  // namespace dgb

@@ -1,0 +1,6 @@
+// brillouin_f16f_l1.cu -- one instantiation of the brillouin stencil (f16 vectors, layout 1, FP32 links); see brillouin.cuh.
+#include "brillouin.cuh"
+
+namespace dgb {
+template int launch_brillouin_v<__half, 1, float>(const dirac_op *, const void *, void *, double, int, cudaStream_t);
+}  // namespace dgb

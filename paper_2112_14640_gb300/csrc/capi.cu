@@ -7,6 +7,7 @@
 #include <map>
 #include <mutex>
 #include <tuple>
+#include <vector>
 
 #include "internal.h"
 
@@ -32,7 +33,8 @@ int op_apply_normal(const dirac_op *op, const void *in, void *out, double m0, cu
 
 static void op_free(dirac_op *op) {
     if (!op) return;
-    for (int i = 0; i < 4; ++i) op_free(op->inner[i]);
+    for (int i = 0; i < 4; ++i)
+        for (int k = 0; k < 2; ++k) op_free(op->inner[i][k]);
     cudaFree(op->links);
     cudaFree(op->w);
     cudaFree(op->scratch);
@@ -56,6 +58,9 @@ static int validate_geom(dirac_kind kind, const dirac_geom *g) {
     if (g->nv < 1 || g->nv > 64) return DIRAC_ERR_INVALID_ARG;
     if (g->prec < DIRAC_F64 || g->prec > DIRAC_F16) return DIRAC_ERR_UNSUPPORTED_PREC;
     if (g->layout != DIRAC_LAYOUT_SITE_OUTER && g->layout != DIRAC_LAYOUT_SITE_INNER) return DIRAC_ERR_INVALID_ARG;
+    if (g->link_storage != DIRAC_LINKS_NATIVE && g->link_storage != DIRAC_LINKS_F32) return DIRAC_ERR_INVALID_ARG;
+    if (g->link_storage == DIRAC_LINKS_F32 && g->prec != DIRAC_BF16 && g->prec != DIRAC_F16)
+        return DIRAC_ERR_UNSUPPORTED_PREC;
     return DIRAC_OK;
 }
 
@@ -71,8 +76,11 @@ static int alloc(void **p, size_t bytes) {
 // Process-wide memory of autotuned launch variants, keyed by what decides
 // the kernel's behaviour.
 using TuneKey = std::tuple<int, int, int, int, long long>;
+struct TuneVal {
+    int vr, minb, block;
+};
 static std::mutex g_tune_mu;
-static std::map<TuneKey, std::pair<int, int>> g_tune;
+static std::map<TuneKey, TuneVal> g_tune;
 
 static TuneKey tune_key(const dirac_op *op) {
     return TuneKey{(int)op->kind * 2 + op->geom.layout, (int)op->prec, op->nc, op->nv, op->V};
@@ -80,15 +88,16 @@ static TuneKey tune_key(const dirac_op *op) {
 
 static void remember_tuning(const dirac_op *op) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune[tune_key(op)] = {op->vr, op->minb};
+    g_tune[tune_key(op)] = TuneVal{op->vr, op->minb, op->block};
 }
 
 static void recall_tuning(dirac_op *op) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(tune_key(op));
     if (it != g_tune.end()) {
-        op->vr = it->second.first;
-        op->minb = it->second.second;
+        op->vr = it->second.vr;
+        op->minb = it->second.minb;
+        op->block = it->second.block;
     }
 }
 
@@ -104,10 +113,10 @@ int op_alloc(dirac_kind kind, const dirac_geom *g, dirac_op **out) {
     op->V = (long long)g->dims[0] * g->dims[1] * g->dims[2] * g->dims[3];
     op->lat = Lat{g->dims[0], g->dims[1], g->dims[2], g->dims[3], g->nv, op->V};
     op->rows = op->V * op->nc * (kind == DIRAC_STAGGERED ? 1 : 4);
-    const size_t eb = elem_bytes(op->prec);
+    const size_t eb = elem_bytes(op->prec), lb = elem_bytes(link_prec(op));
     op->vec_bytes = (size_t)op->rows * op->nv * 2 * eb;
-    op->link_bytes = (size_t)op->V * 4 * op->nc * op->nc * 2 * eb;
-    op->w_bytes = kind == DIRAC_BRILLOUIN ? (size_t)op->V * 80 * op->nc * op->nc * 2 * eb : 0;
+    op->link_bytes = (size_t)op->V * 4 * op->nc * op->nc * 2 * lb;
+    op->w_bytes = kind == DIRAC_BRILLOUIN ? (size_t)op->V * 80 * op->nc * op->nc * 2 * lb : 0;
     // one reduction block per 2 SMs' worth of work, at most 1216 blocks
     long long want = (op->rows + 255) / 256;
     op->red_blocks = (int)(want < 1216 ? (want < 1 ? 1 : want) : 1216);
@@ -125,15 +134,17 @@ int op_alloc(dirac_kind kind, const dirac_geom *g, dirac_op **out) {
 }
 
 // Lower-precision twin of op (same links/W converted), created once.
-int op_inner(const dirac_op *op, dirac_prec p, dirac_op **out, cudaStream_t s) {
+int op_inner(const dirac_op *op, dirac_prec p, int link_storage, dirac_op **out, cudaStream_t s) {
     if (p == op->prec) {
         *out = (dirac_op *)op;
         return DIRAC_OK;
     }
+    if (p != DIRAC_BF16 && p != DIRAC_F16) link_storage = DIRAC_LINKS_NATIVE;
     dirac_op *self = (dirac_op *)op;
-    if (!self->inner[p]) {
+    if (!self->inner[p][link_storage]) {
         dirac_geom g = op->geom;
         g.prec = p;
+        g.link_storage = link_storage;
         dirac_op *tw = nullptr;
         int rc = op_alloc(op->kind, &g, &tw);
         if (rc) return rc;
@@ -142,9 +153,9 @@ int op_inner(const dirac_op *op, dirac_prec p, dirac_op **out, cudaStream_t s) {
             op_free(tw);
             return rc;
         }
-        self->inner[p] = tw;
+        self->inner[p][link_storage] = tw;
     }
-    *out = self->inner[p];
+    *out = self->inner[p][link_storage];
     return DIRAC_OK;
 }
 
@@ -165,10 +176,11 @@ static int load_links(dirac_op *op, const void *U, dirac_prec u_prec, cudaStream
     if (!rc && op->kind == DIRAC_BRILLOUIN) rc = launch_build_w(op, U, u_prec, s);
     if (!rc) rc = cuda_check(cudaStreamSynchronize(s), "link setup");
     // twins built from older links are stale now
-    for (int i = 0; i < 4; ++i) {
-        op_destroy(op->inner[i]);
-        op->inner[i] = nullptr;
-    }
+    for (int i = 0; i < 4; ++i)
+        for (int k = 0; k < 2; ++k) {
+            op_destroy(op->inner[i][k]);
+            op->inner[i][k] = nullptr;
+        }
     return rc;
 }
 
@@ -209,21 +221,24 @@ void dirac_op_destroy(dirac_op *op) { op_destroy(op); }
 
 size_t dirac_vec_bytes(const dirac_op *op) { return op ? op->vec_bytes : 0; }
 
-int dirac_op_set_launch(dirac_op *op, int vr, int minb) {
+int dirac_op_set_launch(dirac_op *op, int vr, int minb, int block) {
     if (!op) return DIRAC_ERR_INVALID_ARG;
     if (vr == 0) {
-        op->vr = op->minb = 0;
+        op->vr = op->minb = op->block = 0;
         return DIRAC_OK;
     }
     if (!variant_compiled(op->nc, vr, minb) || op->nv % vr) return DIRAC_ERR_INVALID_ARG;
+    if (block == 0) block = kStencilBlock;
+    if (block < 32 || block % 32 || block > stencil_max_threads(minb)) return DIRAC_ERR_INVALID_ARG;
     op->vr = vr;
     op->minb = minb;
+    op->block = block;
     return DIRAC_OK;
 }
 
-int dirac_op_get_launch(const dirac_op *op, int *vr, int *minb) {
-    if (!op || !vr || !minb) return DIRAC_ERR_INVALID_ARG;
-    launch_variant(op, *vr, *minb);
+int dirac_op_get_launch(const dirac_op *op, int *vr, int *minb, int *block) {
+    if (!op || !vr || !minb || !block) return DIRAC_ERR_INVALID_ARG;
+    launch_variant(op, *vr, *minb, *block);
     return DIRAC_OK;
 }
 
@@ -236,53 +251,56 @@ int dirac_op_autotune(dirac_op *op, double m0, void *stream, double *best_ms) {
     // realistic operands (power draw, and hence clocks, depend on the data)
     rc = blas_fill_hash(op, op->prec, op->scratch, 12345u, s);
     if (rc) return rc;
+    struct Cand {
+        int vr, minb, block;
+        float ms;
+    };
+    std::vector<Cand> cands;
+    const int vrs[3] = {1, 2, 4}, minbs[4] = {1, 3, 4, 6}, blocks[5] = {128, 256, 384, 512, 768};
+    for (int vr : vrs)
+        for (int mb : minbs)
+            for (int bl : blocks)
+                if (variant_compiled(op->nc, vr, mb) && op->nv % vr == 0 && bl <= stencil_max_threads(mb))
+                    cands.push_back(Cand{vr, mb, bl, 1e30f});
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    const int vrs[3] = {1, 2, 4}, minbs[4] = {1, 3, 4, 6};
-    float times[3][4];
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 4; ++b) times[a][b] = 1e30f;
-    const int saved_vr = op->vr, saved_mb = op->minb;
+    const int saved_vr = op->vr, saved_mb = op->minb, saved_bl = op->block;
     // three interleaved rounds, best time per variant, so that a clock or
     // neighbour transient does not decide the choice
     for (int round = 0; round < 3 && !rc; ++round)
-        for (int a = 0; a < 3 && !rc; ++a)
-            for (int b = 0; b < 4 && !rc; ++b) {
-                if (!variant_compiled(op->nc, vrs[a], minbs[b]) || op->nv % vrs[a]) continue;
-                op->vr = vrs[a];
-                op->minb = minbs[b];
-                rc = op_apply(op, op->scratch, op->stage_out, m0, +1, s);
-                const int reps = 5;
-                cudaEventRecord(e0, s);
-                for (int r = 0; r < reps && !rc; ++r) rc = op_apply(op, op->scratch, op->stage_out, m0, +1, s);
-                cudaEventRecord(e1, s);
-                if (!rc) rc = cuda_check(cudaEventSynchronize(e1), "autotune sync");
-                float ms = 0;
-                cudaEventElapsedTime(&ms, e0, e1);
-                ms /= reps;
-                if (ms < times[a][b]) times[a][b] = ms;
-            }
-    float best = 1e30f;
-    int bvr = 0, bmb = 0;
-    for (int a = 0; a < 3; ++a)
-        for (int b = 0; b < 4; ++b)
-            if (times[a][b] < best) {
-                best = times[a][b];
-                bvr = vrs[a];
-                bmb = minbs[b];
-            }
+        for (Cand &c : cands) {
+            if (rc) break;
+            op->vr = c.vr;
+            op->minb = c.minb;
+            op->block = c.block;
+            rc = op_apply(op, op->scratch, op->stage_out, m0, +1, s);
+            const int reps = 5;
+            cudaEventRecord(e0, s);
+            for (int r = 0; r < reps && !rc; ++r) rc = op_apply(op, op->scratch, op->stage_out, m0, +1, s);
+            cudaEventRecord(e1, s);
+            if (!rc) rc = cuda_check(cudaEventSynchronize(e1), "autotune sync");
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            ms /= reps;
+            if (ms < c.ms) c.ms = ms;
+        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (rc || !bvr) {
+    const Cand *best = nullptr;
+    for (const Cand &c : cands)
+        if (!best || c.ms < best->ms) best = &c;
+    if (rc || !best) {
         op->vr = saved_vr;
         op->minb = saved_mb;
+        op->block = saved_bl;
         return rc ? rc : DIRAC_ERR_INVALID_ARG;
     }
-    op->vr = bvr;
-    op->minb = bmb;
+    op->vr = best->vr;
+    op->minb = best->minb;
+    op->block = best->block;
     remember_tuning(op);
-    if (best_ms) *best_ms = best;
+    if (best_ms) *best_ms = best->ms;
     return DIRAC_OK;
 }
 

@@ -31,8 +31,9 @@ struct dirac_op {
     int red_blocks;
     void *solver_ws;       // solver workspace (lazy), solver_ws_bytes long
     size_t solver_ws_bytes;
-    dirac_op *inner[4];    // lower-precision twins for mixed solves (lazy)
-    int vr, minb;          // stencil launch variant (RHS per thread, min blocks/SM); 0 = default
+    dirac_op *inner[4][2]; // lower-precision twins for mixed solves (lazy), by [prec][link storage]
+    int vr, minb, block;   // stencil launch variant (RHS per thread, register class, threads per block);
+                           // 0 = default
 };
 
 namespace dgb {
@@ -48,6 +49,21 @@ inline int cuda_check(cudaError_t e, const char *what) {
 inline int launch_check(const char *what) { return cuda_check(cudaGetLastError(), what); }
 
 inline size_t elem_bytes(dirac_prec p) { return p == DIRAC_F64 ? 8 : p == DIRAC_F32 ? 4 : 2; }
+
+// precision the links and W links are stored in
+inline dirac_prec link_prec(const dirac_op *op) {
+    return (op->geom.link_storage == DIRAC_LINKS_F32 && (op->prec == DIRAC_BF16 || op->prec == DIRAC_F16))
+               ? DIRAC_F32 : op->prec;
+}
+
+// dispatch the link element type EL for vectors of element type E
+template <typename E, typename F>
+int dispatch_link_elem(const dirac_op *op, F &&f) {
+    if constexpr (sizeof(E) == 2) {
+        if (link_prec(op) == DIRAC_F32) return f((float *)nullptr);
+    }
+    return f((E *)nullptr);
+}
 
 // Largest RHS-vector width (complex numbers per thread) that divides nv and
 // gives at most 16-byte loads.
@@ -89,12 +105,17 @@ int dispatch_vr(int vr, F &&f) {
     return DIRAC_ERR_INVALID_ARG;
 }
 
-// Stencil launch variants: VR right-hand sides per thread and a register cap
-// through __launch_bounds__(128, MINB).  MINB = 1 compiles with the plain
-// __launch_bounds__(128) (the compiler's own register heuristic, which differs
-// from an explicit minimum of one block).  Every (VR, MINB) pair below is
-// compiled for N_c = 3; other N_c have MINB = 1 only.
+// Stencil launch variants: VR right-hand sides per thread and a register
+// class MINB: the register cap of MINB resident 128-thread blocks per SM
+// (65536 / (128 MINB) registers), compiled as __launch_bounds__(128 MINB, 1)
+// so that blocks of up to 128 MINB threads can be launched with it; MINB = 1
+// compiles with the plain __launch_bounds__(128) (the compiler's own register
+// heuristic, which differs from an explicit minimum of one block).  Every
+// (VR, MINB) pair below is compiled for N_c = 3; other N_c have MINB = 1 only.
+// Larger blocks cover more consecutive x-rows, so more of the y-neighbours a
+// block reads are already in its SM's L1.
 constexpr int kStencilBlock = 128;
+__host__ __device__ constexpr int stencil_max_threads(int minb) { return minb > 1 ? 128 * minb : 128; }
 inline bool variant_compiled(int nc, int vr, int minb) {
     if (vr != 1 && vr != 2 && vr != 4) return false;
     if (minb == 1) return true;
@@ -124,15 +145,17 @@ int dispatch_minb(int minb, F &&f) {
     return DIRAC_ERR_INVALID_ARG;
 }
 
-// (vr, minb) an operator launches with: its tuned choice or the default.
-inline void launch_variant(const dirac_op *op, int &vr, int &minb) {
+// (vr, minb, block) an operator launches with: its tuned choice or the default.
+inline void launch_variant(const dirac_op *op, int &vr, int &minb, int &block) {
     if (op->vr) {
         vr = op->vr;
         minb = op->minb ? op->minb : 1;
+        block = op->block ? op->block : kStencilBlock;
         return;
     }
     vr = pick_vr(op->prec, op->nv);
     minb = 1;
+    block = kStencilBlock;
 }
 
 inline unsigned grid_for(long long threads, int block) {
@@ -152,11 +175,16 @@ int launch_convert_links(const dirac_op *src, dirac_op *dst, cudaStream_t s);
 // BLAS-1 (vectors in precision p with op's shape)
 int blas_norm2(const dirac_op *op, dirac_prec p, const void *v, double *out, cudaStream_t s);
 int blas_dot(const dirac_op *op, dirac_prec p, const void *u, const void *v, double *out, cudaStream_t s);
+// Re <u, v> per column: out[v] (N_v doubles)
+int blas_dot_re(const dirac_op *op, dirac_prec p, const void *u, const void *v, double *out, cudaStream_t s);
 int blas_axpy(const dirac_op *op, dirac_prec p, const double *alpha, const void *x, void *y, cudaStream_t s);
 // z = a x + b y per RHS; a = as * a_coef[v] (complex pairs) or as when a_coef is null (same for b);
 // x or y may be null; z may alias x or y; norm_out (device, nv doubles) receives |z|^2 if non-null.
 int blas_axpby(const dirac_op *op, dirac_prec p, void *z, const void *x, const double *a_coef, double as,
                const void *y, const double *b_coef, double bs, double *norm_out, cudaStream_t s);
+// x += a p, then p = r + b p (a, b per-RHS complex pairs)
+int blas_update_xp(const dirac_op *op, dirac_prec p, void *x, void *pv, const void *r, const double *a,
+                   const double *b, cudaStream_t s);
 int blas_gamma5(const dirac_op *op, dirac_prec p, void *v, cudaStream_t s);
 int blas_fill_hash(const dirac_op *op, dirac_prec p, void *v, unsigned seed, cudaStream_t s);
 int blas_convert(const dirac_op *op, const void *src, dirac_prec sp, void *dst, dirac_prec dp, cudaStream_t s);
@@ -165,7 +193,7 @@ int blas_convert(const dirac_op *op, const void *src, dirac_prec sp, void *dst, 
 int op_apply(const dirac_op *op, const void *in, void *out, double m0, int sgn, cudaStream_t s);
 int op_apply_normal(const dirac_op *op, const void *in, void *out, double m0, cudaStream_t s);
 int op_alloc(dirac_kind kind, const dirac_geom *g, dirac_op **out);
-int op_inner(const dirac_op *op, dirac_prec p, dirac_op **out, cudaStream_t s);
+int op_inner(const dirac_op *op, dirac_prec p, int link_storage, dirac_op **out, cudaStream_t s);
 void op_destroy(dirac_op *op);
 
 }  // namespace dgb

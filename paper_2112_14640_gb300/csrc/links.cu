@@ -136,7 +136,7 @@ static Phases phases_of(const dirac_op *op) {
 int launch_phase_links(dirac_op *op, const void *U, dirac_prec u_prec, cudaStream_t s) {
     return dispatch_uprec(u_prec, [&](auto utag) {
         using UE = std::remove_pointer_t<decltype(utag)>;
-        return dispatch_prec(op->prec, [&](auto tag) {
+        return dispatch_prec(link_prec(op), [&](auto tag) {
             using E = std::remove_pointer_t<decltype(tag)>;
             const long long threads = op->V * 4;
             phase_links_kernel<UE, E><<<grid_for(threads, 128), 128, 0, s>>>((const UE *)U, (E *)op->links,
@@ -150,7 +150,7 @@ int launch_phase_links(dirac_op *op, const void *U, dirac_prec u_prec, cudaStrea
 int launch_build_w(dirac_op *op, const void *U, dirac_prec u_prec, cudaStream_t s) {
     return dispatch_uprec(u_prec, [&](auto utag) {
         using UE = std::remove_pointer_t<decltype(utag)>;
-        return dispatch_prec(op->prec, [&](auto tag) {
+        return dispatch_prec(link_prec(op), [&](auto tag) {
             using E = std::remove_pointer_t<decltype(tag)>;
             return dispatch_nc(op->nc, [&](auto ncc) {
                 constexpr int NC = decltype(ncc)::value;
@@ -181,11 +181,11 @@ static int convert_array(const void *src, dirac_prec sp, void *dst, dirac_prec d
 
 int launch_convert_links(const dirac_op *src, dirac_op *dst, cudaStream_t s) {
     long long n = src->V * 4 * src->nc * src->nc * 2;
-    int rc = convert_array(src->links, src->prec, dst->links, dst->prec, n, s);
+    int rc = convert_array(src->links, link_prec(src), dst->links, link_prec(dst), n, s);
     if (rc) return rc;
     if (src->kind == DIRAC_BRILLOUIN) {
         n = src->V * 80 * src->nc * src->nc * 2;
-        rc = convert_array(src->w, src->prec, dst->w, dst->prec, n, s);
+        rc = convert_array(src->w, link_prec(src), dst->w, link_prec(dst), n, s);
     }
     return rc;
 }

@@ -58,6 +58,12 @@ static int get_ws(const dirac_op *op, Ws &w) {
 // The operator's solver workspace: the first nvecs vectors and the scalar
 // area (arrays of 2*64 doubles in the order rr, rr_new, pq, alpha, beta, act,
 // nb, ...), for drivers in other translation units.
+static int apply_A_pq(const dirac_op *op, const void *p, void *q, double *pq, double m0, cudaStream_t s);
+
+int batch_apply_A_pq(const dirac_op *op, const void *p, void *q, double *pq, double m0, cudaStream_t s) {
+    return apply_A_pq(op, p, q, pq, m0, s);
+}
+
 int solver_ws(const dirac_op *op, void **vecs, int nvecs, double **scal) {
     Ws w;
     int rc = get_ws(op, w);
@@ -68,10 +74,11 @@ int solver_ws(const dirac_op *op, void **vecs, int nvecs, double **scal) {
 }
 
 // ---------------------------------------------------------------- coefficient kernels
+// alpha = rr / <p, A p>; pq holds N_v real values <p, D^dag D p> = |D p|^2
 __global__ void cg_alpha_kernel(int nv, const double *rr, const double *pq, const double *act, double *alpha) {
     const int v = threadIdx.x;
     if (v >= nv) return;
-    const double p = pq[2 * v];
+    const double p = pq[v];
     const double a = (act[v] != 0.0 && p != 0.0) ? rr[v] / p : 0.0;
     alpha[2 * v] = a;
     alpha[2 * v + 1] = 0.0;
@@ -188,8 +195,8 @@ struct Lanczos {
     std::vector<double> alpha[kNS], beta[kNS];
     void add(int nv, const double *act, const double *rr, const double *pq, const double *rn) {
         for (int v = 0; v < nv; ++v) {
-            if (act[v] == 0.0 || pq[2 * v] <= 0.0 || rr[v] <= 0.0) continue;
-            alpha[v].push_back(rr[v] / pq[2 * v]);
+            if (act[v] == 0.0 || pq[v] <= 0.0 || rr[v] <= 0.0) continue;
+            alpha[v].push_back(rr[v] / pq[v]);
             beta[v].push_back(rn[v] / rr[v]);
         }
     }
@@ -247,6 +254,20 @@ static int apply_A(const dirac_op *op, const void *in, void *out, double m0, cud
     return op_apply_normal(op, in, out, m0, s);
 }
 
+// q = D^dag D p through the operator scratch, with pq = <p, q> per RHS.  In
+// FP32/FP64 storage pq is taken as |D p|^2 (one reduction over the
+// intermediate instead of a dot product over p and q).  With 16-bit storage
+// the two differ by the rounding of D p and of q, and the step length has to
+// match the q that is subtracted from r, so there pq = Re <p, q> itself.
+static int apply_A_pq(const dirac_op *op, const void *p, void *q, double *pq, double m0, cudaStream_t s) {
+    const bool half = op->prec == DIRAC_BF16 || op->prec == DIRAC_F16;
+    int rc = op_apply(op, p, op->scratch, m0, +1, s);
+    if (!rc && !half) rc = blas_norm2(op, op->prec, op->scratch, pq, s);
+    if (!rc) rc = op_apply(op, op->scratch, q, m0, -1, s);
+    if (!rc && half) rc = blas_dot_re(op, op->prec, p, q, pq, s);
+    return rc;
+}
+
 // CG on A x = rhs (A = D^dag D), x in/out.  Uses ws vectors 0..2.
 static int cg_core(const dirac_op *op, const void *rhs, void *x, double m0, double tol, int maxit, int every,
                    CoreOut &out, cudaStream_t s, Lanczos *lan = nullptr) {
@@ -276,14 +297,12 @@ static int cg_core(const dirac_op *op, const void *rhs, void *x, double m0, doub
     int it = 0;
     while (nact > 0) {
         ++it;
-        TRY(apply_A(op, pv, q, m0, s));
-        TRY(blas_dot(op, p, pv, q, w.pq, s));
+        TRY(apply_A_pq(op, pv, q, w.pq, m0, s));
         cg_alpha_kernel<<<1, kNS, 0, s>>>(nv, w.rr, w.pq, w.act, w.alpha);
-        TRY(blas_axpby(op, p, x, x, nullptr, 1.0, pv, w.alpha, 1.0, nullptr, s));
         TRY(blas_axpby(op, p, r, r, nullptr, 1.0, q, w.alpha, -1.0, w.rr_new, s));
-        double rn[kNS], pq[2 * kNS], rro[kNS];
+        double rn[kNS], pq[kNS], rro[kNS];
         if (lan) {
-            TRY(cuda_check(cudaMemcpyAsync(pq, w.pq, 2 * nv * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H"));
+            TRY(cuda_check(cudaMemcpyAsync(pq, w.pq, nv * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H"));
             TRY(cuda_check(cudaMemcpyAsync(rro, w.rr, nv * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H"));
         }
         TRY(to_host(rn, w.rr_new, nv, s));
@@ -297,7 +316,10 @@ static int cg_core(const dirac_op *op, const void *rhs, void *x, double m0, doub
             out.status = DIRAC_NONFINITE;
             break;
         }
-        if (it % every == 0 || all_pass || it >= maxit) {
+        const bool recompute = it % every == 0 || all_pass || it >= maxit;
+        if (recompute) {
+            // the solution update is needed now; otherwise it is fused with p below
+            TRY(blas_axpby(op, p, x, x, nullptr, 1.0, pv, w.alpha, 1.0, nullptr, s));
             out.recomputes++;
             TRY(apply_A(op, x, q, m0, s));
             TRY(blas_axpby(op, p, r, rhs, nullptr, 1.0, q, nullptr, -1.0, w.rr_new, s));
@@ -330,7 +352,8 @@ static int cg_core(const dirac_op *op, const void *rhs, void *x, double m0, doub
             }
         }
         cg_beta_kernel<<<1, kNS, 0, s>>>(nv, w.rr_new, w.rr, w.act, w.beta);
-        TRY(blas_axpby(op, p, pv, r, nullptr, 1.0, pv, w.beta, 1.0, nullptr, s));
+        if (recompute) TRY(blas_axpby(op, p, pv, r, nullptr, 1.0, pv, w.beta, 1.0, nullptr, s));
+        else TRY(blas_update_xp(op, p, x, pv, r, w.alpha, w.beta, s));   // x += alpha p; p = r + beta p
     }
     out.iters = it;
     TRY(launch_check("cg coefficient kernels"));
@@ -530,14 +553,12 @@ static int cg_reliable(const dirac_op *hi, const dirac_op *lo, const void *rhs, 
     int it = 0;
     while (nact > 0) {
         ++it;
-        TRY(apply_A(lo, ps, qs, m0, s));
-        TRY(blas_dot(lo, pl, ps, qs, wl.pq, s));
+        TRY(apply_A_pq(lo, ps, qs, wl.pq, m0, s));
         cg_alpha_kernel<<<1, kNS, 0, s>>>(nv, wl.rr, wl.pq, wl.act, wl.alpha);
-        TRY(blas_axpby(lo, pl, ys, ys, nullptr, 1.0, ps, wl.alpha, 1.0, nullptr, s));
         TRY(blas_axpby(lo, pl, rs, rs, nullptr, 1.0, qs, wl.alpha, -1.0, wl.rr_new, s));
-        double rn[kNS], pq[2 * kNS], rro[kNS];
+        double rn[kNS], pq[kNS], rro[kNS];
         if (lan) {
-            TRY(cuda_check(cudaMemcpyAsync(pq, wl.pq, 2 * nv * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H"));
+            TRY(cuda_check(cudaMemcpyAsync(pq, wl.pq, nv * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H"));
             TRY(cuda_check(cudaMemcpyAsync(rro, wl.rr, nv * sizeof(double), cudaMemcpyDeviceToHost, s), "D2H"));
         }
         TRY(to_host(rn, wl.rr_new, nv, s));
@@ -563,6 +584,7 @@ static int cg_reliable(const dirac_op *hi, const dirac_op *lo, const void *rhs, 
         }
         if (trigger) {
             out.recomputes++;
+            TRY(blas_axpby(lo, pl, ys, ys, nullptr, 1.0, ps, wl.alpha, 1.0, nullptr, s));
             // x += y / sigma, then the true residual in the high precision
             inverse_kernel<<<1, kNS, 0, s>>>(nv, sig, inv);
             TRY(blas_convert(lo, ys, pl, th, ph, s));
@@ -636,7 +658,8 @@ static int cg_reliable(const dirac_op *hi, const dirac_op *lo, const void *rhs, 
             for (int v = 0; v < nv; ++v) rmax[v] = fmax(rmax[v], sqrt(rn[v]));
         }
         cg_beta_kernel<<<1, kNS, 0, s>>>(nv, wl.rr_new, wl.rr, wl.act, wl.beta);
-        TRY(blas_axpby(lo, pl, ps, rs, nullptr, 1.0, ps, wl.beta, 1.0, nullptr, s));
+        if (trigger) TRY(blas_axpby(lo, pl, ps, rs, nullptr, 1.0, ps, wl.beta, 1.0, nullptr, s));
+        else TRY(blas_update_xp(lo, pl, ys, ps, rs, wl.alpha, wl.beta, s));   // y += alpha p; p = r + beta p
     }
     out.iters = it;
     TRY(launch_check("reliable-update kernels"));
@@ -656,7 +679,7 @@ static double default_inner_tol(dirac_prec p) {
 static int mixed_solve(const dirac_op *op, const void *b, void *x, double m0, const dirac_solve_params *prm,
                        dirac_solve_stats *st, cudaStream_t s) {
     dirac_op *lo = nullptr;
-    TRY(op_inner(op, prm->inner_prec, &lo, s));
+    TRY(op_inner(op, prm->inner_prec, prm->sloppy_links, &lo, s));
     Ws wh, wl;
     TRY(get_ws(op, wh));
     TRY(get_ws(lo, wl));
@@ -733,7 +756,7 @@ static void lanczos_stats(const Lanczos &lan, int nv, dirac_solve_stats *st) {
 static int reliable_solve(const dirac_op *op, const void *b, void *x, double m0, const dirac_solve_params *prm,
                           dirac_solve_stats *st, cudaStream_t s) {
     dirac_op *lo = nullptr;
-    TRY(op_inner(op, prm->inner_prec, &lo, s));
+    TRY(op_inner(op, prm->inner_prec, prm->sloppy_links, &lo, s));
     Ws w;
     TRY(get_ws(op, w));
     void *rhs = w.v[5];
@@ -832,5 +855,7 @@ extern "C" int dirac_solve(const dirac_op *op, const void *b, void *x, double m0
     if (params->mixed_mode != DIRAC_MIXED_RELIABLE && params->mixed_mode != DIRAC_MIXED_RESTART)
         return DIRAC_ERR_INVALID_ARG;
     if (params->delta < 0 || params->delta >= 1) return DIRAC_ERR_INVALID_ARG;
+    if (params->sloppy_links != DIRAC_LINKS_NATIVE && params->sloppy_links != DIRAC_LINKS_F32)
+        return DIRAC_ERR_INVALID_ARG;
     return dgb::solve(op, b, x, m0, params, stats, (cudaStream_t)stream);
 }

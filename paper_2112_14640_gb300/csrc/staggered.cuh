@@ -13,11 +13,11 @@
 
 namespace dgb {
 
-template <int NC, int VR, bool DAG, typename E, typename A>
-__device__ __forceinline__ void stag_hop(cx<A> (&acc)[NC][VR], const E *__restrict__ link, long long lstride,
+template <int NC, int VR, bool DAG, typename E, typename A, typename EL>
+__device__ __forceinline__ void stag_hop(cx<A> (&acc)[NC][VR], const EL *__restrict__ link, long long lstride,
                                          const E *__restrict__ phi, long long cs_stride, A f) {
     cx<A> L[NC][NC];
-    load_mat_s<NC, E, A>(link, lstride, L);
+    load_mat_s<NC, EL, A>(link, lstride, L);
     cx<A> p[NC][VR];
 #pragma unroll
     for (int c = 0; c < NC; ++c) load_cx<E, VR, A>(phi + 2 * c * cs_stride, p[c]);
@@ -35,8 +35,8 @@ __device__ __forceinline__ void stag_hop(cx<A> (&acc)[NC][VR], const E *__restri
         }
 }
 
-template <int NC, int VR, typename E, int MINB, int LAYOUT>
-__global__ void __launch_bounds__(kStencilBlock, (MINB > 1 ? MINB : 0)) staggered_kernel(const E *__restrict__ U, const E *__restrict__ in,
+template <int NC, int VR, typename E, int MINB, int LAYOUT, typename EL>
+__global__ void __launch_bounds__(stencil_max_threads(MINB), (MINB > 1 ? 1 : 0)) staggered_kernel(const EL *__restrict__ U, const E *__restrict__ in,
                                                         E *__restrict__ out, Lat g, typename Acc<E>::T mass,
                                                         typename Acc<E>::T half_sgn) {
     using A = typename Acc<E>::T;
@@ -83,10 +83,10 @@ __global__ void __launch_bounds__(kStencilBlock, (MINB > 1 ? MINB : 0)) staggere
     }
 }
 
-template <typename E>
-int launch_staggered_t(const dirac_op *op, const void *in, void *out, double m0, int sgn, cudaStream_t s) {
-    int vr, minb;
-    launch_variant(op, vr, minb);
+template <typename E, int LAYOUT, typename EL>
+int launch_staggered_v(const dirac_op *op, const void *in, void *out, double m0, int sgn, cudaStream_t s) {
+    int vr, minb, block;
+    launch_variant(op, vr, minb, block);
     using A = typename Acc<E>::T;
     return dispatch_nc(op->nc, [&](auto ncc) {
         constexpr int NC = decltype(ncc)::value;
@@ -94,14 +94,14 @@ int launch_staggered_t(const dirac_op *op, const void *in, void *out, double m0,
             constexpr int VR = decltype(vrc)::value;
             return dispatch_minb<NC>(minb, [&](auto mbc) {
             constexpr int MINB = decltype(mbc)::value;
-            return dispatch_layout(op->geom.layout, [&](auto lyc) {
-                constexpr int LAYOUT = decltype(lyc)::value;
+            {
                 const long long threads = op->V * (op->nv / VR);
-                const int block = kStencilBlock;
-                staggered_kernel<NC, VR, E, MINB, LAYOUT><<<grid_for(threads, block), block, 0, s>>>(
-                    (const E *)op->links, (const E *)in, (E *)out, op->lat, (A)m0, (A)(0.5 * sgn));
+                {
+                staggered_kernel<NC, VR, E, MINB, LAYOUT, EL><<<grid_for(threads, block), block, 0, s>>>(
+                    (const EL *)op->links, (const E *)in, (E *)out, op->lat, (A)m0, (A)(0.5 * sgn));
                 return launch_check("staggered_kernel");
-            });
+                }
+            }
             });
         });
     });

@@ -1,0 +1,6 @@
+// staggered_f16f_l0.cu -- one instantiation of the staggered stencil (f16 vectors, layout 0, FP32 links); see staggered.cuh.
+#include "staggered.cuh"
+
+namespace dgb {
+template int launch_staggered_v<__half, 0, float>(const dirac_op *, const void *, void *, double, int, cudaStream_t);
+}  // namespace dgb

@@ -61,11 +61,11 @@ __device__ __forceinline__ void reconstruct(cx<A> &o0, cx<A> &o1, cx<A> &o2, cx<
 // One hop: acc += (1 + a gamma_MU) (x) L psi(m), L = link or link^dag.  The
 // link elements are lstride complex numbers apart, the spinor components
 // cs_stride apart (both depend on the layout).
-template <int MU, bool DAG, int NC, int VR, typename E, typename A>
-__device__ __forceinline__ void wilson_hop(cx<A> (&acc)[NC][4][VR], const E *__restrict__ link, long long lstride,
+template <int MU, bool DAG, int NC, int VR, typename E, typename A, typename EL>
+__device__ __forceinline__ void wilson_hop(cx<A> (&acc)[NC][4][VR], const EL *__restrict__ link, long long lstride,
                                            const E *__restrict__ psi, long long cs_stride, A a) {
     cx<A> L[NC][NC];
-    load_mat_s<NC, E, A>(link, lstride, L);
+    load_mat_s<NC, EL, A>(link, lstride, L);
     cx<A> h[NC][2][VR];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
@@ -95,8 +95,8 @@ __device__ __forceinline__ void wilson_hop(cx<A> (&acc)[NC][4][VR], const E *__r
     }
 }
 
-template <int MU, int NC, int VR, int LAYOUT, typename E, typename A>
-__device__ __forceinline__ void wilson_dir(cx<A> (&acc)[NC][4][VR], const E *__restrict__ U,
+template <int MU, int NC, int VR, int LAYOUT, typename E, typename A, typename EL>
+__device__ __forceinline__ void wilson_dir(cx<A> (&acc)[NC][4][VR], const EL *__restrict__ U,
                                            const E *__restrict__ in, const Lat &g, long long n, const Coord &c,
                                            int j, A sgn) {
     using L = Layout<LAYOUT>;
@@ -111,8 +111,8 @@ __device__ __forceinline__ void wilson_dir(cx<A> (&acc)[NC][4][VR], const E *__r
                                  in + 2 * (L::vec(g, bw, NC * 4, 0) + (long long)j * VR), cs, sgn);
 }
 
-template <int NC, int VR, typename E, int MINB, int LAYOUT>
-__global__ void __launch_bounds__(kStencilBlock, (MINB > 1 ? MINB : 0)) wilson_kernel(const E *__restrict__ U, const E *__restrict__ in,
+template <int NC, int VR, typename E, int MINB, int LAYOUT, typename EL>
+__global__ void __launch_bounds__(stencil_max_threads(MINB), (MINB > 1 ? 1 : 0)) wilson_kernel(const EL *__restrict__ U, const E *__restrict__ in,
                                                      E *__restrict__ out, Lat g, typename Acc<E>::T diag,
                                                      typename Acc<E>::T sgn) {
     using A = typename Acc<E>::T;
@@ -131,10 +131,10 @@ __global__ void __launch_bounds__(kStencilBlock, (MINB > 1 ? MINB : 0)) wilson_k
 #pragma unroll
             for (int v = 0; v < VR; ++v) acc[a][s][v] = cx<A>{0, 0};
 
-    wilson_dir<0, NC, VR, LAYOUT, E, A>(acc, U, in, g, n, c, j, sgn);
-    wilson_dir<1, NC, VR, LAYOUT, E, A>(acc, U, in, g, n, c, j, sgn);
-    wilson_dir<2, NC, VR, LAYOUT, E, A>(acc, U, in, g, n, c, j, sgn);
-    wilson_dir<3, NC, VR, LAYOUT, E, A>(acc, U, in, g, n, c, j, sgn);
+    wilson_dir<0, NC, VR, LAYOUT, E, A, EL>(acc, U, in, g, n, c, j, sgn);
+    wilson_dir<1, NC, VR, LAYOUT, E, A, EL>(acc, U, in, g, n, c, j, sgn);
+    wilson_dir<2, NC, VR, LAYOUT, E, A, EL>(acc, U, in, g, n, c, j, sgn);
+    wilson_dir<3, NC, VR, LAYOUT, E, A, EL>(acc, U, in, g, n, c, j, sgn);
 
     const long long base = 2 * (Layout<LAYOUT>::vec(g, n, NC * 4, 0) + (long long)j * VR);
     const long long cs = Layout<LAYOUT>::cs_stride(g);
@@ -155,10 +155,10 @@ __global__ void __launch_bounds__(kStencilBlock, (MINB > 1 ? MINB : 0)) wilson_k
         }
 }
 
-template <typename E>
-int launch_wilson_t(const dirac_op *op, const void *in, void *out, double m0, int sgn, cudaStream_t s) {
-    int vr, minb;
-    launch_variant(op, vr, minb);
+template <typename E, int LAYOUT, typename EL>
+int launch_wilson_v(const dirac_op *op, const void *in, void *out, double m0, int sgn, cudaStream_t s) {
+    int vr, minb, block;
+    launch_variant(op, vr, minb, block);
     using A = typename Acc<E>::T;
     return dispatch_nc(op->nc, [&](auto ncc) {
         constexpr int NC = decltype(ncc)::value;
@@ -166,14 +166,14 @@ int launch_wilson_t(const dirac_op *op, const void *in, void *out, double m0, in
             constexpr int VR = decltype(vrc)::value;
             return dispatch_minb<NC>(minb, [&](auto mbc) {
             constexpr int MINB = decltype(mbc)::value;
-            return dispatch_layout(op->geom.layout, [&](auto lyc) {
-                constexpr int LAYOUT = decltype(lyc)::value;
+            {
                 const long long threads = op->V * (op->nv / VR);
-                const int block = kStencilBlock;
-                wilson_kernel<NC, VR, E, MINB, LAYOUT><<<grid_for(threads, block), block, 0, s>>>(
-                    (const E *)op->links, (const E *)in, (E *)out, op->lat, (A)(4.0 + m0), (A)sgn);
+                {
+                wilson_kernel<NC, VR, E, MINB, LAYOUT, EL><<<grid_for(threads, block), block, 0, s>>>(
+                    (const EL *)op->links, (const E *)in, (E *)out, op->lat, (A)(4.0 + m0), (A)sgn);
                 return launch_check("wilson_kernel");
-            });
+                }
+            }
             });
         });
     });

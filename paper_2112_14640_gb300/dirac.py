@@ -31,17 +31,19 @@ _TORCH_DTYPE = {F64: torch.complex128, F32: torch.complex64, BF16: torch.bfloat1
 
 
 SITE_OUTER, SITE_INNER = 0, 1   # vector layouts (include/dirac.h)
+LINKS_NATIVE, LINKS_F32 = 0, 1  # link storage of 16-bit operators
 
 
 class Geom(ctypes.Structure):
     _fields_ = [("dims", ctypes.c_int * 4), ("nc", ctypes.c_int), ("nv", ctypes.c_int),
-                ("bc", ctypes.c_int * 4), ("prec", ctypes.c_int), ("layout", ctypes.c_int)]
+                ("bc", ctypes.c_int * 4), ("prec", ctypes.c_int), ("layout", ctypes.c_int),
+                ("link_storage", ctypes.c_int)]
 
 
 class SolveParams(ctypes.Structure):
     _fields_ = [("solver", ctypes.c_int), ("tol", ctypes.c_double), ("maxit", ctypes.c_int),
                 ("inner_prec", ctypes.c_int), ("inner_tol", ctypes.c_double), ("recompute_every", ctypes.c_int),
-                ("mixed_mode", ctypes.c_int), ("delta", ctypes.c_double)]
+                ("mixed_mode", ctypes.c_int), ("sloppy_links", ctypes.c_int), ("delta", ctypes.c_double)]
 
 
 class SolveStats(ctypes.Structure):
@@ -70,8 +72,8 @@ SIGNATURES = {
     "dirac_apply_dagger": (_I, [_P, _P, _P, _D, _P]),
     "dirac_apply_normal": (_I, [_P, _P, _P, _D, _P]),
     "dirac_apply_host": (_I, [_P, _P, _P, _D, _I, _P]),
-    "dirac_op_set_launch": (_I, [_P, _I, _I]),
-    "dirac_op_get_launch": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I)]),
+    "dirac_op_set_launch": (_I, [_P, _I, _I, _I]),
+    "dirac_op_get_launch": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "dirac_op_autotune": (_I, [_P, _D, _P, ctypes.POINTER(_D)]),
     "dirac_vec_bytes": (_SZ, [_P]),
     "dirac_vec_norm2": (_I, [_P, _P, _P, _P]),
@@ -137,7 +139,8 @@ def _ptr(t):
 class DiracOp:
     """One of D_W, D_B, D_S on a fixed gauge field, for N_v right-hand sides."""
 
-    def __init__(self, kind, U, nv, bc=(1, 1, 1, 1), prec=F32, stream=None, layout=SITE_OUTER):
+    def __init__(self, kind, U, nv, bc=(1, 1, 1, 1), prec=F32, stream=None, layout=SITE_OUTER,
+                 link_storage=LINKS_NATIVE):
         if not U.is_cuda:
             raise ValueError("U must be a CUDA tensor")
         if U.dtype not in (torch.complex128, torch.complex64):
@@ -151,7 +154,7 @@ class DiracOp:
         self.device = U.device
         g = Geom()
         g.dims[:] = self.dims
-        g.nc, g.nv, g.prec, g.layout = self.nc, self.nv, self.prec, self.layout
+        g.nc, g.nv, g.prec, g.layout, g.link_storage = self.nc, self.nv, self.prec, self.layout, int(link_storage)
         g.bc[:] = self.bc
         self._geom = g
         h = ctypes.c_void_p()
@@ -228,14 +231,15 @@ class DiracOp:
             return torch.view_as_complex(v.float().contiguous())
         return v
 
-    def set_launch(self, vr, minb=1):
-        """Pick the stencil launch variant (vr RHS per thread, minb blocks/SM register cap)."""
-        _check(lib().dirac_op_set_launch(self._h, int(vr), int(minb)), "dirac_op_set_launch")
+    def set_launch(self, vr, minb=1, block=0):
+        """Pick the stencil launch variant (vr RHS per thread, register class minb, threads per block)."""
+        _check(lib().dirac_op_set_launch(self._h, int(vr), int(minb), int(block)), "dirac_op_set_launch")
 
     def get_launch(self):
-        vr, mb = ctypes.c_int(), ctypes.c_int()
-        _check(lib().dirac_op_get_launch(self._h, ctypes.byref(vr), ctypes.byref(mb)), "dirac_op_get_launch")
-        return vr.value, mb.value
+        vr, mb, bl = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().dirac_op_get_launch(self._h, ctypes.byref(vr), ctypes.byref(mb), ctypes.byref(bl)),
+               "dirac_op_get_launch")
+        return vr.value, mb.value, bl.value
 
     def autotune(self, m0=0.0, stream=None):
         """Time every compiled launch variant and keep the fastest; returns ms per apply."""
@@ -328,13 +332,14 @@ class DiracOp:
 
     # ---------------------------------------------------------------- solve
     def solve(self, b, x=None, m0=0.0, solver=CG_NORMAL, tol=1e-10, maxit=10000, inner_prec=None,
-              inner_tol=0.0, recompute_every=0, mixed_mode=MIXED_RELIABLE, delta=0.0, stream=None):
+              inner_tol=0.0, recompute_every=0, mixed_mode=MIXED_RELIABLE, delta=0.0, sloppy_links=LINKS_NATIVE,
+              stream=None):
         """Solve D x = b (BiCGstab), D^dag D x = D^dag b (CG_NORMAL) or D^dag D x = b
         (CG_HPD) for all RHS.  Returns (x, stats dict); non-convergence is
         reported in the stats."""
         x = self.new_vector() if x is None else x
         p = SolveParams(int(solver), float(tol), int(maxit), int(self.prec if inner_prec is None else inner_prec),
-                        float(inner_tol), int(recompute_every), int(mixed_mode), float(delta))
+                        float(inner_tol), int(recompute_every), int(mixed_mode), int(sloppy_links), float(delta))
         st = SolveStats()
         rc = _check(lib().dirac_solve(self._h, self._vec(b, "b"), self._vec(x, "x"), float(m0), ctypes.byref(p),
                                       ctypes.byref(st), _stream(stream)), "dirac_solve")
@@ -358,7 +363,7 @@ def solve_batched(ops, bs, xs=None, m0s=None, solver=CG_NORMAL, tol=1e-6, maxit=
     pb = (P * n)(*[op._vec(b, "b") for op, b in zip(ops, bs)])
     px = (P * n)(*[op._vec(x, "x") for op, x in zip(ops, xs)])
     pm = (ctypes.c_double * n)(*[float(m) for m in m0s])
-    prm = SolveParams(int(solver), float(tol), int(maxit), int(ops[0].prec), 0.0, int(recompute_every), 0, 0.0)
+    prm = SolveParams(int(solver), float(tol), int(maxit), int(ops[0].prec), 0.0, int(recompute_every), 0, 0, 0.0)
     st = (SolveStats * n)()
     rc = _check(lib().dirac_solve_batched(n, h, pb, px, pm, ctypes.byref(prm), st, _stream(stream)),
                 "dirac_solve_batched")

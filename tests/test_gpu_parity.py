@@ -24,12 +24,13 @@ KINDS = [D.WILSON, D.BRILLOUIN, D.STAGGERED]
 LAYOUTS = [D.SITE_OUTER, D.SITE_INNER]
 
 
-def make(kind, dims, nc, nv, bc, prec, eps=0.4, seed=5, u_f32=False, layout=D.SITE_OUTER):
+def make(kind, dims, nc, nv, bc, prec, eps=0.4, seed=5, u_f32=False, layout=D.SITE_OUTER,
+         link_storage=D.LINKS_NATIVE):
     U = I.gauge_field(dims, nc, eps, seed)
     Ut = torch.from_numpy(U).cuda()
     if u_f32:
         Ut = Ut.to(torch.complex64)
-    op = D.DiracOp(kind, Ut, nv, bc, prec, layout=layout)
+    op = D.DiracOp(kind, Ut, nv, bc, prec, layout=layout, link_storage=link_storage)
     ref = O.Operator(kind, U.astype(np.complex64).astype(np.complex128) if u_f32 else U, bc)
     src = I.source(dims, nc, nv, seed + 1, staggered=(kind == D.STAGGERED))
     return op, ref, src
@@ -65,13 +66,14 @@ def test_apply_and_dagger(kind, prec, case, layout):
     op.close()
 
 
+@pytest.mark.parametrize("links", [D.LINKS_NATIVE, D.LINKS_F32])
 @pytest.mark.parametrize("layout", LAYOUTS)
 @pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("prec", [D.BF16, D.F16])
-def test_apply_low_precision_storage(kind, prec, layout):
+def test_apply_low_precision_storage(kind, prec, layout, links):
     dims, nc, nv, bc = (8, 4, 4, 8), 3, 12, (1, 1, 1, -1)
     m0 = 0.1
-    op, ref, src = make(kind, dims, nc, nv, bc, prec, layout=layout)
+    op, ref, src = make(kind, dims, nc, nv, bc, prec, layout=layout, link_storage=links)
     x = to_device(op, src)
     for dag in (False, True):
         got = to_numpy(op, op.apply(x, m0=m0, dagger=dag))
@@ -197,3 +199,22 @@ def test_error_codes_from_the_abi():
                          ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert rc == -1   # in place is rejected
     op.close()
+
+
+def test_f32_links_reduce_the_error_of_16bit_operators():
+    """With FP32 links only the rounding of the stored output remains: the
+    error of an F16 apply with F32 links equals that rounding alone, and the
+    all-F16 operator adds the link rounding on top."""
+    from helpers import rounded
+    dims, nc, nv, bc = (8, 4, 4, 8), 3, 4, (1, 1, 1, -1)
+    errs = {}
+    for links in (D.LINKS_NATIVE, D.LINKS_F32):
+        op, ref, src = make(D.WILSON, dims, nc, nv, bc, D.F16, link_storage=links)
+        srcr = rounded(src, D.F16)
+        want = ref.apply(srcr, 0.1)
+        got = to_numpy(op, op.apply(to_device(op, src), m0=0.1))
+        errs[links] = rel_l2(got, want)
+        errs["round"] = rel_l2(rounded(want, D.F16), want)
+        op.close()
+    assert errs[D.LINKS_F32] < 1.05 * errs["round"], errs
+    assert errs[D.LINKS_NATIVE] > errs[D.LINKS_F32], errs

@@ -156,3 +156,14 @@ def test_lanczos_estimates_match_dense_spectrum():
     for lo, hi in zip(st["lambda_min"], st["lambda_max"]):
         assert abs(hi - ev[-1]) < 1e-6 * ev[-1]
         assert abs(lo - ev[0]) < 1e-3 * ev[0]
+
+
+@pytest.mark.parametrize("inner", [D.BF16, D.F16])
+def test_mixed_hybrid_sloppy_links_reach_1e10(inner):
+    """16-bit sloppy vectors with FP32 sloppy links (DIRAC_LINKS_F32)."""
+    m0 = 0.05
+    op, ref, b = setup(D.STAGGERED, (4, 4, 4, 8), 3, 4, (1, 1, 1, -1), D.F64, layout=D.SITE_INNER)
+    x, st = op.solve(to_device(op, b), m0=m0, tol=1e-10, maxit=20000, inner_prec=inner,
+                     sloppy_links=D.LINKS_F32)
+    assert st["status"] == 0, st
+    assert np.all(normal_relres(ref, to_numpy(op, x), b, m0) < 1.01e-10)
