@@ -58,6 +58,9 @@ def parse():
     p.add_argument("--ncu", action="store_true", help="short run for profiler launch lists (no extras)")
     p.add_argument("--ops", default="wilson,brillouin,staggered",
                    help="profiling only: subset of operators to create and time")
+    p.add_argument("--fixed", default=None,
+                   help="profiling only: LAYOUT:VR,MINB,BLOCK (LAYOUT outer|inner), or name=LAYOUT:...;name=... per "
+                        "operator, instead of the autotuned choice")
     return p.parse_args()
 
 
@@ -258,6 +261,20 @@ def main():
         return e0.elapsed_time(e1) / reps
 
     for k in kinds:
+        if args.fixed:
+            spec = args.fixed
+            if "=" in spec:   # per operator: name=LAYOUT:VR,MINB,BLOCK;...
+                spec = dict(x.split("=") for x in spec.split(";"))[D.KIND_NAMES[k]]
+            lay_s, var = spec.split(":")
+            lay = D.SITE_INNER if lay_s == "inner" else D.SITE_OUTER
+            op = D.DiracOp(k, U, NV, BC, D.F32, layout=lay)
+            op.set_launch(*[int(v) for v in var.split(",")])
+            xs[k] = op.to_prec(op.from_site_outer(torch.from_numpy(sources[k]).cuda()))
+            ys[k] = op.new_vector(zero=False)
+            ops[k] = op
+            layout_ms[D.KIND_NAMES[k]] = {"chosen": lay_s, "fixed": True}
+            launch[D.KIND_NAMES[k]] = op.get_launch()
+            continue
         # untimed setup: for each vector layout pick the launch variant, then
         # keep the faster layout for the timed step
         cand = {}

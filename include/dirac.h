@@ -108,11 +108,16 @@ int dirac_op_create(dirac_kind kind, const dirac_geom *geom, const void *U,
  * Synchronises `stream` before returning. */
 int dirac_op_update_links(dirac_op *op, const void *U, dirac_prec u_prec, void *stream);
 
-/* Copy the operator's stored W links (Brillouin only) into w_out, layout
- * [site][80][a][b] (SITE_OUTER) or [80][a][b][site] (SITE_INNER) in
- * geom->prec, directions s = (sx,sy,sz,st) in {-1,0,1}^4
- * numbered d = (st+1)*27+(sz+1)*9+(sy+1)*3+(sx+1) with the centre d = 40
- * left out (index d for d < 40, d-1 for d > 40). */
+/* Copy the operator's W links W_s(n) (Brillouin only) into the device
+ * buffer w_out (w_bytes long, not overlapping the operator), layout
+ * [site][80][a][b] (SITE_OUTER) or [80][a][b][site] (SITE_INNER) in the
+ * link storage precision (geom->prec, FP32 with DIRAC_LINKS_F32),
+ * directions s = (sx,sy,sz,st) in {-1,0,1}^4 numbered
+ * d = (st+1)*27+(sz+1)*9+(sy+1)*3+(sx+1) with the centre d = 40 left out
+ * (index d for d < 40, d-1 for d > 40).  Internally the operator stores
+ * rho_k s_lead W_s, grouped by the axes s moves along; this call undoes the
+ * order and the scale (one kernel on `stream`), so a 16-bit value can differ
+ * from W_s rounded once by one more rounding.  Asynchronous on `stream`. */
 int dirac_op_copy_w(const dirac_op *op, void *w_out, void *stream);
 
 void dirac_op_destroy(dirac_op *op);

@@ -1,39 +1,195 @@
 // brillouin.cuh -- multi-RHS Brillouin Dirac operator, Eq. (app_bril) with
 // Eqs. (def_ider, def_blap) at r = 1, c_SW = 0:
 //   (D_B psi)(n) = (m0 - lambda_0/2) psi(n)
-//       + sum_{s in {-1,0,1}^4, s != 0} [rho_k sum_mu s_mu gamma_mu - lambda_k/2] (x) W_s(n) psi(n+s)
+//       + sum_{s in {-1,0,1}^4, s != 0} [sgn rho_k sum_mu s_mu gamma_mu - lambda_k/2] (x) W_s(n) psi(n+s)
 // rho = (64,16,4,1)/432, lambda = (-240,8,4,2,1)/64, k = |s|_1, W_s from
-// Tab. off-axis (built once per gauge field in links.cu, all 80 directions
-// stored so every output site streams its own W links).  The derivative
+// Tab. off-axis, built once per gauge field (links.cu) and stored in the
+// order q, with the scale rho_k s_lead and the layout of bril_dirs.h.  The derivative
 // carries every axis the offset moves along (sum_mu s_mu gamma_mu), the
-// reading of Eq. (def_ider).  D_B^dag = gamma5 D_B gamma5 flips the sign of
-// the derivative part only (sgn = -1).
+// reading of Eq. (def_ider).  sgn = +1 gives D_B, sgn = -1 gives
+// D_B^dag = gamma5 D_B gamma5 (the derivative part flips sign).
 //
-// Per offset the spin matrix Gamma_s = G - l with G = sum_mu a_mu gamma_mu
-// acts first, in the chiral basis of App. A:
-//   G psi = ( conj(P) p2 - Q p3,  conj(Q) p2 + P p3,  P p0 + Q p1,  -conj(Q) p0 + conj(P) p1 ),
-//   P = a_t + i a_z,  Q = a_y + i a_x,
-// then the colour matrix W_s(n) multiplies the result into the register
-// accumulator; each W_s(n) is loaded once and used for all 4 spins and the
-// thread's VR right-hand sides.
+// With the stored W~ = rho_k s_lead W_s every offset contributes
+//   sgn * W~ [ sum_{mu in M} e_mu gamma_mu psi(n+s) + d psi(n+s) ],
+//   e_mu = s_lead s_mu,  d = -sgn c_k s_lead,
+// and the common factor sgn is applied once to the accumulated sum.  The
+// offsets are visited group by group of equal support M (a compile-time
+// mask), so the gamma matrices of the axes outside M cost nothing: in the
+// chiral basis of App. A each gamma_mu is a signed permutation of the spin
+// components, and the spin combination costs 8k real FMAs per colour and RHS
+// instead of 40.  Inside a group the 2^k sign patterns run in a loop, the W~
+// of the next offset is loaded while the current one is applied, and each W~
+// is used for all 4 spins and the thread's VR right-hand sides.
 #pragma once
+#include "bril_dirs.h"
 #include "internal.h"
 
 namespace dgb {
+namespace bril {
+
+// phase * p[pi] of gamma_mu acting on spin S (chiral basis of App. A):
+//   t: pi = (2,3,0,1), phases ( 1,  1, 1,  1)    z: pi = (2,3,0,1), phases (-i, i, i, -i)
+//   y: pi = (3,2,1,0), phases (-1,  1, 1, -1)    x: pi = (3,2,1,0), phases (-i, -i, i, i)
+template <int MU, int S, typename A>
+__device__ __forceinline__ cx<A> gamma_term(const cx<A> (&p)[4]) {
+    constexpr int PI = MU >= 2 ? (S ^ 2) : (3 - S);
+    // 0: +1, 1: -1, 2: +i, 3: -i
+    constexpr int PH = MU == 3 ? 0
+                     : MU == 2 ? ((S == 0 || S == 3) ? 3 : 2)
+                     : MU == 1 ? ((S == 0 || S == 3) ? 1 : 0)
+                               : (S <= 1 ? 3 : 2);
+    const cx<A> v = p[PI];
+    if constexpr (PH == 0) return v;
+    else if constexpr (PH == 1) return cx<A>{-v.re, -v.im};
+    else if constexpr (PH == 2) return cx<A>{-v.im, v.re};
+    else return cx<A>{v.im, -v.re};
+}
+
+// f += e_mu * (gamma_mu p)_S for the axes MU.. of M other than the lead
+template <int M, int S, int MU, typename A>
+__device__ __forceinline__ void add_axes(cx<A> &f, const cx<A> (&p)[4], const A (&e)[4]) {
+    if constexpr (MU < 4) {
+        if constexpr (((M >> MU) & 1) && MU != lead_axis(M)) {
+            const cx<A> t = gamma_term<MU, S>(p);
+            f.re = fma(e[MU], t.re, f.re);
+            f.im = fma(e[MU], t.im, f.im);
+        }
+        add_axes<M, S, MU + 1>(f, p, e);
+    }
+}
+
+// spin component S of  sum_{mu in M} e_mu gamma_mu p + d p
+template <int M, int S, typename A>
+__device__ __forceinline__ cx<A> spin_mix(const cx<A> (&p)[4], const A (&e)[4], A d) {
+    cx<A> f = gamma_term<lead_axis(M), S>(p);
+    add_axes<M, S, 0>(f, p, e);
+    f.re = fma(d, p[S].re, f.re);
+    f.im = fma(d, p[S].im, f.im);
+    return f;
+}
+
+template <int NC, int VR, typename E, typename EL, int LAYOUT>
+struct Ctx {
+    using A = typename Acc<E>::T;
+    const EL *wp;          // this site's W~ (offset 0, element 0)
+    long long dq, ws;      // W~ stride per offset, per matrix element (in elements)
+    const E *in;
+    long long n;           // output site
+    long long vbase;       // offset of this thread's RHS inside a site (complex numbers)
+    int dp[4], dm[4];      // site-index offsets of n + mu and n - mu (periodic)
+    Lat g;
+    A sgn;
+};
+
+// The 2^k offsets of support M: their signs run in a loop, everything that
+// depends on M alone is fixed at compile time.
+template <int M, int NC, int VR, typename E, typename EL, int LAYOUT, typename A>
+__device__ __forceinline__ void group(const Ctx<NC, VR, E, EL, LAYOUT> &C, int &q, cx<A> (&Wc)[NC][NC],
+                                      cx<A> (&acc)[NC][4][VR]) {
+    using L = Layout<LAYOUT>;
+    constexpr int K = popc4(M);
+    const A ck = (A)c_lambda(K);
+    const long long cs = L::cs_stride(C.g);
+#pragma unroll 1
+    for (int b = 0; b < (1 << K); ++b) {
+        A sig[4] = {1, 1, 1, 1};
+        long long m = C.n;
+        {
+            int jbit = 0;
+#pragma unroll
+            for (int mu = 0; mu < 4; ++mu) {
+                if ((M >> mu) & 1) {
+                    const bool neg = (b >> jbit) & 1;
+                    sig[mu] = neg ? (A)-1 : (A)1;
+                    m += neg ? C.dm[mu] : C.dp[mu];
+                    ++jbit;
+                }
+            }
+        }
+        const A sl = sig[lead_axis(M)];
+        A e[4];
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) e[mu] = sig[mu] * sl;
+        const A d = -C.sgn * ck * sl;
+
+        // the next offset's W~ (storage order = visiting order)
+        cx<A> Wn[NC][NC];
+        if (q + 1 < 80) load_mat_s<NC, EL, A>(C.wp + (long long)(q + 1) * C.dq, C.ws, Wn);
+
+        const E *pm = C.in + 2 * (L::vec(C.g, m, NC * 4, 0) + C.vbase);
+#pragma unroll
+        for (int kc = 0; kc < NC; ++kc) {
+            cx<A> p[4][VR];
+#pragma unroll
+            for (int s = 0; s < 4; ++s) load_cx<E, VR, A>(pm + 2 * (kc * 4 + s) * cs, p[s]);
+#pragma unroll
+            for (int v = 0; v < VR; ++v) {
+                const cx<A> pv[4] = {p[0][v], p[1][v], p[2][v], p[3][v]};
+                const cx<A> f0 = spin_mix<M, 0>(pv, e, d);
+                const cx<A> f1 = spin_mix<M, 1>(pv, e, d);
+                const cx<A> f2 = spin_mix<M, 2>(pv, e, d);
+                const cx<A> f3 = spin_mix<M, 3>(pv, e, d);
+#pragma unroll
+                for (int a = 0; a < NC; ++a) {
+                    cmac(acc[a][0][v], Wc[a][kc], f0);
+                    cmac(acc[a][1][v], Wc[a][kc], f1);
+                    cmac(acc[a][2][v], Wc[a][kc], f2);
+                    cmac(acc[a][3][v], Wc[a][kc], f3);
+                }
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < NC; ++a)
+#pragma unroll
+            for (int c = 0; c < NC; ++c) Wc[a][c] = Wn[a][c];
+        ++q;
+    }
+}
+
+template <int M, int NC, int VR, typename E, typename EL, int LAYOUT, typename A>
+__device__ __forceinline__ void groups_from(const Ctx<NC, VR, E, EL, LAYOUT> &C, int &q, cx<A> (&Wc)[NC][NC],
+                                            cx<A> (&acc)[NC][4][VR]) {
+    if constexpr (M <= 15) {
+        group<M>(C, q, Wc, acc);
+        groups_from<M + 1>(C, q, Wc, acc);
+    }
+}
+
+}  // namespace bril
 
 template <int NC, int VR, typename E, int MINB, int LAYOUT, typename EL>
-__global__ void __launch_bounds__(stencil_max_threads(MINB), (MINB > 1 ? 1 : 0)) brillouin_kernel(const EL *__restrict__ W, const E *__restrict__ in,
-                                                        E *__restrict__ out, Lat g, typename Acc<E>::T centre,
-                                                        typename Acc<E>::T sgn) {
+__global__ void __launch_bounds__(stencil_max_threads(MINB), (MINB > 1 ? 1 : 0))
+    brillouin_kernel(const EL *__restrict__ W, const E *__restrict__ in, E *__restrict__ out, Lat g,
+                     typename Acc<E>::T centre, typename Acc<E>::T sgn) {
     using A = typename Acc<E>::T;
+    using L = Layout<LAYOUT>;
     const int nchunk = g.nv / VR;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= g.V * nchunk) return;
     const long long n = tid / nchunk;
     const int j = (int)(tid - n * nchunk);
     const Coord c = site_coords(g, n);
-    using L = Layout<LAYOUT>;
-    const long long cs = L::cs_stride(g), ws = L::mat_stride(g);
+
+    bril::Ctx<NC, VR, E, EL, LAYOUT> C;
+    C.g = g;
+    C.in = in;
+    C.n = n;
+    C.sgn = sgn;
+    C.vbase = (long long)j * VR;
+    C.ws = L::mat_stride(g);
+    C.dq = 2LL * NC * NC * L::mat_stride(g);
+    C.wp = W + 2 * L::template mat<NC>(g, n, 80, 0);
+    {
+        const int co[4] = {c.x, c.y, c.z, c.t};
+        const int ext[4] = {g.nx, g.ny, g.nz, g.nt};
+        int stride = 1;
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            C.dp[mu] = (co[mu] == ext[mu] - 1 ? -(ext[mu] - 1) : 1) * stride;
+            C.dm[mu] = (co[mu] == 0 ? ext[mu] - 1 : -1) * stride;
+            stride *= ext[mu];
+        }
+    }
 
     cx<A> acc[NC][4][VR];
 #pragma unroll
@@ -43,66 +199,12 @@ __global__ void __launch_bounds__(stencil_max_threads(MINB), (MINB > 1 ? 1 : 0))
 #pragma unroll
             for (int v = 0; v < VR; ++v) acc[a][s][v] = cx<A>{0, 0};
 
-    const int xs[3] = {c.x == 0 ? g.nx - 1 : c.x - 1, c.x, c.x == g.nx - 1 ? 0 : c.x + 1};
-    const int ys[3] = {c.y == 0 ? g.ny - 1 : c.y - 1, c.y, c.y == g.ny - 1 ? 0 : c.y + 1};
-    const int zs[3] = {c.z == 0 ? g.nz - 1 : c.z - 1, c.z, c.z == g.nz - 1 ? 0 : c.z + 1};
-    const int ts[3] = {c.t == 0 ? g.nt - 1 : c.t - 1, c.t, c.t == g.nt - 1 ? 0 : c.t + 1};
+    cx<A> Wc[NC][NC];
+    load_mat_s<NC, EL, A>(C.wp, C.ws, Wc);
+    int q = 0;
+    bril::groups_from<1>(C, q, Wc, acc);
 
-    for (int it = 0; it < 3; ++it) {
-        for (int iz = 0; iz < 3; ++iz) {
-            const long long tz = (long long)ts[it] * g.nz + zs[iz];
-            for (int iy = 0; iy < 3; ++iy) {
-                const long long tzy = tz * g.ny + ys[iy];
-#pragma unroll
-                for (int ix = 0; ix < 3; ++ix) {
-                    const int dir = it * 27 + iz * 9 + iy * 3 + ix;
-                    if (dir == 40) continue;
-                    const int dirp = dir < 40 ? dir : dir - 1;
-                    const int k = (it != 1) + (iz != 1) + (iy != 1) + (ix != 1);
-                    const A rho = k == 1 ? (A)(64.0 / 432.0) : k == 2 ? (A)(16.0 / 432.0)
-                                : k == 3 ? (A)(4.0 / 432.0) : (A)(1.0 / 432.0);
-                    const A l = k == 1 ? (A)(8.0 / 128.0) : k == 2 ? (A)(4.0 / 128.0)
-                              : k == 3 ? (A)(2.0 / 128.0) : (A)(1.0 / 128.0);
-                    const A sr = sgn * rho;
-                    const cx<A> P = {sr * (A)(it - 1), sr * (A)(iz - 1)};
-                    const cx<A> Q = {sr * (A)(iy - 1), sr * (A)(ix - 1)};
-                    const cx<A> mQ = {-Q.re, -Q.im};
-                    const A ml = -l;
-
-                    cx<A> Wm[NC][NC];
-                    load_mat_s<NC, EL, A>(W + 2 * L::template mat<NC>(g, n, 80, dirp), ws, Wm);
-                    const long long m = tzy * g.nx + xs[ix];
-                    const E *pm = in + 2 * (L::vec(g, m, NC * 4, 0) + (long long)j * VR);
-#pragma unroll
-                    for (int kc = 0; kc < NC; ++kc) {
-                        cx<A> p[4][VR];
-#pragma unroll
-                        for (int s = 0; s < 4; ++s) load_cx<E, VR, A>(pm + 2 * (kc * 4 + s) * cs, p[s]);
-#pragma unroll
-                        for (int v = 0; v < VR; ++v) {
-                            cx<A> f0 = ml * p[0][v], f1 = ml * p[1][v], f2 = ml * p[2][v], f3 = ml * p[3][v];
-                            cmac_conj(f0, P, p[2][v]);
-                            cmac(f0, mQ, p[3][v]);
-                            cmac_conj(f1, Q, p[2][v]);
-                            cmac(f1, P, p[3][v]);
-                            cmac(f2, P, p[0][v]);
-                            cmac(f2, Q, p[1][v]);
-                            cmac_conj(f3, mQ, p[0][v]);
-                            cmac_conj(f3, P, p[1][v]);
-#pragma unroll
-                            for (int a = 0; a < NC; ++a) {
-                                cmac(acc[a][0][v], Wm[a][kc], f0);
-                                cmac(acc[a][1][v], Wm[a][kc], f1);
-                                cmac(acc[a][2][v], Wm[a][kc], f2);
-                                cmac(acc[a][3][v], Wm[a][kc], f3);
-                            }
-                        }
-                    }
-                }
-            }
-        }
-    }
-
+    const long long cs = L::cs_stride(g);
     const long long base = 2 * (L::vec(g, n, NC * 4, 0) + (long long)j * VR);
 #pragma unroll
     for (int a = 0; a < NC; ++a)
@@ -113,8 +215,8 @@ __global__ void __launch_bounds__(stencil_max_threads(MINB), (MINB > 1 ? 1 : 0))
             load_cx<E, VR, A>(in + off, p);
 #pragma unroll
             for (int v = 0; v < VR; ++v) {
-                o[v] = acc[a][s][v];
-                rmac(o[v], centre, p[v]);
+                o[v] = cx<A>{centre * p[v].re, centre * p[v].im};
+                rmac(o[v], sgn, acc[a][s][v]);
             }
             store_cx<E, VR, A>(out + off, o);
         }

@@ -213,8 +213,7 @@ int dirac_op_update_links(dirac_op *op, const void *U, dirac_prec u_prec, void *
 
 int dirac_op_copy_w(const dirac_op *op, void *w_out, void *stream) {
     if (!op || !w_out || op->kind != DIRAC_BRILLOUIN) return DIRAC_ERR_INVALID_ARG;
-    return cuda_check(cudaMemcpyAsync(w_out, op->w, op->w_bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream),
-                      "copy W");
+    return launch_unpack_w(op, w_out, (cudaStream_t)stream);
 }
 
 void dirac_op_destroy(dirac_op *op) { op_destroy(op); }

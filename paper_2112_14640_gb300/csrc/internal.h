@@ -134,15 +134,16 @@ int dispatch_layout(int layout, F &&f) {
 template <int NC, typename F>
 int dispatch_minb(int minb, F &&f) {
     if constexpr (NC != 3) {
-        return f(std::integral_constant<int, 1>{});
+        return minb == 1 ? f(std::integral_constant<int, 1>{}) : DIRAC_ERR_INVALID_ARG;
+    } else {
+        switch (minb) {
+        case 1: return f(std::integral_constant<int, 1>{});
+        case 3: return f(std::integral_constant<int, 3>{});
+        case 4: return f(std::integral_constant<int, 4>{});
+        case 6: return f(std::integral_constant<int, 6>{});
+        }
+        return DIRAC_ERR_INVALID_ARG;
     }
-    if (minb == 1) return f(std::integral_constant<int, 1>{});
-    switch (minb) {
-    case 3: return f(std::integral_constant<int, 3>{});
-    case 4: return f(std::integral_constant<int, 4>{});
-    case 6: return f(std::integral_constant<int, 6>{});
-    }
-    return DIRAC_ERR_INVALID_ARG;
 }
 
 // (vr, minb, block) an operator launches with: its tuned choice or the default.
@@ -170,6 +171,8 @@ int launch_brillouin(const dirac_op *op, const void *in, void *out, double m0, i
 // link preparation
 int launch_phase_links(dirac_op *op, const void *U, dirac_prec u_prec, cudaStream_t s);
 int launch_build_w(dirac_op *op, const void *U, dirac_prec u_prec, cudaStream_t s);
+// the stored W~ (order and scale of bril_dirs.h) back to W_s in the public order
+int launch_unpack_w(const dirac_op *op, void *out, cudaStream_t s);
 int launch_convert_links(const dirac_op *src, dirac_op *dst, cudaStream_t s);
 
 // BLAS-1 (vectors in precision p with op's shape)

@@ -8,6 +8,7 @@
 //      W_s(n) = (1/k) sum_{mu: s_mu != 0} W_{s - s_mu mu}(n) V_{s_mu mu}(n + s - s_mu mu),
 //    evaluated level by level (k = 1..4) in shared memory, in FP64, one
 //    thread block per site; the result is stored in the operator precision.
+#include "bril_dirs.h"
 #include "internal.h"
 
 namespace dgb {
@@ -110,14 +111,48 @@ __global__ void __launch_bounds__(96) build_w_kernel(const UE *__restrict__ U, E
         __syncthreads();
     }
     if (dir < 81 && dir != 40) {
-        const int dirp = dir < 40 ? dir : dir - 1;
+        // stored as rho_k s_lead W_s at index q (bril_dirs.h)
+        double scale;
+        const int q = bril::store_index(s, &scale);
         for (int e = 0; e < NC * NC; ++e) {
-            // [site][dir][a][b] (site-outer) or [dir][a][b][site] (site-inner)
-            const long long o = layout == 0 ? (n * 80 + dirp) * NC * NC + e : ((long long)dirp * NC * NC + e) * g.V + n;
-            W[2 * o] = from_acc<E, double>(Ws[dir][e].re);
-            W[2 * o + 1] = from_acc<E, double>(Ws[dir][e].im);
+            // [site][q][a][b] (site-outer) or [q][a][b][site] (site-inner)
+            const long long o = bril::w_index(q, e, n, g.V, NC, layout);
+            W[2 * o] = from_acc<E, double>(scale * Ws[dir][e].re);
+            W[2 * o + 1] = from_acc<E, double>(scale * Ws[dir][e].im);
         }
     }
+}
+
+// The stored W~ back to W_s in the public order d = (st+1)*27 + (sz+1)*9 +
+// (sy+1)*3 + (sx+1), centre left out, in the operator's layout and link precision.
+template <typename E>
+__global__ void unpack_w_kernel(const E *__restrict__ Wst, E *__restrict__ out, Lat g, int nc, int layout) {
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;   // (site, dirp)
+    if (tid >= g.V * 80) return;
+    const long long n = tid / 80;
+    const int dirp = (int)(tid % 80);
+    const int dir = dirp < 40 ? dirp : dirp + 1;
+    const int s[4] = {dir % 3 - 1, (dir / 3) % 3 - 1, (dir / 9) % 3 - 1, dir / 27 - 1};
+    double scale;
+    const int q = bril::store_index(s, &scale);
+    const int per = nc * nc;
+    for (int e = 0; e < per; ++e) {
+        const long long i = bril::w_index(q, e, n, g.V, nc, layout);
+        const long long o = layout == 0 ? (n * 80 + dirp) * per + e : ((long long)dirp * per + e) * g.V + n;
+        using A = typename Acc<E>::T;
+        out[2 * o] = from_acc<E, double>((double)to_acc<E>(Wst[2 * i]) / scale);
+        out[2 * o + 1] = from_acc<E, double>((double)to_acc<E>(Wst[2 * i + 1]) / scale);
+    }
+}
+
+int launch_unpack_w(const dirac_op *op, void *out, cudaStream_t s) {
+    return dispatch_prec(link_prec(op), [&](auto tag) {
+        using E = std::remove_pointer_t<decltype(tag)>;
+        const long long threads = op->V * 80;
+        unpack_w_kernel<E><<<grid_for(threads, 128), 128, 0, s>>>((const E *)op->w, (E *)out, op->lat, op->nc,
+                                                                  op->geom.layout);
+        return launch_check("unpack_w_kernel");
+    });
 }
 
 template <typename F>
@@ -184,6 +219,7 @@ int launch_convert_links(const dirac_op *src, dirac_op *dst, cudaStream_t s) {
     int rc = convert_array(src->links, link_prec(src), dst->links, link_prec(dst), n, s);
     if (rc) return rc;
     if (src->kind == DIRAC_BRILLOUIN) {
+        // same order, scale and layout, element by element
         n = src->V * 80 * src->nc * src->nc * 2;
         rc = convert_array(src->w, link_prec(src), dst->w, link_prec(dst), n, s);
     }
