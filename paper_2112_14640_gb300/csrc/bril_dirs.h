@@ -8,7 +8,8 @@
 // b, bit j of b set when the j-th axis of M (in increasing mu) has s_mu = -1.
 // Storage index q = group_offset(M) + b.
 //
-// With k = |s|_1 and lead(M) the lowest axis of M, the stored matrix is
+// With k = |s|_1 and lead(M) the highest axis of M (t when s moves in time,
+// whose gamma matrix is a plain permutation), the stored matrix is
 //   W~_q(n) = rho_k * s_lead * W_s(n),
 // which turns the spin factor rho_k sum_mu s_mu gamma_mu - lambda_k/2 of
 // Eq. (app_bril) into  sum_mu e_mu gamma_mu - c_k s_lead  with e_mu = s_lead s_mu
@@ -19,7 +20,7 @@ namespace dgb {
 namespace bril {
 
 __host__ __device__ constexpr int popc4(int m) { return (m & 1) + ((m >> 1) & 1) + ((m >> 2) & 1) + ((m >> 3) & 1); }
-__host__ __device__ constexpr int lead_axis(int m) { return (m & 1) ? 0 : (m & 2) ? 1 : (m & 4) ? 2 : 3; }
+__host__ __device__ constexpr int lead_axis(int m) { return (m & 8) ? 3 : (m & 4) ? 2 : (m & 2) ? 1 : 0; }
 // number of stored offsets before group M
 __host__ __device__ constexpr int group_offset(int m) {
     int o = 0;
