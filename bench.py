@@ -93,7 +93,8 @@ def ncu_traffic(op_name):
     try:
         text = open(prof).read()
         h = hashlib.sha256()
-        for f in ("%s.cuh" % op_name, "common.cuh"):
+        srcs = ("%s.cuh" % op_name,) + (("bril_dirs.h",) if op_name == "brillouin" else ()) + ("common.cuh",)
+        for f in srcs:
             h.update(open(os.path.join(csrc, f), "rb").read())
         fields = dict(l.split(":", 1) for l in text.splitlines() if ":" in l and not l.startswith(("#", " ", "|")))
         if fields.get("kernel_source_sha256_16", "").strip() != h.hexdigest()[:16]:
