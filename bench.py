@@ -510,9 +510,16 @@ def solver_comparison(D, I, torch):
     out = {}
     U = torch.from_numpy(I.gauge_field(dims, NC, 0.6, 99)).cuda()
     for kind in (D.STAGGERED, D.WILSON):
-        op = D.DiracOp(kind, U, NV, BC, D.F64)
-        op32 = D.DiracOp(kind, U, NV, BC, D.F32)
-        src = torch.from_numpy(I.source(dims, NC, NV, 5, staggered=(kind == D.STAGGERED))).cuda()
+        op = D.DiracOp(kind, U, NV, BC, D.F64, layout=D.SITE_INNER)
+        # tune the launch variants of the sloppy operators first: the solver's
+        # internal lower-precision twins pick the tuning up by their shape
+        for prec, links in ((D.F32, D.LINKS_NATIVE), (D.F16, D.LINKS_F32), (D.BF16, D.LINKS_F32),
+                            (D.F16, D.LINKS_NATIVE), (D.BF16, D.LINKS_NATIVE)):
+            tw = D.DiracOp(kind, U, NV, BC, prec, layout=D.SITE_INNER, link_storage=links)
+            tw.autotune(0.1 if kind == D.WILSON else 0.05)
+            tw.close()
+        op32 = D.DiracOp(kind, U, NV, BC, D.F32, layout=D.SITE_INNER)
+        src = op.from_site_outer(torch.from_numpy(I.source(dims, NC, NV, 5, staggered=(kind == D.STAGGERED))).cuda())
         m0, info = tune_mass(D, op32, op32.to_prec(src), kind, torch_mod=torch)
         op32.close()
         b = op.to_prec(src)

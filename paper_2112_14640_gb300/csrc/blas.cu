@@ -2,11 +2,22 @@
 // a vector is a [rows][nv] array of complex numbers (rows = sites x internal
 // dofs), and every operation acts column by column with its own coefficient.
 //
-// Reductions (norm^2, dot) accumulate in FP64 whatever the storage precision
-// (Sec. 3 accumulates sp norms in dp) and are deterministic: a fixed grid of
-// blocks, thread (r, v) of a block owns column v, partial sums are combined in
-// a fixed tree inside the block and then summed in block order by a second
-// one-block kernel.
+// Reductions (norm^2, dot) carry at least FP64-like precision whatever the
+// storage precision (Sec. 3 accumulates sp norms in dp) and are
+// deterministic: a fixed grid of blocks, thread (r, v) of a block owns column
+// v, partial sums are combined in a fixed tree inside the block and then
+// summed in block order by a second one-block kernel.  FP64 vectors
+// accumulate in FP64.  FP32 and 16-bit vectors accumulate per thread in FP32
+// with error-free transformations (Dekker's product, Knuth's two-sum): every
+// product is split exactly into a rounded part and its error, the rounded
+// parts are summed with their rounding errors collected, and the pair
+// (sum, error) goes to the FP64 block reduction.  That keeps the thread
+// loops on the FP32 pipe: FP64 arithmetic on this GPU runs at a small
+// fraction of the FP32 rate and would limit the reductions far below HBM
+// bandwidth.
+//
+// Every thread handles four rows per loop trip so that four independent
+// 16-byte loads per operand are in flight.
 #include "internal.h"
 
 namespace dgb {
@@ -46,29 +57,63 @@ __device__ __forceinline__ void block_reduce_store(const double (&vals)[G][NOUT]
     }
 }
 
-// partial[b][v][NOUT] -> out[v][NOUT], summed in block order
-template <int NOUT>
-__global__ void finalize_kernel(const double *__restrict__ partial, int nblocks, int nv, double *__restrict__ out) {
-    const int v = threadIdx.x;
-    if (v >= nv) return;
-    double acc[NOUT];
-#pragma unroll
-    for (int q = 0; q < NOUT; ++q) acc[q] = 0.0;
-    for (int b = 0; b < nblocks; ++b)
-#pragma unroll
-        for (int q = 0; q < NOUT; ++q) acc[q] += partial[((long long)b * nv + v) * NOUT + q];
-#pragma unroll
-    for (int q = 0; q < NOUT; ++q) out[v * NOUT + q] = acc[q];
+// Second pass of a reduction: partial[b][col] (col = v*NOUT + q, cols =
+// nv*NOUT) -> out[col].  One block of kFinThreads threads: T = kFinThreads /
+// cols threads per column each sum the blocks t, t+T, ... in order, then a
+// fixed pairwise tree combines the T partial sums, so the result does not
+// depend on timing.  KEEP = 1 keeps only q = 0 of each v (the real part of a
+// dot product) and writes out[v].
+constexpr int kFinThreads = 256;
+template <int NOUT, int KEEP>
+__global__ void __launch_bounds__(kFinThreads) finalize_kernel(const double *__restrict__ partial, int nblocks,
+                                                               int nv, double *__restrict__ out) {
+    __shared__ double sh[kFinThreads];
+    const int cols = nv * KEEP;
+    const int T = kFinThreads / cols;
+    const int t = threadIdx.x / cols, c = threadIdx.x % cols;
+    // column c of the output is column src of the partials
+    const int src = KEEP == NOUT ? c : c * NOUT;
+    double acc = 0.0;
+    if (t < T)
+        for (int b = t; b < nblocks; b += T) acc += partial[(long long)b * nv * NOUT + src];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int off = 1; off < T; off *= 2) {
+        if (t % (2 * off) == 0 && t + off < T) sh[t * cols + c] += sh[(t + off) * cols + c];
+        __syncthreads();
+    }
+    if (t == 0) out[c] = sh[c];
 }
 
-// partial[b][v][2] -> out[v] = the real part only, summed in block order
-__global__ void finalize_re_kernel(const double *__restrict__ partial, int nblocks, int nv, double *__restrict__ out) {
-    const int v = threadIdx.x;
-    if (v >= nv) return;
-    double acc = 0.0;
-    for (int b = 0; b < nblocks; ++b) acc += partial[((long long)b * nv + v) * 2];
-    out[v] = acc;
-}
+// Per-thread accumulator of a real sum.  FP64 data: a plain double.  FP32
+// data: (s, c) with the exact value s + c of everything added so far up to
+// the errors of the error-free steps (Knuth's two-sum and Dekker's product via
+// FMA); the explicit __f*_rn intrinsics keep the compiler from contracting or
+// reassociating them.
+template <typename A>
+struct RedAcc;
+template <>
+struct RedAcc<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void mac(double x, double y) { s = fma(x, y, s); }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct RedAcc<float> {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add(float p) {
+        const float t = __fadd_rn(s, p);
+        const float bp = __fsub_rn(t, s);
+        c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp)));
+        s = t;
+    }
+    __device__ __forceinline__ void mac(float x, float y) {
+        const float p = __fmul_rn(x, y);
+        add(p);
+        c = __fadd_rn(c, __fmaf_rn(x, y, -p));
+    }
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
 
 // thread (r, vg) of a block walks the rows r0 = block*R + r, stride grid*R and
 // owns columns vg*G .. vg*G+G-1
@@ -76,25 +121,41 @@ __global__ void finalize_re_kernel(const double *__restrict__ partial, int nbloc
     const int ng = nv / G;                                  \
     const int R = blockDim.x / ng;                          \
     const int r = threadIdx.x / ng, vg = threadIdx.x % ng;  \
-    const bool live = r < R;
+    const bool live = r < R;                                \
+    const long long stride = (long long)gridDim.x * R;
 
 template <typename E, int G>
 __global__ void norm2_kernel(const E *__restrict__ x, long long rows, int nv, double *__restrict__ partial) {
     extern __shared__ double sh[];
     using A = typename Acc<E>::T;
     BLAS_THREAD_SETUP
-    double acc[G][1] = {};
-    if (live)
-        for (long long row = (long long)blockIdx.x * R + r; row < rows; row += (long long)gridDim.x * R) {
-            cx<A> a[G];
-            load_cx<E, G, A>(x + 2 * (row * nv + vg * G), a);
+    RedAcc<A> acc[G];
+    auto add = [&](const cx<A> (&a)[G]) {
 #pragma unroll
-            for (int i = 0; i < G; ++i) {
-                acc[i][0] = fma((double)a[i].re, (double)a[i].re, acc[i][0]);
-                acc[i][0] = fma((double)a[i].im, (double)a[i].im, acc[i][0]);
-            }
+        for (int i = 0; i < G; ++i) {
+            acc[i].mac(a[i].re, a[i].re);
+            acc[i].mac(a[i].im, a[i].im);
         }
-    block_reduce_store<G, 1>(acc, sh, r, vg, R, ng, partial + (long long)blockIdx.x * nv);
+    };
+    if (live) {
+        long long row = (long long)blockIdx.x * R + r;
+        for (; row + 3 * stride < rows; row += 4 * stride) {
+            cx<A> a[4][G];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) load_cx<E, G, A>(x + 2 * ((row + u * stride) * nv + vg * G), a[u]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) add(a[u]);
+        }
+        for (; row < rows; row += stride) {
+            cx<A> a[1][G];
+            load_cx<E, G, A>(x + 2 * (row * nv + vg * G), a[0]);
+            add(a[0]);
+        }
+    }
+    double out[G][1];
+#pragma unroll
+    for (int i = 0; i < G; ++i) out[i][0] = acc[i].value();
+    block_reduce_store<G, 1>(out, sh, r, vg, R, ng, partial + (long long)blockIdx.x * nv);
 }
 
 template <typename E, int G>
@@ -103,21 +164,42 @@ __global__ void dot_kernel(const E *__restrict__ x, const E *__restrict__ y, lon
     extern __shared__ double sh[];
     using A = typename Acc<E>::T;
     BLAS_THREAD_SETUP
-    double acc[G][2] = {};
-    if (live)
-        for (long long row = (long long)blockIdx.x * R + r; row < rows; row += (long long)gridDim.x * R) {
-            cx<A> a[G], b[G];
-            load_cx<E, G, A>(x + 2 * (row * nv + vg * G), a);
-            load_cx<E, G, A>(y + 2 * (row * nv + vg * G), b);
+    RedAcc<A> re[G], im[G];
+    auto add = [&](const cx<A> (&a)[G], const cx<A> (&b)[G]) {
 #pragma unroll
-            for (int i = 0; i < G; ++i) {   // conj(x) * y
-                acc[i][0] = fma((double)a[i].re, (double)b[i].re, acc[i][0]);
-                acc[i][0] = fma((double)a[i].im, (double)b[i].im, acc[i][0]);
-                acc[i][1] = fma((double)a[i].re, (double)b[i].im, acc[i][1]);
-                acc[i][1] = fma(-(double)a[i].im, (double)b[i].re, acc[i][1]);
-            }
+        for (int i = 0; i < G; ++i) {   // conj(x) * y
+            re[i].mac(a[i].re, b[i].re);
+            re[i].mac(a[i].im, b[i].im);
+            im[i].mac(a[i].re, b[i].im);
+            im[i].mac(-a[i].im, b[i].re);
         }
-    block_reduce_store<G, 2>(acc, sh, r, vg, R, ng, partial + 2LL * blockIdx.x * nv);
+    };
+    if (live) {
+        long long row = (long long)blockIdx.x * R + r;
+        for (; row + 3 * stride < rows; row += 4 * stride) {
+            cx<A> a[4][G], b[4][G];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                load_cx<E, G, A>(x + 2 * ((row + u * stride) * nv + vg * G), a[u]);
+                load_cx<E, G, A>(y + 2 * ((row + u * stride) * nv + vg * G), b[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) add(a[u], b[u]);
+        }
+        for (; row < rows; row += stride) {
+            cx<A> a[1][G], b[1][G];
+            load_cx<E, G, A>(x + 2 * (row * nv + vg * G), a[0]);
+            load_cx<E, G, A>(y + 2 * (row * nv + vg * G), b[0]);
+            add(a[0], b[0]);
+        }
+    }
+    double out[G][2];
+#pragma unroll
+    for (int i = 0; i < G; ++i) {
+        out[i][0] = re[i].value();
+        out[i][1] = im[i].value();
+    }
+    block_reduce_store<G, 2>(out, sh, r, vg, R, ng, partial + 2LL * blockIdx.x * nv);
 }
 
 template <typename A>
@@ -140,37 +222,56 @@ __global__ void axpby_kernel(E *z, const E *x, const E *y, const double *__restr
         a[i] = coef<A>(ac, as, vg * G + i);
         b[i] = coef<A>(bc, bs, vg * G + i);
     }
-    double acc[G][1] = {};
-    if (live)
-        for (long long row = (long long)blockIdx.x * R + r; row < rows; row += (long long)gridDim.x * R) {
-            const long long e = 2 * (row * nv + vg * G);
-            cx<A> out[G], t[G];
+    RedAcc<A> acc[G];
+    // one row: combine, store, and (optionally) add |z|^2 of the value as
+    // stored: the registers rounded through the storage type (z may alias x
+    // or y, so it is not re-read)
+    auto finish = [&](long long e, const cx<A> (&tx)[G], const cx<A> (&ty)[G]) {
+        cx<A> out[G];
 #pragma unroll
-            for (int i = 0; i < G; ++i) out[i] = cx<A>{0, 0};
-            if (x) {
-                load_cx<E, G, A>(x + e, t);
+        for (int i = 0; i < G; ++i) {
+            out[i] = cx<A>{0, 0};
+            if (x) cmac(out[i], a[i], tx[i]);
+            if (y) cmac(out[i], b[i], ty[i]);
+        }
+        store_cx<E, G, A>(z + e, out);
+        if (partial) {
 #pragma unroll
-                for (int i = 0; i < G; ++i) cmac(out[i], a[i], t[i]);
-            }
-            if (y) {
-                load_cx<E, G, A>(y + e, t);
-#pragma unroll
-                for (int i = 0; i < G; ++i) cmac(out[i], b[i], t[i]);
-            }
-            store_cx<E, G, A>(z + e, out);
-            if (partial) {
-                // the norm of the value as stored: round the registers through
-                // the storage type (z may alias x or y, so it is not re-read)
-#pragma unroll
-                for (int i = 0; i < G; ++i) {
-                    const double re = (double)to_acc<E>(from_acc<E, A>(out[i].re));
-                    const double im = (double)to_acc<E>(from_acc<E, A>(out[i].im));
-                    acc[i][0] = fma(re, re, acc[i][0]);
-                    acc[i][0] = fma(im, im, acc[i][0]);
-                }
+            for (int i = 0; i < G; ++i) {
+                const A re = (A)to_acc<E>(from_acc<E, A>(out[i].re));
+                const A im = (A)to_acc<E>(from_acc<E, A>(out[i].im));
+                acc[i].mac(re, re);
+                acc[i].mac(im, im);
             }
         }
-    if (partial) block_reduce_store<G, 1>(acc, sh, r, vg, R, ng, partial + (long long)blockIdx.x * nv);
+    };
+    if (live) {
+        long long row = (long long)blockIdx.x * R + r;
+        for (; row + 3 * stride < rows; row += 4 * stride) {
+            cx<A> tx[4][G], ty[4][G];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const long long e = 2 * ((row + u * stride) * nv + vg * G);
+                if (x) load_cx<E, G, A>(x + e, tx[u]);
+                if (y) load_cx<E, G, A>(y + e, ty[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) finish(2 * ((row + u * stride) * nv + vg * G), tx[u], ty[u]);
+        }
+        for (; row < rows; row += stride) {
+            const long long e = 2 * (row * nv + vg * G);
+            cx<A> tx[1][G], ty[1][G];
+            if (x) load_cx<E, G, A>(x + e, tx[0]);
+            if (y) load_cx<E, G, A>(y + e, ty[0]);
+            finish(e, tx[0], ty[0]);
+        }
+    }
+    if (partial) {
+        double out[G][1];
+#pragma unroll
+        for (int i = 0; i < G; ++i) out[i][0] = acc[i].value();
+        block_reduce_store<G, 1>(out, sh, r, vg, R, ng, partial + (long long)blockIdx.x * nv);
+    }
 }
 
 // The two Krylov updates that use the old search direction, in one pass:
@@ -187,12 +288,7 @@ __global__ void update_xp_kernel(E *x, E *p, const E *__restrict__ r_, const dou
         a[i] = coef<A>(ac, 1.0, vg * G + i);
         b[i] = coef<A>(bc, 1.0, vg * G + i);
     }
-    for (long long row = (long long)blockIdx.x * R + r; row < rows; row += (long long)gridDim.x * R) {
-        const long long e = 2 * (row * nv + vg * G);
-        cx<A> xv[G], pv[G], rv[G];
-        load_cx<E, G, A>(x + e, xv);
-        load_cx<E, G, A>(p + e, pv);
-        load_cx<E, G, A>(r_ + e, rv);
+    auto finish = [&](long long e, cx<A> (&xv)[G], cx<A> (&pv)[G], const cx<A> (&rv)[G]) {
 #pragma unroll
         for (int i = 0; i < G; ++i) {
             cmac(xv[i], a[i], pv[i]);
@@ -202,6 +298,27 @@ __global__ void update_xp_kernel(E *x, E *p, const E *__restrict__ r_, const dou
         }
         store_cx<E, G, A>(x + e, xv);
         store_cx<E, G, A>(p + e, pv);
+    };
+    long long row = (long long)blockIdx.x * R + r;
+    for (; row + 3 * stride < rows; row += 4 * stride) {
+        cx<A> xv[4][G], pv[4][G], rv[4][G];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const long long e = 2 * ((row + u * stride) * nv + vg * G);
+            load_cx<E, G, A>(x + e, xv[u]);
+            load_cx<E, G, A>(p + e, pv[u]);
+            load_cx<E, G, A>(r_ + e, rv[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) finish(2 * ((row + u * stride) * nv + vg * G), xv[u], pv[u], rv[u]);
+    }
+    for (; row < rows; row += stride) {
+        const long long e = 2 * (row * nv + vg * G);
+        cx<A> xv[1][G], pv[1][G], rv[1][G];
+        load_cx<E, G, A>(x + e, xv[0]);
+        load_cx<E, G, A>(p + e, pv[0]);
+        load_cx<E, G, A>(r_ + e, rv[0]);
+        finish(e, xv[0], pv[0], rv[0]);
     }
 }
 
@@ -293,7 +410,7 @@ static int launch_norm2(const E *v, long long rows, int nv, dirac_prec p, double
     return dispatch_group(L.G, [&](auto gc) {
         constexpr int G = decltype(gc)::value;
         norm2_kernel<E, G><<<blocks, L.tb, L.sh, s>>>(v, rows, nv, partial);
-        finalize_kernel<1><<<1, 64, 0, s>>>(partial, blocks, nv, out);
+        finalize_kernel<1, 1><<<1, kFinThreads, 0, s>>>(partial, blocks, nv, out);
         return launch_check("norm2_kernel");
     });
 }
@@ -313,7 +430,7 @@ int blas_dot(const dirac_op *op, dirac_prec p, const void *u, const void *v, dou
             constexpr int G = decltype(gc)::value;
             dot_kernel<E, G><<<red_grid(op), L.tb, L.sh, s>>>((const E *)u, (const E *)v, op->rows, op->nv,
                                                               op->red_partial);
-            finalize_kernel<2><<<1, 64, 0, s>>>(op->red_partial, red_grid(op), op->nv, out);
+            finalize_kernel<2, 2><<<1, kFinThreads, 0, s>>>(op->red_partial, red_grid(op), op->nv, out);
             return launch_check("dot_kernel");
         });
     });
@@ -327,7 +444,7 @@ int blas_dot_re(const dirac_op *op, dirac_prec p, const void *u, const void *v, 
             constexpr int G = decltype(gc)::value;
             dot_kernel<E, G><<<red_grid(op), L.tb, L.sh, s>>>((const E *)u, (const E *)v, op->rows, op->nv,
                                                               op->red_partial);
-            finalize_re_kernel<<<1, 64, 0, s>>>(op->red_partial, red_grid(op), op->nv, out);
+            finalize_kernel<2, 1><<<1, kFinThreads, 0, s>>>(op->red_partial, red_grid(op), op->nv, out);
             return launch_check("dot_kernel");
         });
     });
@@ -343,7 +460,7 @@ int blas_axpby(const dirac_op *op, dirac_prec p, void *z, const void *x, const d
             axpby_kernel<E, G><<<red_grid(op), L.tb, L.sh, s>>>((E *)z, (const E *)x, (const E *)y, a, as, b, bs,
                                                                 op->rows, op->nv,
                                                                 norm_out ? op->red_partial : nullptr);
-            if (norm_out) finalize_kernel<1><<<1, 64, 0, s>>>(op->red_partial, red_grid(op), op->nv, norm_out);
+            if (norm_out) finalize_kernel<1, 1><<<1, kFinThreads, 0, s>>>(op->red_partial, red_grid(op), op->nv, norm_out);
             return launch_check("axpby_kernel");
         });
     });

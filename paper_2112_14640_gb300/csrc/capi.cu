@@ -75,7 +75,8 @@ static int alloc(void **p, size_t bytes) {
 
 // Process-wide memory of autotuned launch variants, keyed by what decides
 // the kernel's behaviour.
-using TuneKey = std::tuple<int, int, int, int, long long>;
+// (kind, layout, precision, link storage, N_c, N_v, volume)
+using TuneKey = std::tuple<int, int, int, int, int, int, long long>;
 struct TuneVal {
     int vr, minb, block;
 };
@@ -83,7 +84,7 @@ static std::mutex g_tune_mu;
 static std::map<TuneKey, TuneVal> g_tune;
 
 static TuneKey tune_key(const dirac_op *op) {
-    return TuneKey{(int)op->kind * 2 + op->geom.layout, (int)op->prec, op->nc, op->nv, op->V};
+    return TuneKey{(int)op->kind, op->geom.layout, (int)op->prec, (int)link_prec(op), op->nc, op->nv, op->V};
 }
 
 static void remember_tuning(const dirac_op *op) {

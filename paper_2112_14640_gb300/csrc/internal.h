@@ -154,9 +154,21 @@ inline void launch_variant(const dirac_op *op, int &vr, int &minb, int &block) {
         block = op->block ? op->block : kStencilBlock;
         return;
     }
+    // untuned: the widest 16-byte RHS group and, for N_c = 3, the register
+    // class and block size the autotuner picks for FP32 on 16^3x32 lattices
     vr = pick_vr(op->prec, op->nv);
     minb = 1;
     block = kStencilBlock;
+    if (op->nc == 3) {
+        if (op->kind == DIRAC_WILSON) {
+            minb = vr == 4 ? 3 : 4;
+        } else if (op->kind == DIRAC_STAGGERED) {
+            minb = 3;
+        } else if (vr <= 2) {   // Brillouin
+            minb = 3;
+            block = 384;
+        }
+    }
 }
 
 inline unsigned grid_for(long long threads, int block) {

@@ -218,3 +218,74 @@ def test_f32_links_reduce_the_error_of_16bit_operators():
         op.close()
     assert errs[D.LINKS_F32] < 1.05 * errs["round"], errs
     assert errs[D.LINKS_NATIVE] > errs[D.LINKS_F32], errs
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_every_launch_variant_matches_the_oracle(kind):
+    """Every compiled (VR, register class, block size) variant gives the same
+    operator (the autotuner may pick any of them)."""
+    dims, nc, nv, bc = (4, 4, 2, 6), 3, 12, (1, -1, 1, -1)
+    m0 = 0.05 if kind == D.STAGGERED else 0.1
+    for layout in LAYOUTS:
+        op, ref, src = make(kind, dims, nc, nv, bc, D.F32, layout=layout)
+        x = to_device(op, src)
+        want = ref.apply(src, m0)
+        tried = 0
+        for vr in (1, 2, 4):
+            for minb in (1, 3, 4, 6):
+                for block in (64, 128, 384):
+                    try:
+                        op.set_launch(vr, minb, block)
+                    except D.DiracError:
+                        continue
+                    tried += 1
+                    got = to_numpy(op, op.apply(x, m0=m0))
+                    assert rel_l2(got, want) <= TOL[D.F32], (kind, layout, vr, minb, block)
+        assert tried >= 20
+        op.close()
+
+
+def test_set_launch_rejects_invalid_variants():
+    op, _, _ = make(D.WILSON, (4, 4, 4, 4), 3, 12, (1, 1, 1, 1), D.F32)
+    for args in ((3, 1, 128), (2, 2, 128), (2, 1, 100), (2, 1, 256), (8, 1, 128)):
+        with pytest.raises(D.DiracError):
+            op.set_launch(*args)
+    op.set_launch(2, 4, 256)
+    assert op.get_launch() == (2, 4, 256)
+    op.set_launch(0)
+    vr, minb, block = op.get_launch()
+    assert 12 % vr == 0 and block % 32 == 0
+    op.close()
+    op, _, _ = make(D.WILSON, (4, 4, 4, 4), 3, 6, (1, 1, 1, 1), D.F32)
+    with pytest.raises(D.DiracError):
+        op.set_launch(4, 1, 128)        # 4 does not divide N_v = 6
+    op.close()
+
+
+@pytest.mark.parametrize("prec", [D.F32, D.BF16])
+def test_blas_reductions_full_size(prec):
+    """Norms and dot products over 16^3x32 x Nv = 4 (6.3 M complex numbers per
+    column group) keep FP64-level accuracy: compensated FP32 accumulation in
+    the thread loops, FP64 across threads."""
+    dims, nc, nv = (16, 16, 16, 32), 3, 4
+    op = D.DiracOp(D.WILSON, torch.from_numpy(I.unit_gauge_field(dims, nc)).cuda(), nv, (1, 1, 1, 1), prec)
+    g = torch.Generator(device="cpu").manual_seed(7)
+    rows = op.vec_bytes() // (nv * (8 if prec == D.F32 else 4))
+    a = torch.randn(rows, nv, dtype=torch.complex128, generator=g) * 3 + 1
+    b = torch.randn(rows, nv, dtype=torch.complex128, generator=g)
+    if prec == D.F32:
+        xa, xb = a.to(torch.complex64), b.to(torch.complex64)
+        ha, hb = xa.to(torch.complex128), xb.to(torch.complex128)
+    else:
+        xa = torch.view_as_real(a).to(torch.bfloat16)
+        xb = torch.view_as_real(b).to(torch.bfloat16)
+        ha = torch.view_as_complex(xa.to(torch.float64).contiguous())
+        hb = torch.view_as_complex(xb.to(torch.float64).contiguous())
+    n2 = op.norm2(xa.cuda().reshape(op.new_vector().shape)).cpu().numpy()
+    want = (ha.abs() ** 2).sum(0).numpy()
+    assert np.allclose(n2, want, rtol=1e-12, atol=0)
+    dt = op.dot(xa.cuda().reshape(op.new_vector().shape), xb.cuda().reshape(op.new_vector().shape)).cpu().numpy()
+    wdot = (ha.conj() * hb).sum(0).numpy()
+    scale = (ha.abs() ** 2).sum(0).sqrt().numpy() * (hb.abs() ** 2).sum(0).sqrt().numpy()
+    assert np.all(np.abs(dt - wdot) <= 1e-12 * scale), (np.abs(dt - wdot) / scale)
+    op.close()
