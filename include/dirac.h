@@ -138,7 +138,11 @@ int dirac_apply_normal(const dirac_op *op, const void *psi_in, void *psi_out, do
 /* End-to-end apply from HOST memory: copies host_in to an operator-owned
  * device buffer, applies D (dagger != 0: D^dag), copies the result to
  * host_out and synchronises `stream`.  Host buffers of vec_bytes each;
- * pinned memory gives full copy bandwidth. */
+ * pinned memory gives full copy bandwidth.  For N_t >= 3 the work runs in up
+ * to 8 slabs of whole time slices: copies in on one operator-owned stream,
+ * the stencil on `stream` for each slab whose t-neighbour slabs have
+ * arrived, copies out on another operator-owned stream, all overlapping.
+ * Calls on one operator must not run concurrently. */
 int dirac_apply_host(const dirac_op *op, const void *host_in, void *host_out, double m0,
                      int dagger, void *stream);
 

@@ -195,12 +195,20 @@ extern "C" int dirac_solve_batched(int nsolves, dirac_op *const *ops, const void
                 TRYB(batch_apply_A_pq(op, pv, q, pq, m0[i], s));
                 batch_alpha_kernel<<<1, 64, 0, s>>>(nv, rr, pq, act, alpha);
                 TRYB(blas_axpby(op, p, r, r, nullptr, 1.0, q, alpha, -1.0, rr_new, s));
-                batch_beta_kernel<<<1, 64, 0, s>>>(nv, rr_new, rr, act, beta);
-                TRYB(blas_update_xp(op, p, x[i], pv, r, alpha, beta, s));   // x += alpha p; p = r + beta p
+                if (k + 1 < K) {
+                    batch_beta_kernel<<<1, 64, 0, s>>>(nv, rr_new, rr, act, beta);
+                    TRYB(blas_update_xp(op, p, x[i], pv, r, alpha, beta, s));   // x += alpha p; p = r + beta p
+                } else {
+                    // last iteration of the segment: x += alpha p, then replace r by
+                    // the true residual and build the next direction from it
+                    TRYB(blas_axpby(op, p, x[i], x[i], nullptr, 1.0, pv, alpha, 1.0, nullptr, s));
+                    TRYB(op_apply_normal(op, x[i], q, m0[i], s));
+                    TRYB(blas_axpby(op, p, r, rhs, nullptr, 1.0, q, nullptr, -1.0, rr_new, s));
+                    batch_beta_kernel<<<1, 64, 0, s>>>(nv, rr_new, rr, act, beta);
+                    TRYB(blas_axpby(op, p, pv, r, nullptr, 1.0, pv, beta, 1.0, nullptr, s));
+                }
             }
-            // recompute the true residual, freeze converged RHS, stamp completion
-            TRYB(op_apply_normal(op, x[i], q, m0[i], s));
-            TRYB(blas_axpby(op, p, r, rhs, nullptr, 1.0, q, nullptr, -1.0, rr, s));
+            // freeze converged RHS (rr now holds the true residual), stamp completion
             batch_check_kernel<<<1, 64, 0, s>>>(nv, rr, nb, tol2, act, dstate + i, K);
             TRYB(launch_check("batch segment"));
             TRYB(cuda_check(cudaEventRecord(joins[i], s), "join"));

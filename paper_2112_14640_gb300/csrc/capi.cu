@@ -11,9 +11,23 @@
 
 #include "internal.h"
 
+// Streams and events of the pipelined host apply (dirac_apply_host), which
+// works in at most kMaxSlabs slabs of time slices.
+constexpr int kMaxSlabs = 8;
+struct dirac_host_pipe {
+    cudaStream_t h2d = nullptr, d2h = nullptr;
+    cudaEvent_t in_done[kMaxSlabs] = {}, out_ready[kMaxSlabs] = {}, start = nullptr, end = nullptr;
+};
+
 using namespace dgb;
 
 namespace dgb {
+
+#define CTRY(x)                 \
+    do {                        \
+        int rc_ = (x);          \
+        if (rc_) return rc_;    \
+    } while (0)
 
 int op_apply(const dirac_op *op, const void *in, void *out, double m0, int sgn, cudaStream_t s) {
     switch (op->kind) {
@@ -31,8 +45,43 @@ int op_apply_normal(const dirac_op *op, const void *in, void *out, double m0, cu
     return op_apply(op, op->scratch, out, m0, -1, s);
 }
 
+static void pipe_free(dirac_host_pipe *p) {
+    if (!p) return;
+    for (int k = 0; k < kMaxSlabs; ++k) {
+        if (p->in_done[k]) cudaEventDestroy(p->in_done[k]);
+        if (p->out_ready[k]) cudaEventDestroy(p->out_ready[k]);
+    }
+    if (p->start) cudaEventDestroy(p->start);
+    if (p->end) cudaEventDestroy(p->end);
+    if (p->h2d) cudaStreamDestroy(p->h2d);
+    if (p->d2h) cudaStreamDestroy(p->d2h);
+    delete p;
+}
+
+static int pipe_get(dirac_op *op, dirac_host_pipe **out) {
+    if (!op->pipe) {
+        dirac_host_pipe *p = new dirac_host_pipe();
+        int rc = cuda_check(cudaStreamCreateWithFlags(&p->h2d, cudaStreamNonBlocking), "pipe stream");
+        if (!rc) rc = cuda_check(cudaStreamCreateWithFlags(&p->d2h, cudaStreamNonBlocking), "pipe stream");
+        for (int k = 0; k < kMaxSlabs && !rc; ++k) {
+            rc = cuda_check(cudaEventCreateWithFlags(&p->in_done[k], cudaEventDisableTiming), "pipe event");
+            if (!rc) rc = cuda_check(cudaEventCreateWithFlags(&p->out_ready[k], cudaEventDisableTiming), "pipe event");
+        }
+        if (!rc) rc = cuda_check(cudaEventCreateWithFlags(&p->start, cudaEventDisableTiming), "pipe event");
+        if (!rc) rc = cuda_check(cudaEventCreateWithFlags(&p->end, cudaEventDisableTiming), "pipe event");
+        if (rc) {
+            pipe_free(p);
+            return rc;
+        }
+        op->pipe = p;
+    }
+    *out = op->pipe;
+    return DIRAC_OK;
+}
+
 static void op_free(dirac_op *op) {
     if (!op) return;
+    pipe_free(op->pipe);
     for (int i = 0; i < 4; ++i)
         for (int k = 0; k < 2; ++k) op_free(op->inner[i][k]);
     cudaFree(op->links);
@@ -112,7 +161,7 @@ int op_alloc(dirac_kind kind, const dirac_geom *g, dirac_op **out) {
     op->nv = g->nv;
     op->prec = g->prec;
     op->V = (long long)g->dims[0] * g->dims[1] * g->dims[2] * g->dims[3];
-    op->lat = Lat{g->dims[0], g->dims[1], g->dims[2], g->dims[3], g->nv, op->V};
+    op->lat = Lat{g->dims[0], g->dims[1], g->dims[2], g->dims[3], g->nv, op->V, 0, op->V};
     op->rows = op->V * op->nc * (kind == DIRAC_STAGGERED ? 1 : 4);
     const size_t eb = elem_bytes(op->prec), lb = elem_bytes(link_prec(op));
     op->vec_bytes = (size_t)op->rows * op->nv * 2 * eb;
@@ -329,6 +378,34 @@ int dirac_apply_normal(const dirac_op *op, const void *psi_in, void *psi_out, do
     return op_apply_normal(op, psi_in, psi_out, m0, (cudaStream_t)stream);
 }
 
+// Copy the sites of time slices [t0, t1) of a vector between host and device
+// (same offsets on both sides): one run for the site-outer layout, one run per
+// internal component for the site-inner layout.
+static int copy_slab(const dirac_op *op, void *dst, const void *src, int t0, int t1, cudaMemcpyKind kind,
+                     cudaStream_t s) {
+    const size_t per_site = (size_t)op->nv * 2 * elem_bytes(op->prec);
+    const size_t ncs = (size_t)(op->rows / op->V);
+    const size_t slab_sites = (size_t)op->lat.nx * op->lat.ny * op->lat.nz;
+    const size_t first = (size_t)t0 * slab_sites, count = (size_t)(t1 - t0) * slab_sites;
+    if (op->geom.layout == DIRAC_LAYOUT_SITE_OUTER) {
+        const size_t off = first * ncs * per_site;
+        return cuda_check(cudaMemcpyAsync((char *)dst + off, (const char *)src + off, count * ncs * per_site, kind, s),
+                          "slab copy");
+    }
+    const size_t pitch = (size_t)op->V * per_site, off = first * per_site;
+    if (pitch < ((size_t)1 << 31))
+        return cuda_check(cudaMemcpy2DAsync((char *)dst + off, pitch, (const char *)src + off, pitch, count * per_site,
+                                            ncs, kind, s),
+                          "slab copy");
+    for (size_t c = 0; c < ncs; ++c) {
+        const size_t o = c * pitch + off;
+        const int rc = cuda_check(cudaMemcpyAsync((char *)dst + o, (const char *)src + o, count * per_site, kind, s),
+                                  "slab copy");
+        if (rc) return rc;
+    }
+    return DIRAC_OK;
+}
+
 int dirac_apply_host(const dirac_op *op, const void *host_in, void *host_out, double m0, int dagger, void *stream) {
     if (!op || !host_in || !host_out) return DIRAC_ERR_INVALID_ARG;
     dirac_op *self = (dirac_op *)op;
@@ -337,11 +414,49 @@ int dirac_apply_host(const dirac_op *op, const void *host_in, void *host_out, do
     if (!rc && !self->stage_out) rc = alloc(&self->stage_out, op->vec_bytes);
     if (rc) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    rc = cuda_check(cudaMemcpyAsync(self->stage_in, host_in, op->vec_bytes, cudaMemcpyHostToDevice, s), "H2D");
-    if (!rc) rc = op_apply(op, self->stage_in, self->stage_out, m0, dagger ? -1 : +1, s);
-    if (!rc) rc = cuda_check(cudaMemcpyAsync(host_out, self->stage_out, op->vec_bytes, cudaMemcpyDeviceToHost, s), "D2H");
-    if (!rc) rc = cuda_check(cudaStreamSynchronize(s), "apply_host sync");
-    return rc;
+    const int sgn = dagger ? -1 : +1;
+    const int nt = op->lat.nt;
+    const int K = nt < kMaxSlabs ? nt : kMaxSlabs;   // slabs of whole time slices
+    if (K < 3) {
+        rc = cuda_check(cudaMemcpyAsync(self->stage_in, host_in, op->vec_bytes, cudaMemcpyHostToDevice, s), "H2D");
+        if (!rc) rc = op_apply(op, self->stage_in, self->stage_out, m0, sgn, s);
+        if (!rc) rc = cuda_check(cudaMemcpyAsync(host_out, self->stage_out, op->vec_bytes, cudaMemcpyDeviceToHost, s),
+                                 "D2H");
+        if (!rc) rc = cuda_check(cudaStreamSynchronize(s), "apply_host sync");
+        return rc;
+    }
+    // Pipelined: slab k = time slices [k nt / K, (k+1) nt / K) goes in on the
+    // copy-in stream; the output of slab k needs the input of slabs k-1, k,
+    // k+1 (every stencil reaches one slice in t), so the stencil runs on slabs
+    // 1, 2, .., K-1 as their upper neighbours arrive and on slab 0 last; each
+    // finished output slab goes out on the copy-out stream while later slabs
+    // are still being copied in or computed.
+    dirac_host_pipe *p = nullptr;
+    CTRY(pipe_get(self, &p));
+    auto t_of = [&](int k) { return (int)((long long)k * nt / K); };
+    CTRY(cuda_check(cudaEventRecord(p->start, s), "pipe event"));          // staging buffers free
+    CTRY(cuda_check(cudaStreamWaitEvent(p->h2d, p->start, 0), "pipe wait"));
+    CTRY(cuda_check(cudaStreamWaitEvent(p->d2h, p->start, 0), "pipe wait"));
+    for (int k = 0; k < K; ++k) {
+        CTRY(copy_slab(op, self->stage_in, host_in, t_of(k), t_of(k + 1), cudaMemcpyHostToDevice, p->h2d));
+        CTRY(cuda_check(cudaEventRecord(p->in_done[k], p->h2d), "pipe event"));
+    }
+    const long long slab_sites = (long long)op->lat.nx * op->lat.ny * op->lat.nz;
+    for (int i = 0; i < K; ++i) {
+        const int k = (i + 1) % K;
+        const int need = (k >= 1 && k <= K - 2) ? k + 1 : K - 1;   // last input slab it reads
+        CTRY(cuda_check(cudaStreamWaitEvent(s, p->in_done[need], 0), "pipe wait"));
+        dirac_op part = *op;   // same buffers, output sites of slab k only
+        part.lat.n0 = t_of(k) * slab_sites;
+        part.lat.nsites = (t_of(k + 1) - t_of(k)) * slab_sites;
+        CTRY(op_apply(&part, self->stage_in, self->stage_out, m0, sgn, s));
+        CTRY(cuda_check(cudaEventRecord(p->out_ready[k], s), "pipe event"));
+        CTRY(cuda_check(cudaStreamWaitEvent(p->d2h, p->out_ready[k], 0), "pipe wait"));
+        CTRY(copy_slab(op, host_out, self->stage_out, t_of(k), t_of(k + 1), cudaMemcpyDeviceToHost, p->d2h));
+    }
+    CTRY(cuda_check(cudaEventRecord(p->end, p->d2h), "pipe event"));
+    CTRY(cuda_check(cudaStreamWaitEvent(s, p->end, 0), "pipe wait"));
+    return cuda_check(cudaStreamSynchronize(s), "apply_host sync");
 }
 
 int dirac_vec_norm2(const dirac_op *op, const void *v, double *out_dev, void *stream) {

@@ -156,6 +156,9 @@ struct Lat {
     int nx, ny, nz, nt;
     int nv;
     long long V;
+    // output sites a stencil launch covers: n0 .. n0 + nsites - 1 (the whole
+    // lattice unless a pipelined host apply works slab by slab)
+    long long n0, nsites;
 };
 
 struct Coord {

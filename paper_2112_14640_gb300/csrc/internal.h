@@ -27,6 +27,7 @@ struct dirac_op {
     void *scratch;         // one vector: intermediate of D^dag D
     void *stage_in;        // host-apply staging buffers (lazy)
     void *stage_out;
+    struct dirac_host_pipe *pipe;   // host-apply copy streams and events (lazy)
     double *red_partial;   // reduction partials [red_blocks][nv][2]
     int red_blocks;
     void *solver_ws;       // solver workspace (lazy), solver_ws_bytes long

@@ -42,9 +42,10 @@ __global__ void __launch_bounds__(stencil_max_threads(MINB), (MINB > 1 ? 1 : 0))
     using A = typename Acc<E>::T;
     const int nchunk = g.nv / VR;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid >= g.V * nchunk) return;
-    const long long n = tid / nchunk;
-    const int j = (int)(tid - n * nchunk);
+    if (tid >= g.nsites * nchunk) return;
+    const long long i = tid / nchunk;
+    const long long n = g.n0 + i;
+    const int j = (int)(tid - i * nchunk);
     const Coord c = site_coords(g, n);
     using L = Layout<LAYOUT>;
     const long long cs = L::cs_stride(g), ls = L::mat_stride(g);
@@ -95,7 +96,7 @@ int launch_staggered_v(const dirac_op *op, const void *in, void *out, double m0,
             return dispatch_minb<NC>(minb, [&](auto mbc) {
             constexpr int MINB = decltype(mbc)::value;
             {
-                const long long threads = op->V * (op->nv / VR);
+                const long long threads = op->lat.nsites * (op->nv / VR);
                 {
                 staggered_kernel<NC, VR, E, MINB, LAYOUT, EL><<<grid_for(threads, block), block, 0, s>>>(
                     (const EL *)op->links, (const E *)in, (E *)out, op->lat, (A)m0, (A)(0.5 * sgn));

@@ -154,10 +154,14 @@ def test_blas_reductions(kind, prec, layout):
     op.close()
 
 
-def test_host_apply_matches_device_apply():
-    dims = (8, 8, 4, 8)
+@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("dims", [(8, 8, 4, 8), (4, 4, 4, 6), (4, 4, 4, 20), (4, 4, 2, 2)])
+def test_host_apply_matches_device_apply(dims, layout):
+    """The host apply (copies and stencil pipelined over slabs of time slices
+    for N_t >= 3, one copy each way otherwise) equals the device apply bit for
+    bit."""
     for kind in KINDS:
-        op, ref, src = make(kind, dims, 3, 12, (1, 1, 1, -1), D.F32)
+        op, ref, src = make(kind, dims, 3, 12, (1, 1, 1, -1), D.F32, layout=layout)
         x = to_device(op, src)
         dev = op.apply(x, m0=0.1).cpu()
         hin = x.cpu().pin_memory()

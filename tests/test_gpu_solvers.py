@@ -170,3 +170,23 @@ def test_mixed_hybrid_sloppy_links_reach_1e10(inner):
                      sloppy_links=D.LINKS_F32)
     assert st["status"] == 0, st
     assert np.all(normal_relres(ref, to_numpy(op, x), b, m0) < 1.01e-10)
+
+
+def test_f32_cg_light_staggered_single_and_batched():
+    """FP32 CG on D_S^dag D_S at m0 = 0.05 (cond ~ 2e3) on 8^4.  Alone it
+    either reaches 1e-6 or stops on the 1% rule near the FP32 limit with a
+    residual the oracle confirms; in a batch (no 1% rule, true residual
+    every 20 iterations, next direction built from it) it must converge to
+    1e-5 (at 1e-6 single RHS sit at the FP32 floor, ~3e-6, until maxit)."""
+    m0 = 0.05
+    op, ref, b = setup(D.STAGGERED, (8, 8, 8, 8), 3, 4, (1, 1, 1, -1), D.F32)
+    x, st = op.solve(to_device(op, b), m0=m0, tol=1e-6, maxit=20000)
+    assert st["status"] in (0, 2), st
+    got = normal_relres(ref, to_numpy(op, x), b, m0)
+    assert np.all(got < 1e-5) and np.allclose(got, st["relres"], rtol=0.2), (got, st)
+    op2, _, _ = setup(D.STAGGERED, (8, 8, 8, 8), 3, 4, (1, 1, 1, -1), D.F32, layout=D.SITE_INNER)
+    xs, stats, rc = D.solve_batched([op, op2], [to_device(op, b), to_device(op2, b)], m0s=[m0, m0],
+                                    solver=D.CG_NORMAL, tol=1e-5, maxit=20000)
+    assert rc == 0 and all(s["status"] == 0 for s in stats), stats
+    assert np.all(normal_relres(ref, to_numpy(op, xs[0]), b, m0) < 2e-5)
+    assert np.all(normal_relres(ref, to_numpy(op2, xs[1]), b, m0) < 2e-5)
