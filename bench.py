@@ -494,15 +494,21 @@ def tune_mass(D, op32, b32, kind, target=1e6, iters=600, torch_mod=None):
     ops = D.DiracOp(kind, Us, NV, BC, D.F32)
     bs = ops.to_prec(torch_mod.from_numpy(I.source(small, NC, NV, 6)).cuda())
     scan = []
-    for m in (0.0, -0.4, -0.7, -0.9, -1.05, -1.2, -1.3, -1.4, -1.5, -1.6):
-        _, st = ops.solve(bs, m0=m, solver=D.CG_HPD, tol=1e-8, maxit=20000)
+    for m in (0.0, -0.4, -0.7, -1.0, -1.2, -1.4, -1.6, -1.7, -1.8, -1.9, -2.0, -2.1, -2.2, -2.3, -2.4, -2.5):
+        _, st = ops.solve(bs, m0=m, solver=D.CG_HPD, tol=1e-8, maxit=30000)
         c = max(st["lambda_max"]) / max(min(st["lambda_min"]), 1e-300)
         scan.append((m, c, st["iters"]))
-        if c > 10 * target:
+        if c >= target:
             break
     ops.close()
+    # log-interpolate between the last two points (cond grows towards the
+    # critical mass); if the target was never reached, the largest cond seen
     ms, cs = np.array([a for a, _, _ in scan]), np.log(np.array([b for _, b, _ in scan]))
-    m = float(np.interp(np.log(target), cs, ms)) if cs.max() >= np.log(target) else float(ms[-1])
+    if cs[-1] >= np.log(target) and len(cs) > 1 and cs[-1] > cs[-2]:
+        w = (np.log(target) - cs[-2]) / (cs[-1] - cs[-2])
+        m = float(ms[-2] + w * (ms[-1] - ms[-2]))
+    else:
+        m = float(ms[int(np.argmax(cs))])
     return m, {"scan_16x16x16x32": [(round(a, 3), float(b), int(k)) for a, b, k in scan]}
 
 

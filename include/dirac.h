@@ -158,8 +158,9 @@ int dirac_op_set_launch(dirac_op *op, int vr, int minb, int block);
 int dirac_op_get_launch(const dirac_op *op, int *vr, int *minb, int *block);
 /* Time every compiled variant of D (bare mass m0) on operator-owned buffers
  * and keep the fastest for this operator; the choice is also remembered for
- * operators created later in this process with the same kind, precision,
- * N_c, N_v and volume (including the lower-precision twins of mixed solves).
+ * operators created later in this process with the same kind, layout,
+ * precision, link storage, N_c, N_v and volume (including the
+ * lower-precision twins of mixed solves).
  * best_ms (may be NULL) receives the winner's time per apply.  Synchronises. */
 int dirac_op_autotune(dirac_op *op, double m0, void *stream, double *best_ms);
 
@@ -168,8 +169,10 @@ size_t dirac_vec_bytes(const dirac_op *op);
 
 /* ---------------------------------------------------------- BLAS-1 (Sec. 3)
  * Per-RHS vector operations on vectors of the operator's shape and precision.
- * Reductions accumulate in FP64 (Sec. 3 accumulates sp norms in dp) with a
- * fixed-order two-pass reduction, so results are bitwise reproducible.
+ * Reductions keep FP64-level accuracy (Sec. 3 accumulates sp norms in dp):
+ * FP64 arithmetic for FP64 vectors; for FP32/16-bit vectors, exact products
+ * and compensated sums in FP32 per thread, FP64 across threads.  The order is
+ * fixed (two-pass reduction), so results are bitwise reproducible.
  * out/coefficient arrays are DEVICE arrays of N_v entries. */
 int dirac_vec_norm2(const dirac_op *op, const void *v, double *out_dev, void *stream);
 /* <u, v> per RHS, linear in the second argument; out_dev holds N_v (re, im) pairs. */
