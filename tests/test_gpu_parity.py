@@ -293,3 +293,23 @@ def test_blas_reductions_full_size(prec):
     scale = (ha.abs() ** 2).sum(0).sqrt().numpy() * (hb.abs() ** 2).sum(0).sqrt().numpy()
     assert np.all(np.abs(dt - wdot) <= 1e-12 * scale), (np.abs(dt - wdot) / scale)
     op.close()
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("prec", [D.F64, D.F32])
+def test_extreme_shapes(kind, prec):
+    """The largest N_v (64) on the smallest lattice (extent 2 in every
+    direction: the forward and backward neighbour are the same site), and a
+    single RHS with N_c = 4 on a lattice long in t."""
+    for dims, nc, nv, bc in (((2, 2, 2, 2), 3, 64, (1, 1, 1, -1)), ((2, 2, 2, 34), 4, 1, (-1, 1, 1, -1))):
+        m0 = 0.05 if kind == D.STAGGERED else 0.1
+        op, ref, src = make(kind, dims, nc, nv, bc, prec)
+        x = to_device(op, src)
+        for dag in (False, True):
+            got = to_numpy(op, op.apply(x, m0=m0, dagger=dag))
+            want = ref.apply_dagger(src, m0) if dag else ref.apply(src, m0)
+            assert rel_l2(got, want) <= TOL[prec], (kind, dims, nv, dag)
+        n2 = op.norm2(x).cpu().numpy()
+        assert np.allclose(n2, O.norm2(src if prec == D.F64 else src.astype(np.complex64).astype(np.complex128)),
+                           rtol=1e-12)
+        op.close()
