@@ -45,11 +45,13 @@ __host__ __device__ inline int store_index(const int s[4], double *scale) {
     return group_offset(m) + b;
 }
 
-// W~ memory layout, in complex numbers, of element e of matrix q at site n:
-//   site-outer (layout 0): (n * 80 + q) * nc^2 + e   -- one site's 80 matrices contiguous
-//   site-inner (layout 1): (q * nc^2 + e) * V + n    -- consecutive sites contiguous
-__host__ __device__ inline long long w_index(int q, int e, long long n, long long V, int nc, int layout) {
-    return layout == 0 ? (n * 80 + q) * nc * nc + e : ((long long)q * nc * nc + e) * V + n;
+// W~ memory layout, in complex numbers, of element e of matrix q at site n,
+// for either vector layout: (n * 80 + q) * nc^2 + e, one site's 80 matrices
+// contiguous in visiting order, so a thread streams its own W~ sequentially.
+// (Storing them site-innermost when the vectors are site-inner was measured
+// slower: the nine elements of one matrix then sit in nine DRAM pages.)
+__host__ __device__ inline long long w_index(int q, int e, long long n, int nc) {
+    return (n * 80 + q) * nc * nc + e;
 }
 
 }  // namespace bril

@@ -4,7 +4,7 @@
 //       + sum_{s in {-1,0,1}^4, s != 0} [sgn rho_k sum_mu s_mu gamma_mu - lambda_k/2] (x) W_s(n) psi(n+s)
 // rho = (64,16,4,1)/432, lambda = (-240,8,4,2,1)/64, k = |s|_1, W_s from
 // Tab. off-axis, built once per gauge field (links.cu) and stored in the
-// order q, with the scale rho_k s_lead and the layout of bril_dirs.h.  The derivative
+// order q, with the scale rho_k s_lead and the per-site layout of bril_dirs.h.  The derivative
 // carries every axis the offset moves along (sum_mu s_mu gamma_mu), the
 // reading of Eq. (def_ider).  sgn = +1 gives D_B, sgn = -1 gives
 // D_B^dag = gamma5 D_B gamma5 (the derivative part flips sign).
@@ -177,9 +177,10 @@ __global__ void __launch_bounds__(stencil_max_threads(MINB), (MINB > 1 ? 1 : 0))
     C.n = n;
     C.sgn = sgn;
     C.vbase = (long long)j * VR;
-    C.ws = L::mat_stride(g);
-    C.dq = 2LL * NC * NC * L::mat_stride(g);
-    C.wp = W + 2 * L::template mat<NC>(g, n, 80, 0);
+    // W~ of one site contiguous in visiting order for either vector layout
+    C.ws = 1;
+    C.dq = 2LL * NC * NC;
+    C.wp = W + 2LL * n * 80 * NC * NC;
     {
         const int co[4] = {c.x, c.y, c.z, c.t};
         const int ext[4] = {g.nx, g.ny, g.nz, g.nt};

@@ -63,8 +63,7 @@ __device__ __forceinline__ void signed_link(const UE *__restrict__ U, const Lat 
 }
 
 template <int NC, typename UE, typename E>
-__global__ void __launch_bounds__(96) build_w_kernel(const UE *__restrict__ U, E *__restrict__ W, Lat g, Phases ph,
-                                                     int layout) {
+__global__ void __launch_bounds__(96) build_w_kernel(const UE *__restrict__ U, E *__restrict__ W, Lat g, Phases ph) {
     __shared__ cx<double> Ws[81][NC * NC];
     const long long n = blockIdx.x;
     const int dir = threadIdx.x;
@@ -115,8 +114,8 @@ __global__ void __launch_bounds__(96) build_w_kernel(const UE *__restrict__ U, E
         double scale;
         const int q = bril::store_index(s, &scale);
         for (int e = 0; e < NC * NC; ++e) {
-            // [site][q][a][b] (site-outer) or [q][a][b][site] (site-inner)
-            const long long o = bril::w_index(q, e, n, g.V, NC, layout);
+            // [site][q][a][b] for either vector layout
+            const long long o = bril::w_index(q, e, n, NC);
             W[2 * o] = from_acc<E, double>(scale * Ws[dir][e].re);
             W[2 * o + 1] = from_acc<E, double>(scale * Ws[dir][e].im);
         }
@@ -137,7 +136,7 @@ __global__ void unpack_w_kernel(const E *__restrict__ Wst, E *__restrict__ out, 
     const int q = bril::store_index(s, &scale);
     const int per = nc * nc;
     for (int e = 0; e < per; ++e) {
-        const long long i = bril::w_index(q, e, n, g.V, nc, layout);
+        const long long i = bril::w_index(q, e, n, nc);
         const long long o = layout == 0 ? (n * 80 + dirp) * per + e : ((long long)dirp * per + e) * g.V + n;
         using A = typename Acc<E>::T;
         out[2 * o] = from_acc<E, double>((double)to_acc<E>(Wst[2 * i]) / scale);
@@ -190,7 +189,7 @@ int launch_build_w(dirac_op *op, const void *U, dirac_prec u_prec, cudaStream_t 
             return dispatch_nc(op->nc, [&](auto ncc) {
                 constexpr int NC = decltype(ncc)::value;
                 build_w_kernel<NC, UE, E><<<(unsigned)op->V, 96, 0, s>>>((const UE *)U, (E *)op->w, op->lat,
-                                                                       phases_of(op), op->geom.layout);
+                                                                       phases_of(op));
                 return launch_check("build_w_kernel");
             });
         });
