@@ -17,9 +17,10 @@
 // mask), so the gamma matrices of the axes outside M cost nothing: in the
 // chiral basis of App. A each gamma_mu is a signed permutation of the spin
 // components, and the spin combination costs 8k real FMAs per colour and RHS
-// instead of 40.  Inside a group the 2^k sign patterns run in a loop, the W~
-// of the next offset is loaded while the current one is applied, and each W~
-// is used for all 4 spins and the thread's VR right-hand sides.
+// instead of 40.  Inside a group the 2^k sign patterns run in a loop (two per
+// trip), the W~ of the next offset is loaded while the current one is
+// applied, and each W~ is used for all 4 spins and the thread's VR
+// right-hand sides.
 #pragma once
 #include "bril_dirs.h"
 #include "internal.h"
@@ -81,68 +82,76 @@ struct Ctx {
     A sgn;
 };
 
-// The 2^k offsets of support M: their signs run in a loop, everything that
-// depends on M alone is fixed at compile time.
+// Offset b (sign pattern) of support M, applied with the W~ in Wcur while the
+// next offset's W~ is loaded into Wnext (storage order = visiting order).
 template <int M, int NC, int VR, typename E, typename EL, int LAYOUT, typename A>
-__device__ __forceinline__ void group(const Ctx<NC, VR, E, EL, LAYOUT> &C, int &q, cx<A> (&Wc)[NC][NC],
-                                      cx<A> (&acc)[NC][4][VR]) {
+__device__ __forceinline__ void offset(const Ctx<NC, VR, E, EL, LAYOUT> &C, int q, int b,
+                                       const cx<A> (&Wcur)[NC][NC], cx<A> (&Wnext)[NC][NC],
+                                       cx<A> (&acc)[NC][4][VR]) {
     using L = Layout<LAYOUT>;
     constexpr int K = popc4(M);
     const A ck = (A)c_lambda(K);
     const long long cs = L::cs_stride(C.g);
+    A sig[4] = {1, 1, 1, 1};
+    long long m = C.n;
+    {
+        int jbit = 0;
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            if ((M >> mu) & 1) {
+                const bool neg = (b >> jbit) & 1;
+                sig[mu] = neg ? (A)-1 : (A)1;
+                m += neg ? C.dm[mu] : C.dp[mu];
+                ++jbit;
+            }
+        }
+    }
+    const A sl = sig[lead_axis(M)];
+    A e[4];
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) e[mu] = sig[mu] * sl;
+    const A d = -C.sgn * ck * sl;
+
+    if (q + 1 < 80) load_mat_s<NC, EL, A>(C.wp + (long long)(q + 1) * C.dq, C.ws, Wnext);
+
+    const E *pm = C.in + 2 * (L::vec(C.g, m, NC * 4, 0) + C.vbase);
+#pragma unroll
+    for (int kc = 0; kc < NC; ++kc) {
+        cx<A> p[4][VR];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) load_cx<E, VR, A>(pm + 2 * (kc * 4 + s) * cs, p[s]);
+#pragma unroll
+        for (int v = 0; v < VR; ++v) {
+            const cx<A> pv[4] = {p[0][v], p[1][v], p[2][v], p[3][v]};
+            const cx<A> f0 = spin_mix<M, 0>(pv, e, d);
+            const cx<A> f1 = spin_mix<M, 1>(pv, e, d);
+            const cx<A> f2 = spin_mix<M, 2>(pv, e, d);
+            const cx<A> f3 = spin_mix<M, 3>(pv, e, d);
+#pragma unroll
+            for (int a = 0; a < NC; ++a) {
+                cmac(acc[a][0][v], Wcur[a][kc], f0);
+                cmac(acc[a][1][v], Wcur[a][kc], f1);
+                cmac(acc[a][2][v], Wcur[a][kc], f2);
+                cmac(acc[a][3][v], Wcur[a][kc], f3);
+            }
+        }
+    }
+}
+
+// The 2^k offsets of support M: their signs run in a loop, everything that
+// depends on M alone is fixed at compile time.  Two offsets per trip, so the
+// two W~ buffers swap roles without copies (every group has an even count);
+// Wc holds the current W~ on entry and on exit.
+template <int M, int NC, int VR, typename E, typename EL, int LAYOUT, typename A>
+__device__ __forceinline__ void group(const Ctx<NC, VR, E, EL, LAYOUT> &C, int &q, cx<A> (&Wc)[NC][NC],
+                                      cx<A> (&acc)[NC][4][VR]) {
+    constexpr int K = popc4(M);
+    cx<A> Wn[NC][NC];
 #pragma unroll 1
-    for (int b = 0; b < (1 << K); ++b) {
-        A sig[4] = {1, 1, 1, 1};
-        long long m = C.n;
-        {
-            int jbit = 0;
-#pragma unroll
-            for (int mu = 0; mu < 4; ++mu) {
-                if ((M >> mu) & 1) {
-                    const bool neg = (b >> jbit) & 1;
-                    sig[mu] = neg ? (A)-1 : (A)1;
-                    m += neg ? C.dm[mu] : C.dp[mu];
-                    ++jbit;
-                }
-            }
-        }
-        const A sl = sig[lead_axis(M)];
-        A e[4];
-#pragma unroll
-        for (int mu = 0; mu < 4; ++mu) e[mu] = sig[mu] * sl;
-        const A d = -C.sgn * ck * sl;
-
-        // the next offset's W~ (storage order = visiting order)
-        cx<A> Wn[NC][NC];
-        if (q + 1 < 80) load_mat_s<NC, EL, A>(C.wp + (long long)(q + 1) * C.dq, C.ws, Wn);
-
-        const E *pm = C.in + 2 * (L::vec(C.g, m, NC * 4, 0) + C.vbase);
-#pragma unroll
-        for (int kc = 0; kc < NC; ++kc) {
-            cx<A> p[4][VR];
-#pragma unroll
-            for (int s = 0; s < 4; ++s) load_cx<E, VR, A>(pm + 2 * (kc * 4 + s) * cs, p[s]);
-#pragma unroll
-            for (int v = 0; v < VR; ++v) {
-                const cx<A> pv[4] = {p[0][v], p[1][v], p[2][v], p[3][v]};
-                const cx<A> f0 = spin_mix<M, 0>(pv, e, d);
-                const cx<A> f1 = spin_mix<M, 1>(pv, e, d);
-                const cx<A> f2 = spin_mix<M, 2>(pv, e, d);
-                const cx<A> f3 = spin_mix<M, 3>(pv, e, d);
-#pragma unroll
-                for (int a = 0; a < NC; ++a) {
-                    cmac(acc[a][0][v], Wc[a][kc], f0);
-                    cmac(acc[a][1][v], Wc[a][kc], f1);
-                    cmac(acc[a][2][v], Wc[a][kc], f2);
-                    cmac(acc[a][3][v], Wc[a][kc], f3);
-                }
-            }
-        }
-#pragma unroll
-        for (int a = 0; a < NC; ++a)
-#pragma unroll
-            for (int c = 0; c < NC; ++c) Wc[a][c] = Wn[a][c];
-        ++q;
+    for (int b = 0; b < (1 << K); b += 2) {
+        offset<M>(C, q, b, Wc, Wn, acc);
+        offset<M>(C, q + 1, b + 1, Wn, Wc, acc);
+        q += 2;
     }
 }
 
