@@ -72,10 +72,9 @@ __device__ __forceinline__ cx<A> spin_mix(const cx<A> (&p)[4], const A (&e)[4], 
 template <int NC, int VR, typename E, typename EL, int LAYOUT>
 struct Ctx {
     using A = typename Acc<E>::T;
-    const EL *wp;          // this site's W~ (offset 0, element 0)
-    long long dq, ws;      // W~ stride per offset, per matrix element (in elements)
+    const EL *wp;          // this site's W~ (offset 0, element 0), [q][a][b]
     const E *in;
-    long long n;           // output site
+    int n;                 // output site (volumes are below 2^31 sites)
     long long vbase;       // offset of this thread's RHS inside a site (complex numbers)
     int dp[4], dm[4];      // site-index offsets of n + mu and n - mu (periodic)
     Lat g;
@@ -93,7 +92,7 @@ __device__ __forceinline__ void offset(const Ctx<NC, VR, E, EL, LAYOUT> &C, int 
     const A ck = (A)c_lambda(K);
     const long long cs = L::cs_stride(C.g);
     A sig[4] = {1, 1, 1, 1};
-    long long m = C.n;
+    int m = C.n;
     {
         int jbit = 0;
 #pragma unroll
@@ -112,9 +111,10 @@ __device__ __forceinline__ void offset(const Ctx<NC, VR, E, EL, LAYOUT> &C, int 
     for (int mu = 0; mu < 4; ++mu) e[mu] = sig[mu] * sl;
     const A d = -C.sgn * ck * sl;
 
-    if (q + 1 < 80) load_mat_s<NC, EL, A>(C.wp + (long long)(q + 1) * C.dq, C.ws, Wnext);
+    // one site's W~ are contiguous: compile-time element offsets
+    if (q + 1 < 80) load_mat<NC, EL, A>(C.wp + (q + 1) * (2 * NC * NC), Wnext);
 
-    const E *pm = C.in + 2 * (L::vec(C.g, m, NC * 4, 0) + C.vbase);
+    const E *pm = C.in + 2 * (L::vec(C.g, (long long)m, NC * 4, 0) + C.vbase);
 #pragma unroll
     for (int kc = 0; kc < NC; ++kc) {
         cx<A> p[4][VR];
@@ -183,12 +183,10 @@ __global__ void __launch_bounds__(stencil_max_threads(MINB), (MINB > 1 ? 1 : 0))
     bril::Ctx<NC, VR, E, EL, LAYOUT> C;
     C.g = g;
     C.in = in;
-    C.n = n;
+    C.n = (int)n;
     C.sgn = sgn;
     C.vbase = (long long)j * VR;
     // W~ of one site contiguous in visiting order for either vector layout
-    C.ws = 1;
-    C.dq = 2LL * NC * NC;
     C.wp = W + 2LL * n * 80 * NC * NC;
     {
         const int co[4] = {c.x, c.y, c.z, c.t};
@@ -211,7 +209,7 @@ __global__ void __launch_bounds__(stencil_max_threads(MINB), (MINB > 1 ? 1 : 0))
             for (int v = 0; v < VR; ++v) acc[a][s][v] = cx<A>{0, 0};
 
     cx<A> Wc[NC][NC];
-    load_mat_s<NC, EL, A>(C.wp, C.ws, Wc);
+    load_mat<NC, EL, A>(C.wp, Wc);
     int q = 0;
     bril::groups_from<1>(C, q, Wc, acc);
 
