@@ -155,6 +155,23 @@ def dist_setup(args):
     return world, rank, local
 
 
+def max_over_ranks(x, world, device):
+    """The largest x over all ranks (one all-reduce; x itself when world = 1)."""
+    if world == 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, ms_step):
+    """Whole-job throughput of independent replicas: the units all ranks
+    processed per second of the slowest rank's step time."""
+    return units_per_rank * world / (ms_step * 1e-3)
+
+
 # ------------------------------------------------------------------ oracle leg
 def oracle_rate(target_s, U_np, sources):
     """FP64 CPU oracle on a bounded sample of output sites of each operator.
@@ -325,13 +342,9 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     clk = clocks.stop()
-    ms_total = t_start.elapsed_time(t_end)
-    if world > 1:
-        t = torch.tensor([ms_total], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = max_over_ranks(t_start.elapsed_time(t_end), world, "cuda")
     ms_step = ms_total / K
-    value = step_flop * world / (ms_step * 1e-3) / 1e9
+    value = job_rate(step_flop, world, ms_step) / 1e9
 
     per_op = {}
     fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk["sm_max"] * 1e6 / 1e12   # TFLOP/s
