@@ -99,7 +99,8 @@ typedef struct dirac_op dirac_op;   /* opaque */
  * precision u_prec = DIRAC_F64 or DIRAC_F32, no boundary phases applied).
  * The operator keeps its own copy of the phased links in geom->prec; for
  * DIRAC_BRILLOUIN it also builds and keeps the 80 off-centre W_s(n) of
- * Tab. off-axis (computed in FP64 from U, stored in geom->prec).
+ * Tab. off-axis (computed from U in FP64 for FP64 operators and in FP32
+ * otherwise, stored in the link precision).
  * Synchronises `stream` before returning.  U may be freed afterwards. */
 int dirac_op_create(dirac_kind kind, const dirac_geom *geom, const void *U,
                     dirac_prec u_prec, void *stream, dirac_op **out);

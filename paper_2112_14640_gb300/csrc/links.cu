@@ -6,8 +6,9 @@
 //               products of signed links V_{+mu}(m) = U_mu(m), V_{-mu}(m) = U_mu(m-mu)^dag.
 //    Grouping the paths by their last hop sigma gives the recursion
 //      W_s(n) = (1/k) sum_{mu: s_mu != 0} W_{s - s_mu mu}(n) V_{s_mu mu}(n + s - s_mu mu),
-//    evaluated level by level (k = 1..4) in shared memory, in FP64, one
-//    thread block per site; the result is stored in the operator precision.
+//    evaluated level by level (k = 1..4) in shared memory, one thread block
+//    per site, in FP64 for FP64 operators and FP32 otherwise; the result is
+//    stored in the link precision.
 #include "bril_dirs.h"
 #include "internal.h"
 
@@ -43,10 +44,10 @@ __global__ void phase_links_kernel(const UE *__restrict__ U, E *__restrict__ out
     }
 }
 
-// signed link V_{sign mu}(m) with boundary phase, in FP64
-template <int NC, typename UE>
+// signed link V_{sign mu}(m) with boundary phase, in the arithmetic type AB
+template <int NC, typename UE, typename AB>
 __device__ __forceinline__ void signed_link(const UE *__restrict__ U, const Lat &g, const Phases &ph,
-                                            const int x[4], int mu, int sign, cx<double> (&L)[NC][NC]) {
+                                            const int x[4], int mu, int sign, cx<AB> (&L)[NC][NC]) {
     const int ext[4] = {g.nx, g.ny, g.nz, g.nt};
     int y[4] = {x[0], x[1], x[2], x[3]};
     if (sign < 0) y[mu] = (y[mu] == 0) ? ext[mu] - 1 : y[mu] - 1;
@@ -58,13 +59,16 @@ __device__ __forceinline__ void signed_link(const UE *__restrict__ U, const Lat 
 #pragma unroll
         for (int b = 0; b < NC; ++b) {
             cx<double> u = ld_u(U, base + (sign > 0 ? a * NC + b : b * NC + a));
-            L[a][b] = sign > 0 ? cx<double>{f * u.re, f * u.im} : cx<double>{f * u.re, -f * u.im};
+            L[a][b] = sign > 0 ? cx<AB>{(AB)(f * u.re), (AB)(f * u.im)} : cx<AB>{(AB)(f * u.re), (AB)(-f * u.im)};
         }
 }
 
+// W in FP64 for FP64 links, in FP32 otherwise (FP32 links carry 24 bits; the
+// four levels add a few FP32 roundings, and FP64 arithmetic is slow here).
 template <int NC, typename UE, typename E>
 __global__ void __launch_bounds__(96) build_w_kernel(const UE *__restrict__ U, E *__restrict__ W, Lat g, Phases ph) {
-    __shared__ cx<double> Ws[81][NC * NC];
+    using AB = std::conditional_t<sizeof(E) == 8, double, float>;
+    __shared__ cx<AB> Ws[81][NC * NC];
     const long long n = blockIdx.x;
     const int dir = threadIdx.x;
     const Coord c = site_coords(g, n);
@@ -79,15 +83,15 @@ __global__ void __launch_bounds__(96) build_w_kernel(const UE *__restrict__ U, E
         k = (s[0] != 0) + (s[1] != 0) + (s[2] != 0) + (s[3] != 0);
         if (k == 0)
             for (int a = 0; a < NC; ++a)
-                for (int b = 0; b < NC; ++b) Ws[40][a * NC + b] = cx<double>{a == b ? 1.0 : 0.0, 0.0};
+                for (int b = 0; b < NC; ++b) Ws[40][a * NC + b] = cx<AB>{(AB)(a == b ? 1 : 0), (AB)0};
     }
     const int pow3[4] = {1, 3, 9, 27};
     __syncthreads();   // the identity at the centre feeds level 1
     for (int level = 1; level <= 4; ++level) {
         if (dir < 81 && k == level) {
-            cx<double> acc[NC][NC];
+            cx<AB> acc[NC][NC];
             for (int a = 0; a < NC; ++a)
-                for (int b = 0; b < NC; ++b) acc[a][b] = cx<double>{0, 0};
+                for (int b = 0; b < NC; ++b) acc[a][b] = cx<AB>{0, 0};
             for (int mu = 0; mu < 4; ++mu) {
                 if (s[mu] == 0) continue;
                 const int prev = dir - s[mu] * pow3[mu];   // offset s - s_mu mu
@@ -97,13 +101,13 @@ __global__ void __launch_bounds__(96) build_w_kernel(const UE *__restrict__ U, E
                     int v = x0[nu] + (nu == mu ? 0 : s[nu]);
                     m[nu] = (v + ext[nu]) % ext[nu];
                 }
-                cx<double> L[NC][NC];
-                signed_link<NC>(U, g, ph, m, mu, s[mu], L);
+                cx<AB> L[NC][NC];
+                signed_link<NC, UE, AB>(U, g, ph, m, mu, s[mu], L);
                 for (int a = 0; a < NC; ++a)
                     for (int b = 0; b < NC; ++b)
                         for (int q = 0; q < NC; ++q) cmac(acc[a][b], Ws[prev][a * NC + q], L[q][b]);
             }
-            const double inv = 1.0 / level;
+            const AB inv = (AB)1 / (AB)level;
             for (int a = 0; a < NC; ++a)
                 for (int b = 0; b < NC; ++b) Ws[dir][a * NC + b] = inv * acc[a][b];
         }
@@ -116,8 +120,8 @@ __global__ void __launch_bounds__(96) build_w_kernel(const UE *__restrict__ U, E
         for (int e = 0; e < NC * NC; ++e) {
             // [site][q][a][b] for either vector layout
             const long long o = bril::w_index(q, e, n, NC);
-            W[2 * o] = from_acc<E, double>(scale * Ws[dir][e].re);
-            W[2 * o + 1] = from_acc<E, double>(scale * Ws[dir][e].im);
+            W[2 * o] = from_acc<E, double>(scale * (double)Ws[dir][e].re);
+            W[2 * o + 1] = from_acc<E, double>(scale * (double)Ws[dir][e].im);
         }
     }
 }
