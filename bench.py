@@ -548,14 +548,17 @@ def solver_comparison(D, I, torch):
         op32.close()
         b = op.to_prec(src)
         row = {"m0": m0, "tuning": info}
-        for inner, links in ((D.F32, D.LINKS_NATIVE), (D.F16, D.LINKS_F32), (D.BF16, D.LINKS_F32),
-                             (D.F16, D.LINKS_NATIVE), (D.BF16, D.LINKS_NATIVE)):
+        for inner, links, mode in ((D.F32, D.LINKS_NATIVE, D.MIXED_RELIABLE),
+                                   (D.F16, D.LINKS_F32, D.MIXED_RELIABLE), (D.BF16, D.LINKS_F32, D.MIXED_RELIABLE),
+                                   (D.F16, D.LINKS_NATIVE, D.MIXED_RELIABLE), (D.BF16, D.LINKS_NATIVE, D.MIXED_RELIABLE),
+                                   (D.F16, D.LINKS_F32, D.MIXED_ADAPTIVE), (D.BF16, D.LINKS_F32, D.MIXED_ADAPTIVE)):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             x, st = op.solve(b, m0=m0, solver=D.CG_NORMAL, tol=1e-10, maxit=40000, inner_prec=inner,
-                             sloppy_links=links)
+                             sloppy_links=links, mixed_mode=mode)
             torch.cuda.synchronize()
-            name = D.PREC_NAMES[inner] + ("+f32links" if links == D.LINKS_F32 else "")
+            name = D.PREC_NAMES[inner] + ("+f32links" if links == D.LINKS_F32 else "") + \
+                ("+adaptive" if mode == D.MIXED_ADAPTIVE else "")
             row[name] = {"seconds": time.perf_counter() - t0, "iters": st["iters"],
                                         "updates": st["outer_iters"], "status": st["status"],
                                         "max_relres": max(st["relres"]), "max_true_relres": max(st["true_relres"]),

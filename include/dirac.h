@@ -228,7 +228,8 @@ typedef struct {
                               iterations in inner_prec */
     double inner_tol;      /* restarted mode: relative tolerance of each inner solve (0 = default) */
     int recompute_every;   /* 0 = paper default: 50 for F64 solves, 20 otherwise */
-    int mixed_mode;        /* DIRAC_MIXED_RELIABLE (CG only) or DIRAC_MIXED_RESTART */
+    int mixed_mode;        /* DIRAC_MIXED_RELIABLE (CG only), DIRAC_MIXED_RESTART or
+                              DIRAC_MIXED_ADAPTIVE (CG only) */
     int sloppy_links;      /* link storage of the inner operator: DIRAC_LINKS_NATIVE or
                               DIRAC_LINKS_F32 (16-bit inner vectors with FP32 links) */
     double delta;          /* reliable updates: recompute when the sloppy residual fell by
@@ -241,8 +242,13 @@ typedef struct {
  * one Krylov iteration in inner_prec on the scaled residual, with the
  * solution and the true residual refreshed in the operator precision each
  * time the iterated residual has dropped by delta; the search direction is
- * kept across refreshes.  BiCGstab always uses RESTART. */
-enum { DIRAC_MIXED_RELIABLE = 0, DIRAC_MIXED_RESTART = 1 };
+ * kept across refreshes.  ADAPTIVE (CG, 16-bit inner_prec, FP64 operator):
+ * RELIABLE in inner_prec while the refreshes keep halving the true residual
+ * (4 refreshes in a row that fail to end it), then RELIABLE with an FP32
+ * iteration from the current solution, within the same maxit; the stats
+ * count both phases (no counterpart in the paper).  For other inner
+ * precisions it is RELIABLE.  BiCGstab always uses RESTART. */
+enum { DIRAC_MIXED_RELIABLE = 0, DIRAC_MIXED_RESTART = 1, DIRAC_MIXED_ADAPTIVE = 2 };
 
 typedef struct {
     int iters;                 /* Krylov iterations (summed over inner solves) */

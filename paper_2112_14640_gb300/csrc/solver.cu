@@ -498,7 +498,7 @@ __global__ void inverse_kernel(int nv, const double *c, double *inv) {
 // (rescaled) instead of restarting.  Converged RHS are frozen.
 // Workspace: hi vectors 0..1, lo vectors 0..3.
 static int cg_reliable(const dirac_op *hi, const dirac_op *lo, const void *rhs, void *x, double m0, double tol,
-                       int maxit, double delta, CoreOut &out, Lanczos *lan, cudaStream_t s) {
+                       int maxit, double delta, CoreOut &out, Lanczos *lan, cudaStream_t s, int give_up = 30) {
     Ws wh, wl;
     TRY(get_ws(hi, wh));
     TRY(get_ws(lo, wl));
@@ -608,11 +608,11 @@ static int cg_reliable(const dirac_op *hi, const dirac_op *lo, const void *rhs, 
                 // the true residual grew across the segment: the sloppy search
                 // direction is no longer useful, restart it below
                 stalled[v] = stalled[v] || sqrt(rrt[v]) > prev_true[v];
-                // give up when 30 updates in a row failed to halve the best true residual
+                // give up when give_up updates in a row failed to halve the best true residual
                 if (sqrt(rrt[v]) < 0.5 * best_true[v]) {
                     best_true[v] = sqrt(rrt[v]);
                     slow[v] = 0;
-                } else if (++slow[v] >= 30) {
+                } else if (++slow[v] >= give_up) {
                     stagnated = true;
                 }
                 prev_true[v] = sqrt(rrt[v]);
@@ -764,10 +764,27 @@ static int reliable_solve(const dirac_op *op, const void *b, void *x, double m0,
     CoreOut co;
     Lanczos lan;
     const double delta = prm->delta > 0 ? prm->delta : 0.1;
-    TRY(cg_reliable(op, lo, rhs, x, m0, prm->tol, prm->maxit, delta, co, &lan, s));
-    st->iters = co.iters;
-    st->outer_iters = co.recomputes;
-    st->recomputes = co.recomputes;
+    const bool half = prm->inner_prec == DIRAC_BF16 || prm->inner_prec == DIRAC_F16;
+    const bool adaptive = prm->mixed_mode == DIRAC_MIXED_ADAPTIVE && half && op->prec == DIRAC_F64;
+    // adaptive: the 16-bit iteration runs while reliable updates keep halving
+    // the true residual (4 misses in a row end it), then an FP32 iteration
+    // continues from the current solution
+    TRY(cg_reliable(op, lo, rhs, x, m0, prm->tol, prm->maxit, delta, co, &lan, s, adaptive ? 4 : 30));
+    int iters = co.iters, updates = co.recomputes;
+    if (adaptive && co.status == DIRAC_STAGNATED && co.iters < prm->maxit) {
+        dirac_op *lo32 = nullptr;
+        TRY(op_inner(op, DIRAC_F32, DIRAC_LINKS_NATIVE, &lo32, s));
+        CoreOut co2;
+        Lanczos lan2;
+        TRY(cg_reliable(op, lo32, rhs, x, m0, prm->tol, prm->maxit - co.iters, delta, co2, &lan2, s));
+        co = co2;
+        lan = lan2;
+        iters += co2.iters;
+        updates += co2.recomputes;
+    }
+    st->iters = iters;
+    st->outer_iters = updates;
+    st->recomputes = updates;
     st->status = co.status;
     bool all = true;
     for (int v = 0; v < op->nv; ++v) {
@@ -821,7 +838,7 @@ int solve(const dirac_op *op, const void *b, void *x, double m0, const dirac_sol
     memset(&st, 0, sizeof(st));
     int rc;
     if (prm->inner_prec == op->prec) rc = plain_solve(op, b, x, m0, prm, &st, s);
-    else if (prm->solver != DIRAC_BICGSTAB && prm->mixed_mode == DIRAC_MIXED_RELIABLE)
+    else if (prm->solver != DIRAC_BICGSTAB && prm->mixed_mode != DIRAC_MIXED_RESTART)
         rc = reliable_solve(op, b, x, m0, prm, &st, s);
     else rc = mixed_solve(op, b, x, m0, prm, &st, s);
     if (rc) return rc;
@@ -851,7 +868,8 @@ extern "C" int dirac_solve(const dirac_op *op, const void *b, void *x, double m0
         return DIRAC_ERR_INVALID_ARG;
     if (params->inner_prec < DIRAC_F64 || params->inner_prec > DIRAC_F16) return DIRAC_ERR_UNSUPPORTED_PREC;
     if (!(params->tol > 0) || params->maxit < 1) return DIRAC_ERR_INVALID_ARG;
-    if (params->mixed_mode != DIRAC_MIXED_RELIABLE && params->mixed_mode != DIRAC_MIXED_RESTART)
+    if (params->mixed_mode != DIRAC_MIXED_RELIABLE && params->mixed_mode != DIRAC_MIXED_RESTART &&
+        params->mixed_mode != DIRAC_MIXED_ADAPTIVE)
         return DIRAC_ERR_INVALID_ARG;
     if (params->delta < 0 || params->delta >= 1) return DIRAC_ERR_INVALID_ARG;
     if (params->sloppy_links != DIRAC_LINKS_NATIVE && params->sloppy_links != DIRAC_LINKS_F32)

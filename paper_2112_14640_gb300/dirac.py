@@ -23,7 +23,7 @@ from . import build as _build
 WILSON, BRILLOUIN, STAGGERED = 0, 1, 2
 F64, F32, BF16, F16 = 0, 1, 2, 3
 CG_NORMAL, BICGSTAB, CG_HPD = 0, 1, 2
-MIXED_RELIABLE, MIXED_RESTART = 0, 1
+MIXED_RELIABLE, MIXED_RESTART, MIXED_ADAPTIVE = 0, 1, 2
 FORCE_TA, FORCE_GRAD = 0, 1
 PREC_NAMES = {F64: "f64", F32: "f32", BF16: "bf16", F16: "f16"}
 KIND_NAMES = {WILSON: "wilson", BRILLOUIN: "brillouin", STAGGERED: "staggered"}

@@ -37,3 +37,16 @@ def rounded(v_np, prec):
     dt = torch.bfloat16 if prec == D.BF16 else torch.float16
     r = torch.view_as_real(t).to(dt).to(torch.float64)
     return torch.view_as_complex(r.contiguous()).numpy()
+
+
+def golden_flops():
+    """tests/golden/app_e_flops_per_site.txt as {operator: (nc, flops, flops_nv12 or None, polynomial)}."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "app_e_flops_per_site.txt")
+    out = {}
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        name, nc, f, f12, poly = line.split()
+        out[name] = (int(nc), int(f), None if f12 == "-" else int(f12), poly)
+    return out

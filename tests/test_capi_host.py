@@ -38,9 +38,14 @@ def test_every_declared_symbol_is_exported(lib):
 
 
 def test_flop_counts_match_app_e(lib):
-    assert D.flops_per_site(D.WILSON, 3) == 1368
-    assert D.flops_per_site(D.BRILLOUIN, 3) == 30168
-    assert D.flops_per_site(D.STAGGERED, 3) == 582
+    """dirac_flops_per_site against the values and N_c polynomials App. E
+    prints (tests/golden/app_e_flops_per_site.txt)."""
+    from helpers import golden_flops
+    kinds = {"wilson": D.WILSON, "brillouin": D.BRILLOUIN, "staggered": D.STAGGERED}
+    for name, (nc, flops, flops12, poly) in golden_flops().items():
+        assert D.flops_per_site(kinds[name], nc) == flops
+        for n in (1, 2, 3, 4):
+            assert D.flops_per_site(kinds[name], n) == eval(poly.replace("^", "**"), {"nc": n})
     assert D.flops_per_site(7, 3) == -1
 
 

@@ -190,3 +190,22 @@ def test_f32_cg_light_staggered_single_and_batched():
     assert rc == 0 and all(s["status"] == 0 for s in stats), stats
     assert np.all(normal_relres(ref, to_numpy(op, xs[0]), b, m0) < 2e-5)
     assert np.all(normal_relres(ref, to_numpy(op2, xs[1]), b, m0) < 2e-5)
+
+
+def test_adaptive_mode_finishes_a_stalling_fp16_solve():
+    """Staggered at m0 = 0.05 with FP16 sloppy vectors and FP32 sloppy links:
+    plain reliable updates need > 20000 iterations here; the adaptive mode
+    hands over to an FP32 iteration once the FP16 one stops gaining and
+    reaches 1e-10 (checked by the oracle)."""
+    m0 = 0.05
+    op, ref, b = setup(D.STAGGERED, (4, 4, 4, 8), 3, 4, (1, 1, 1, -1), D.F64, layout=D.SITE_INNER)
+    x, st = op.solve(to_device(op, b), m0=m0, tol=1e-10, maxit=20000, inner_prec=D.F16,
+                     sloppy_links=D.LINKS_F32, mixed_mode=D.MIXED_ADAPTIVE)
+    assert st["status"] == 0, st
+    assert st["iters"] < 5000, st
+    assert np.all(normal_relres(ref, to_numpy(op, x), b, m0) < 1.01e-10)
+    # FP32 inner: adaptive is the plain reliable mode
+    x2, st2 = op.solve(to_device(op, b), m0=m0, tol=1e-10, maxit=20000, inner_prec=D.F32,
+                       mixed_mode=D.MIXED_ADAPTIVE)
+    x3, st3 = op.solve(to_device(op, b), m0=m0, tol=1e-10, maxit=20000, inner_prec=D.F32)
+    assert st2["iters"] == st3["iters"] and torch.equal(x2, x3)

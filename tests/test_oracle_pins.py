@@ -357,9 +357,16 @@ def test_cg_stagnation_rule_reports_discrepancy():
 # ------------------------------------------------------------ App. E counts
 
 def test_flop_counts_app_e():
-    assert O.flops_per_site(O.WILSON, 3) == 1368
-    assert O.flops_per_site(O.BRILLOUIN, 3) == 30168
-    assert O.flops_per_site(O.STAGGERED, 3) == 582
+    """The oracle's flop counts against the values and N_c polynomials App. E
+    prints (tests/golden/app_e_flops_per_site.txt)."""
+    from helpers import golden_flops
+    kinds = {"wilson": O.WILSON, "brillouin": O.BRILLOUIN, "staggered": O.STAGGERED}
+    for name, (nc, flops, flops12, poly) in golden_flops().items():
+        assert O.flops_per_site(kinds[name], nc) == flops
+        if flops12 is not None:
+            assert 12 * O.flops_per_site(kinds[name], nc) == flops12
+        for n in (1, 2, 3, 4):
+            assert O.flops_per_site(kinds[name], n) == eval(poly.replace("^", "**"), {"nc": n})
 
 
 # ------------------------------------------------------------- fermion force
@@ -411,3 +418,40 @@ def test_action_gradient_matches_finite_differences():
     fd = (Sp - Sm) / (2 * eps)
     an = float(np.sum(np.real(np.conj(G) * dU)))
     assert abs(fd - an) < 1e-6 * abs(an)
+
+
+def test_brillouin_weights_golden_and_free_field_moments():
+    """The printed weights (tests/golden/brillouin_weights.txt) satisfy the
+    identities that make Eq. (def_ider) a derivative and Eq. (def_blap) a
+    Laplacian on the 3^4 hypercube: sum_s rho_k s_mu^2 = 1, sum_s lambda_k =
+    0, sum_s lambda_k s_mu^2 = 2 (k = |s|_1); and the oracle's free D_B acting
+    on a plane wave of momentum p along x equals the symbol built from them."""
+    import itertools
+    import os
+    from fractions import Fraction
+    path = os.path.join(os.path.dirname(__file__), "golden", "brillouin_weights.txt")
+    w = {}
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        name, rest = line.split(None, 1)
+        nums, den = rest.split("/")
+        w[name] = [Fraction(int(a), int(den)) for a in nums.split()]
+    rho, lam = [None] + w["rho"], w["lambda"]
+    offs = [s for s in itertools.product((-1, 0, 1), repeat=4)]
+    k = lambda s: sum(1 for a in s if a)
+    assert sum(rho[k(s)] * s[0] ** 2 for s in offs if k(s)) == 1
+    assert sum(lam[k(s)] for s in offs) == 0
+    assert sum(lam[k(s)] * s[0] ** 2 for s in offs) == 2
+    # free field: D_B e^{ipx} = [sum_s (rho_k i s.gamma-part) ...]; check the
+    # scalar (Laplacian) part on a plane wave through the oracle with m0 = 0:
+    # the gamma-free part of the symbol is -1/2 sum_s lambda_k e^{i p s_x}
+    dims, p = (8, 4, 4, 4), 2 * np.pi / 8
+    U = I.unit_gauge_field(dims, 1)
+    op = O.Operator(O.BRILLOUIN, U, (1, 1, 1, 1))
+    x = np.arange(dims[0])
+    psi = np.zeros((dims[3], dims[2], dims[1], dims[0], 1, 4, 1), complex)
+    psi[..., 0, 0, 0] = np.exp(1j * p * x)[None, None, None, :]
+    out = op.apply(psi, 0.0)
+    scal = float(-0.5 * sum(lam[k(s)] * np.cos(p * s[0]) for s in offs))
+    assert np.allclose(out[..., 0, 0, 0], scal * psi[..., 0, 0, 0], atol=1e-12)
