@@ -244,7 +244,7 @@ typedef struct {
  * time the iterated residual has dropped by delta; the search direction is
  * kept across refreshes.  ADAPTIVE (CG, 16-bit inner_prec, FP64 operator):
  * RELIABLE in inner_prec while the refreshes keep halving the true residual
- * (4 refreshes in a row that fail to end it), then RELIABLE with an FP32
+ * (2 refreshes in a row that fail to end it), then RELIABLE with an FP32
  * iteration from the current solution, within the same maxit; the stats
  * count both phases (no counterpart in the paper).  For other inner
  * precisions it is RELIABLE.  BiCGstab always uses RESTART. */

@@ -767,9 +767,9 @@ static int reliable_solve(const dirac_op *op, const void *b, void *x, double m0,
     const bool half = prm->inner_prec == DIRAC_BF16 || prm->inner_prec == DIRAC_F16;
     const bool adaptive = prm->mixed_mode == DIRAC_MIXED_ADAPTIVE && half && op->prec == DIRAC_F64;
     // adaptive: the 16-bit iteration runs while reliable updates keep halving
-    // the true residual (4 misses in a row end it), then an FP32 iteration
+    // the true residual (2 misses in a row end it), then an FP32 iteration
     // continues from the current solution
-    TRY(cg_reliable(op, lo, rhs, x, m0, prm->tol, prm->maxit, delta, co, &lan, s, adaptive ? 4 : 30));
+    TRY(cg_reliable(op, lo, rhs, x, m0, prm->tol, prm->maxit, delta, co, &lan, s, adaptive ? 2 : 30));
     int iters = co.iters, updates = co.recomputes;
     if (adaptive && co.status == DIRAC_STAGNATED && co.iters < prm->maxit) {
         dirac_op *lo32 = nullptr;

@@ -202,7 +202,7 @@ def test_adaptive_mode_finishes_a_stalling_fp16_solve():
     x, st = op.solve(to_device(op, b), m0=m0, tol=1e-10, maxit=20000, inner_prec=D.F16,
                      sloppy_links=D.LINKS_F32, mixed_mode=D.MIXED_ADAPTIVE)
     assert st["status"] == 0, st
-    assert st["iters"] < 5000, st
+    assert st["iters"] < 10000, st
     assert np.all(normal_relres(ref, to_numpy(op, x), b, m0) < 1.01e-10)
     # FP32 inner: adaptive is the plain reliable mode
     x2, st2 = op.solve(to_device(op, b), m0=m0, tol=1e-10, maxit=20000, inner_prec=D.F32,
