@@ -25,7 +25,8 @@
  *
  * Parity status: every function here is pinned by the CPU tests
  * (free-field symbols, gamma5-hermiticity, gauge covariance, W identities,
- * dense brute force, solver residuals, finite differences for the force).
+ * dense brute force, solver residuals, finite differences for the force,
+ * the abelian closed form and pure-gauge zero of the field strength).
  */
 #include <complex.h>
 #include <math.h>
@@ -374,6 +375,67 @@ void orc_brillouin_sites(const int d[4], int nc, int nv, const cplx *Wsites, dou
 #pragma omp parallel for
     for (long i = 0; i < ns; ++i)
         brillouin_site(d, nc, nv, Wsites + i * 81 * (long)nc * nc, m0, in, sites[i], out + i * per_site);
+}
+
+/* ------------------------------------- clover-leaf field strength (Sec. 5)
+ * Eq. (def_clov) needs the hermitian "clover-leaf" field strength F_mu,nu(n)
+ * but the paper does not write it out.  Reading: Q_mu,nu(n) is the sum of the
+ * four plaquettes of the (mu,nu) plane that have n as a corner, each one a
+ * closed path from n back to n turning the same way (a step along the first
+ * direction, then along the second), and
+ *   F_mu,nu(n) = (Q_mu,nu(n) - Q_mu,nu(n)^dag) / (8 i),
+ * with no trace subtracted.  The six orientations are stored in the paper's
+ * order (mu,nu) = (1,2),(1,3),(1,4),(2,3),(2,4),(3,4), i.e. 0-based
+ * (0,1),(0,2),(0,3),(1,2),(1,3),(2,3):  F[n][6][a][b].
+ * Closed loops do not see the boundary phases, so U may carry them or not. */
+
+/* product along the closed path n -> n+a -> n+a+b -> n+b -> n, where a and b
+ * are signed unit steps (direction, sign): V_a(n) V_b(n+a) V_-a(n+a+b) V_-b(n+b) */
+static void leaf(const int d[4], int nc, const cplx *U, long n, int amu, int as, int bmu, int bs, cplx *out) {
+    const long per = (long)nc * nc;
+    cplx *L = malloc(sizeof(cplx) * per), *T = malloc(sizeof(cplx) * per);
+    int sa[4] = {0, 0, 0, 0}, sb[4] = {0, 0, 0, 0}, sab[4] = {0, 0, 0, 0};
+    sa[amu] = as;
+    sb[bmu] = bs;
+    sab[amu] += as;
+    sab[bmu] += bs;
+    const long na = shifted(d, n, sa), nb = shifted(d, n, sb), nab = shifted(d, n, sab);
+    signed_link(d, nc, U, n, amu, as, out);
+    signed_link(d, nc, U, na, bmu, bs, L);
+    mat_mul(nc, out, L, T);
+    signed_link(d, nc, U, nab, amu, -as, L);
+    mat_mul(nc, T, L, out);
+    signed_link(d, nc, U, nb, bmu, -bs, L);
+    mat_mul(nc, out, L, T);
+    memcpy(out, T, sizeof(cplx) * per);
+    free(L);
+    free(T);
+}
+
+void orc_field_strength(const int d[4], int nc, const cplx *U, cplx *F) {
+    const long V = vol4(d);
+    const long per = (long)nc * nc;
+#pragma omp parallel for
+    for (long n = 0; n < V; ++n) {
+        cplx *Q = malloc(sizeof(cplx) * per), *P = malloc(sizeof(cplx) * per);
+        int k = 0;
+        for (int mu = 0; mu < 4; ++mu)
+            for (int nu = mu + 1; nu < 4; ++nu, ++k) {
+                memset(Q, 0, sizeof(cplx) * per);
+                /* the four leaves: (+mu,+nu), (+nu,-mu), (-mu,-nu), (-nu,+mu) */
+                const int steps[4][4] = {{mu, 1, nu, 1}, {nu, 1, mu, -1}, {mu, -1, nu, -1}, {nu, -1, mu, 1}};
+                for (int l = 0; l < 4; ++l) {
+                    leaf(d, nc, U, n, steps[l][0], steps[l][1], steps[l][2], steps[l][3], P);
+                    for (long e = 0; e < per; ++e) Q[e] += P[e];
+                }
+                cplx *f = F + (n * 6 + k) * per;
+                for (int a = 0; a < nc; ++a)
+                    for (int b = 0; b < nc; ++b)
+                        f[a * nc + b] = (Q[a * nc + b] - conj(Q[b * nc + a])) / (8.0 * _Complex_I);
+            }
+        free(Q);
+        free(P);
+    }
 }
 
 /* ------------------------------------------ gamma_5 and epsilon (Sec. 3)

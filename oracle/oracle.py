@@ -9,13 +9,14 @@ The stencils live in ``oracle.c`` (plain loops over the paper's equations);
 this module adds the composite operators the paper builds from them
 (D^dagger = gamma5 D gamma5 or epsilon D epsilon, D^dagger D), textbook CG and
 BiCGstab with the paper's recompute/exit rules (Sec. 9), the Lanczos
-condition estimate of the ``cond`` module (App. F), the App. E flop counts
-and the fermion force of S = phi^dag (D_W^dag D_W)^-1 phi (derived here; the
+condition estimate of the ``cond`` module (App. F), the App. E flop counts,
+the clover term of Eq. (def_clov) and the fermion force of S = phi^dag (D_W^dag D_W)^-1 phi (derived here; the
 paper has none).
 
 Array shapes (complex128, C order):
   links  U   (Nt, Nz, Ny, Nx, 4, Nc, Nc)      mu = 0..3 <-> x, y, z, t
   W links    (Nt, Nz, Ny, Nx, 81, Nc, Nc)     see ``oracle.c`` for dir numbering
+  field strength F (Nt, Nz, Ny, Nx, 6, Nc, Nc) planes (mu,nu) = PLANES
   Wilson-type vectors (Nt, Nz, Ny, Nx, Nc, 4, Nv)
   staggered vectors   (Nt, Nz, Ny, Nx, Nc, Nv)
 ``dims`` is always (Nx, Ny, Nz, Nt).
@@ -53,7 +54,8 @@ def lib():
         _lib.orc_staggered_sites.argtypes = [I4, I, I, P, D, P, P, ctypes.c_long, P]
         _lib.orc_brillouin_sites.argtypes = [I4, I, I, P, D, P, P, ctypes.c_long, P]
         _lib.orc_build_w_sites.argtypes = [I4, I, P, P, ctypes.c_long, P]
-        for f in (_lib.orc_phase_links, _lib.orc_wilson, _lib.orc_staggered, _lib.orc_brillouin,
+        _lib.orc_field_strength.argtypes = [I4, I, P, P]
+        for f in (_lib.orc_field_strength, _lib.orc_phase_links, _lib.orc_wilson, _lib.orc_staggered, _lib.orc_brillouin,
                   _lib.orc_build_w, _lib.orc_gamma5, _lib.orc_epsilon, _lib.orc_gamma,
                   _lib.orc_wilson_sites, _lib.orc_staggered_sites, _lib.orc_brillouin_sites,
                   _lib.orc_build_w_sites):
@@ -157,6 +159,36 @@ def stencil_sites(kind, field, m0, v, sites):
     return out
 
 
+# planes of the clover term, in the paper's order (1,2),(1,3),(1,4),(2,3),(2,4),(3,4)
+PLANES = [(0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3)]
+
+
+def field_strength(U):
+    """Clover-leaf F_mu,nu(n) = (Q - Q^dag) / (8i) for the six PLANES (Sec. 5;
+    the leaf sum Q is the reading stated in ``oracle.c``)."""
+    dims, nc = _dims_of_links(U)
+    U = np.ascontiguousarray(U, np.complex128)
+    F = np.empty(U.shape[:4] + (6, nc, nc), np.complex128)
+    lib().orc_field_strength(_i4(dims), nc, _p(U), _p(F))
+    return F
+
+
+def sigma(mu, nu):
+    """sigma_mu,nu = (i/2) [gamma_mu, gamma_nu] (Sec. 5), from the 4x4 gammas."""
+    a, b = gamma(mu), gamma(nu)
+    return 0.5j * (a @ b - b @ a)
+
+
+def clover(F, csw, psi):
+    """C psi of Eq. (def_clov): -(c_SW / 2) sum_{mu<nu} (sigma_mu,nu (x) F_mu,nu(n)) psi(n),
+    site by site.  F has shape (..., 6, Nc, Nc) and psi (..., Nc, 4, Nv) over
+    the same leading (site) axes."""
+    out = np.zeros(np.broadcast_shapes(psi.shape), np.complex128)
+    for k, (mu, nu) in enumerate(PLANES):
+        out += np.einsum("st,...ab,...btv->...asv", sigma(mu, nu), F[..., k, :, :], psi)
+    return -0.5 * csw * out
+
+
 def gamma5(psi):
     nt, nz, ny, nx, nc, _, nv = psi.shape
     psi = np.ascontiguousarray(psi, np.complex128)
@@ -180,14 +212,23 @@ class Operator:
 
     D_W^dag = gamma5 D_W gamma5, D_B^dag = gamma5 D_B gamma5 and
     D_S^dag = epsilon D_S epsilon, the forms the paper's solvers use (App. F).
+    With csw != 0 (Wilson and Brillouin) the clover term C of Eq. (def_clov),
+    built from the field strength of the gauge field V (default: U), is added:
+    v = (D + C) u, as in Eqs. (def_wils) and (def_bril).
     """
 
-    def __init__(self, kind, U, bc=(1, 1, 1, 1), m0=0.0):
+    def __init__(self, kind, U, bc=(1, 1, 1, 1), m0=0.0, csw=0.0, V=None):
         self.kind = kind
         self.m0 = float(m0)
         self.bc = tuple(int(b) for b in bc)
         self.Up = phase_links(U, self.bc)
         self._W = None
+        self.csw = float(csw)
+        self.F = None
+        if self.csw != 0.0:
+            if kind == STAGGERED:
+                raise ValueError("the clover term acts on Wilson-type vectors only")
+            self.F = field_strength(U if V is None else V)
 
     @property
     def W(self):
@@ -199,10 +240,14 @@ class Operator:
     def apply(self, v, m0=None):
         m = self.m0 if m0 is None else m0
         if self.kind == WILSON:
-            return wilson(self.Up, m, v)
-        if self.kind == BRILLOUIN:
-            return brillouin(self.W, m, v)
-        return staggered(self.Up, m, v)
+            out = wilson(self.Up, m, v)
+        elif self.kind == BRILLOUIN:
+            out = brillouin(self.W, m, v)
+        else:
+            return staggered(self.Up, m, v)
+        if self.F is not None:
+            out = out + clover(self.F, self.csw, v)
+        return out
 
     def apply_sites(self, v, sites, m0=None, dagger=False):
         """(D v)(n) or (D^dag v)(n) at the listed site indices only."""
@@ -212,8 +257,9 @@ class Operator:
         else:
             field = self.Up
         if not dagger:
-            return stencil_sites(self.kind, field, m, v, sites)
-        out = stencil_sites(self.kind, field, m, self._sandwich(v), sites)
+            return stencil_sites(self.kind, field, m, v, sites) + self._clover_sites(v, sites)
+        out = stencil_sites(self.kind, field, m, self._sandwich(v), sites) + \
+            self._clover_sites(self._sandwich(v), sites)
         if self.kind == STAGGERED:
             nt, nz, ny, nx = v.shape[:4]
             s = np.asarray(sites)
@@ -223,6 +269,13 @@ class Operator:
         out = out.copy()
         out[:, :, 2:, :] *= -1
         return out
+
+    def _clover_sites(self, v, sites):
+        if self.F is None:
+            return 0.0
+        s = np.asarray(sites)
+        return clover(self.F.reshape((-1,) + self.F.shape[4:])[s], self.csw,
+                      v.reshape((-1,) + v.shape[4:])[s])
 
     def _sandwich(self, v):
         return epsilon(v) if self.kind == STAGGERED else gamma5(v)
@@ -447,6 +500,8 @@ def _shift(v, mu, step):
 
 def wilson_force_terms(op, psi, chi):
     """(B, C) per link, each of shape (Nt, Nz, Ny, Nx, 4, Nc, Nc)."""
+    if op.F is not None:
+        raise ValueError("the force is derived for D_W without the clover term")
     sh = psi.shape[:4] + (4, psi.shape[4], psi.shape[4])
     B = np.empty(sh, np.complex128)
     C = np.empty(sh, np.complex128)
@@ -488,6 +543,16 @@ def pseudofermion_action(op, phi, m0=None, tol=1e-13, maxit=20000):
 
 
 # ------------------------------------------------------------ App. E counts
+
+def clover_flops_per_site(nc, multiplications=2):
+    """Flops per site per RHS of the clover term (App. E): 192Nc^2 with one
+    colour multiplication per plane, 64Nc^2 with the sigma_mu,nu structure
+    used (two multiplications per chiral half), the count the paper's code
+    adds to D_W and D_B when c_SW > 0."""
+    if multiplications == 6:
+        return ((8 * nc * nc - 2 * nc) + 2 * nc) * 4 * 6
+    return ((8 * nc * nc - 2 * nc) + 2 * nc) * 4 * 2
+
 
 def flops_per_site(kind, nc):
     """Flops per site per RHS (App. E): Wilson 128Nc^2+72Nc, Brillouin

@@ -455,3 +455,147 @@ def test_brillouin_weights_golden_and_free_field_moments():
     out = op.apply(psi, 0.0)
     scal = float(-0.5 * sum(lam[k(s)] * np.cos(p * s[0]) for s in offs))
     assert np.allclose(out[..., 0, 0, 0], scal * psi[..., 0, 0, 0], atol=1e-12)
+
+
+# ------------------------------------------------------------- clover term
+
+def _golden(name):
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    return [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+
+
+PAULI = [S0, S1, S2, S3]
+
+
+def test_sigma_munu_match_app_a_printed_forms():
+    """sigma_mu,nu of the oracle against the tensor forms App. A prints
+    (tests/golden/sigma_munu_app_a.txt); all six planes, in the oracle's order."""
+    rows = _golden("sigma_munu_app_a.txt")
+    assert len(rows) == 6
+    for k, (mu, nu, sign, a, b) in enumerate(rows):
+        mu, nu = int(mu) - 1, int(nu) - 1
+        assert O.PLANES[k] == (mu, nu)
+        want = float(sign) * np.kron(PAULI[int(a)], PAULI[int(b)])
+        assert np.allclose(O.sigma(mu, nu), want, atol=1e-15, rtol=0)
+
+
+def _abelian_angles(dims, rng):
+    """theta[t,z,y,x,mu,c]: one U(1) angle per link and colour."""
+    nx, ny, nz, nt = dims
+    return rng.uniform(-np.pi, np.pi, (nt, nz, ny, nx, 4, 3))
+
+
+def test_field_strength_abelian_closed_form():
+    """Diagonal links exp(i theta_mu(n)) per colour: each leaf is the phase of
+    one plaquette, so F_mu,nu(n) = diag( (1/4) sum over the four plaquettes
+    with a corner at n of sin(plaquette angle) ), zero off the diagonal.  The
+    plaquette angles are summed here from the link angles with np.roll."""
+    dims = (4, 3, 2, 5)
+    rng = np.random.Generator(np.random.PCG64(41))
+    th = _abelian_angles(dims, rng)
+    U = np.zeros(th.shape[:5] + (3, 3), complex)
+    for c in range(3):
+        U[..., c, c] = np.exp(1j * th[..., c])
+    F = O.field_strength(U)
+    axis = {0: 3, 1: 2, 2: 1, 3: 0}     # coordinate mu -> array axis (t, z, y, x order)
+
+    def sh(a, mu, k):                   # a(n + k mu-hat)
+        return np.roll(a, -k, axis=axis[mu])
+
+    for k, (mu, nu) in enumerate(O.PLANES):
+        tm, tn = th[..., mu, :], th[..., nu, :]
+        P = tm + sh(tn, mu, 1) - sh(tm, nu, 1) - tn          # plaquette with lower corner m
+        want = 0.25 * (np.sin(P) + np.sin(sh(P, mu, -1)) + np.sin(sh(sh(P, mu, -1), nu, -1))
+                       + np.sin(sh(P, nu, -1)))
+        got = F[..., k, :, :]
+        assert np.abs(np.diagonal(got, axis1=-2, axis2=-1) - want).max() < 1e-13
+        off = got - np.einsum("...c,cd->...cd", np.diagonal(got, axis1=-2, axis2=-1), np.eye(3))
+        assert np.abs(off).max() < 1e-15
+
+
+def test_field_strength_constant_field_and_clover_eigenvalues():
+    """A constant field B in the (1,2) plane only (U_x(n) = exp(-i B y), the
+    y extent a multiple of 2 pi / B): F_12 = sin(B), the other planes vanish,
+    and C = -(c_SW/2) sigma_12 sin B = (c_SW/2) sin B (pauli_0 (x) pauli_3)
+    multiplies spins 1, 3 by +(c_SW/2) sin B and spins 2, 4 by its negative."""
+    dims = (2, 6, 2, 2)
+    B = 2 * np.pi / 6
+    nx, ny, nz, nt = dims
+    y = np.arange(ny)[None, None, :, None]
+    U = np.zeros((nt, nz, ny, nx, 4, 1, 1), complex)
+    U[..., :, 0, 0] = 1.0
+    U[..., 0, 0, 0] = np.exp(-1j * B * y) * np.ones((nt, nz, ny, nx))
+    F = O.field_strength(U)
+    assert np.abs(F[..., 0, 0, 0] - np.sin(B)).max() < 1e-14
+    assert np.abs(F[..., 1:, :, :]).max() < 1e-14
+    csw = 1.7
+    psi = I.source(dims, 1, 3, seed=42)
+    Cpsi = O.clover(F, csw, psi)
+    lam = 0.5 * csw * np.sin(B)
+    sign = np.array([1, -1, 1, -1])[None, None, None, None, None, :, None]
+    assert np.abs(Cpsi - lam * sign * psi).max() < 1e-14
+
+
+def test_field_strength_vanishes_for_pure_gauge():
+    """U_mu(n) = g(n) g(n+mu)^dag has every closed loop equal to 1, so F = 0."""
+    dims = (4, 2, 3, 4)
+    g = I.gauge_transform(dims, 3, seed=43)
+    U = _transform_links(I.unit_gauge_field(dims, 3), g)
+    assert np.abs(O.field_strength(U)).max() < 1e-13
+
+
+def test_field_strength_gauge_covariant_hermitian_and_phase_blind():
+    dims = (4, 2, 4, 3)
+    U = I.gauge_field(dims, 3, 0.6, seed=44)
+    g = I.gauge_transform(dims, 3, seed=45)
+    F = O.field_strength(U)
+    Fg = O.field_strength(_transform_links(U, g))
+    want = np.einsum("...ab,...kbc,...dc->...kad", g, F, np.conj(g))
+    assert np.abs(Fg - want).max() < 1e-13
+    assert np.abs(F - np.conj(np.swapaxes(F, -1, -2))).max() < 1e-15
+    assert np.abs(O.field_strength(O.phase_links(U, (-1, 1, -1, -1))) - F).max() < 1e-15
+    assert np.abs(F).max() > 0.05          # not trivially zero
+
+
+@pytest.mark.parametrize("kind", [O.WILSON, O.BRILLOUIN])
+def test_clover_operator_dense_hermiticity_and_gamma5(kind):
+    """On a 2^4 lattice as dense matrices: C is hermitian and commutes with
+    gamma5, so (D + C) stays gamma5-hermitian and its oracle dagger is the
+    conjugate transpose; C vanishes on the free field."""
+    dims, nc = (2, 2, 2, 2), 2
+    U = I.gauge_field(dims, nc, 0.7, seed=46)
+    op = O.Operator(kind, U, (1, 1, 1, -1), 0.1, csw=1.3)
+    F = op.F
+    n = 16 * nc * 4
+    basis = np.eye(n, dtype=complex).reshape((n,) + (2, 2, 2, 2, nc, 4))
+    basis = np.moveaxis(basis, 0, -1)                     # nv = n unit vectors
+    Cm = O.clover(F, 1.3, basis).reshape(n, n)
+    assert np.abs(Cm - Cm.conj().T).max() < 1e-14
+    g5 = np.kron(np.eye(16 * nc), np.diag([1, 1, -1, -1]))
+    assert np.abs(g5 @ Cm - Cm @ g5).max() < 1e-14
+    Dm = op.apply(basis).reshape(n, n)
+    Dd = op.apply_dagger(basis).reshape(n, n)
+    assert np.abs(Dd - Dm.conj().T).max() < 1e-13
+    D0 = O.Operator(kind, U, (1, 1, 1, -1), 0.1).apply(basis).reshape(n, n)
+    assert np.abs(Dm - D0 - Cm).max() < 1e-13
+    assert np.abs(O.field_strength(I.unit_gauge_field(dims, nc))).max() == 0
+
+
+def test_clover_sites_match_full_apply():
+    dims = (4, 2, 2, 4)
+    U = I.gauge_field(dims, 3, 0.5, seed=47)
+    psi = I.source(dims, 3, 2, seed=48)
+    op = O.Operator(O.WILSON, U, (1, 1, 1, -1), -0.3, csw=1.0)
+    full = op.apply(psi).reshape((-1, 3, 4, 2))
+    fulld = op.apply_dagger(psi).reshape((-1, 3, 4, 2))
+    sites = [0, 5, 17, 63]
+    assert np.abs(op.apply_sites(psi, sites) - full[sites]).max() < 1e-13
+    assert np.abs(op.apply_sites(psi, sites, dagger=True) - fulld[sites]).max() < 1e-13
+
+
+def test_clover_flop_counts_app_e():
+    for form, nc, flops, poly, mults in _golden("app_e_clover_flops.txt"):
+        assert O.clover_flops_per_site(int(nc), int(mults)) == int(flops)
+        for n in (1, 2, 3, 4):
+            assert O.clover_flops_per_site(n, int(mults)) == eval(poly.replace("^", "**"), {"nc": n})
