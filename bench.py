@@ -56,6 +56,9 @@ def parse():
     p.add_argument("--solve", action="store_true", help="add the config-3 mixed-precision solver comparison")
     p.add_argument("--batch", action="store_true", help="add the config-4 batched-solve measurement")
     p.add_argument("--ncu", action="store_true", help="short run for profiler launch lists (no extras)")
+    p.add_argument("--csw", type=float, default=0.0,
+                   help="time D_W and D_B with the clover term of this c_SW (0: the plain operators)")
+    p.add_argument("--no-clover", action="store_true", help="skip the separate clover-term measurement")
     p.add_argument("--ops", default="wilson,brillouin,staggered",
                    help="profiling only: subset of operators to create and time")
     p.add_argument("--fixed", default=None,
@@ -74,13 +77,14 @@ def peaks():
         return dict(hbm=6800.0, sm_max=2070.0, source="fallback")
 
 
-def alg_bytes_per_site(kind, nc, nv, eb=4):
+def alg_bytes_per_site(kind, nc, nv, eb=4, clover=False):
     """Compulsory bytes per site and apply: spinor in + out once, links once
-    (Brillouin: the 80 stored W links of this implementation)."""
+    (Brillouin: the 80 stored W links of this implementation), plus the four
+    N_c x N_c clover blocks per site when the clover term is applied."""
     spin = 1 if kind == 2 else 4
     vec = nc * spin * nv * 2 * eb
     links = (80 if kind == 1 else 4) * nc * nc * 2 * eb
-    return 2 * vec + links
+    return 2 * vec + links + (4 * nc * nc * 2 * eb if clover else 0)
 
 
 def ncu_traffic(op_name):
@@ -93,7 +97,8 @@ def ncu_traffic(op_name):
     try:
         text = open(prof).read()
         h = hashlib.sha256()
-        srcs = ("%s.cuh" % op_name,) + (("bril_dirs.h",) if op_name == "brillouin" else ()) + ("common.cuh",)
+        srcs = ("%s.cuh" % op_name,) + (("bril_dirs.h",) if op_name == "brillouin" else ()) + \
+            (("clover.cuh",) if op_name != "staggered" else ()) + ("common.cuh",)
         for f in srcs:
             h.update(open(os.path.join(csrc, f), "rb").read())
         fields = dict(l.split(":", 1) for l in text.splitlines() if ":" in l and not l.startswith(("#", " ", "|")))
@@ -308,8 +313,16 @@ def main():
         _, ops[k], xs[k], ys[k] = cand[best]
         cand[1 - best][1].close()
         launch[D.KIND_NAMES[k]] = ops[k].get_launch()
+    clov = {k: bool(args.csw) and k != D.STAGGERED for k in kinds}
+    for k in kinds:
+        if clov[k]:
+            ops[k].set_clover(args.csw, U)
+            if not args.fixed:
+                ops[k].autotune(MASS[k])
+                launch[D.KIND_NAMES[k]] = ops[k].get_launch()
     V = int(np.prod(DIMS))
-    flop = {k: D.flops_per_site(k, NC) * V * NV for k in kinds}
+    flop = {k: (D.flops_per_site(k, NC) + (D.clover_flops_per_site(NC) if clov[k] else 0)) * V * NV
+            for k in kinds}
     step_flop = sum(flop.values())
     stream = torch.cuda.current_stream()
 
@@ -351,7 +364,7 @@ def main():
     for i, k in enumerate(kinds):
         times = [evs[s][i].elapsed_time(evs[s][i + 1]) for s in range(K)]
         t_ms = statistics.mean(times)
-        gbytes = alg_bytes_per_site(k, NC, NV) * V / 1e9
+        gbytes = alg_bytes_per_site(k, NC, NV, clover=clov[k]) * V / 1e9
         per_op[D.KIND_NAMES[k]] = {
             "ms": t_ms, "gflops": flop[k] / (t_ms * 1e-3) / 1e9, "alg_GBps": gbytes / (t_ms * 1e-3),
             "hbm_frac": gbytes / (t_ms * 1e-3) / pk["hbm"],
@@ -381,9 +394,13 @@ def main():
                       "unit": "TFLOP/s", "frac": per_op["brillouin"]["alu_frac"], "traffic": ncu_traffic("brillouin")},
     }
 
+    cfg = config_dict()
+    if args.csw:
+        cfg["workload"] += ", clover term c_SW=%g on D_W and D_B" % args.csw
+        cfg["csw"] = args.csw
     line = {"metric": METRIC, "value": value, "unit": "Gflop/s", "n_gpus": world, "steps": K,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_dict(),
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
             "gpu_launches": K * len(kinds), "roofline": roof, "rooflines": rooflines, "per_op": per_op,
             "clocks": clk, "peaks_source": pk["source"], "launch_variants": launch, "layouts": layout_ms}
 
@@ -429,6 +446,9 @@ def main():
             sweep["nv=%d" % nv] = row
         line["nv_sweep"] = sweep
 
+    if not args.ncu and not args.no_clover and not args.csw:
+        line["clover"] = clover_measurement(D, U, ops, xs, ys, per_op, pk, fp32_peak, quick_ms)
+
     if args.solve:
         line["solve"] = solver_comparison(D, I, torch)
     if args.batch:
@@ -442,6 +462,34 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def clover_measurement(D, U, ops, xs, ys, per_op, pk, fp32_peak, quick_ms, csw=1.0):
+    """D_W + C and D_B + C (c_SW = 1, F from the same field) on the timed
+    workload, in the layout chosen for the plain operator and an autotuned
+    launch variant: time per apply, Gflop/s with the 64 N_c^2 clover flops of
+    App. E added, algorithmic bandwidth with the clover blocks added, and the
+    cost over the plain operator timed the same way."""
+    import numpy as np
+    V = int(np.prod(DIMS))
+    out = {"csw": csw}
+    for k in (D.WILSON, D.BRILLOUIN):
+        if k not in ops:
+            continue
+        op = D.DiracOp(k, U, NV, BC, D.F32, layout=ops[k].layout)
+        op.set_clover(csw, U)
+        op.autotune(MASS[k])
+        plain_ms = quick_ms(ops[k], xs[k], ys[k], MASS[k], reps=50)
+        ms = quick_ms(op, xs[k], ys[k], MASS[k], reps=50)
+        flop = (D.flops_per_site(k, NC) + D.clover_flops_per_site(NC)) * V * NV
+        gbytes = alg_bytes_per_site(k, NC, NV, clover=True) * V / 1e9
+        out[D.KIND_NAMES[k]] = {
+            "ms": ms, "plain_ms": plain_ms, "overhead": ms / plain_ms - 1.0,
+            "gflops": flop / (ms * 1e-3) / 1e9, "alg_GBps": gbytes / (ms * 1e-3),
+            "hbm_frac": gbytes / (ms * 1e-3) / pk["hbm"], "alu_frac": flop / (ms * 1e-3) / 1e12 / fp32_peak,
+            "launch": op.get_launch()}
+        op.close()
+    return out
 
 
 # FP32 CG on the normal equations of the light staggered operator sits at an

@@ -105,9 +105,32 @@ typedef struct dirac_op dirac_op;   /* opaque */
 int dirac_op_create(dirac_kind kind, const dirac_geom *geom, const void *U,
                     dirac_prec u_prec, void *stream, dirac_op **out);
 
-/* Replace the gauge field (same geometry); rebuilds W for Brillouin.
+/* Replace the gauge field (same geometry); rebuilds W for Brillouin and
+ * removes a clover term (dirac_op_set_clover builds it for the new field).
  * Synchronises `stream` before returning. */
 int dirac_op_update_links(dirac_op *op, const void *U, dirac_prec u_prec, void *stream);
+
+/* Clover term (Sec. 5): from now on dirac_apply, _dagger, _normal, the
+ * solvers and the batched solves apply D + C (Eqs. def_wils, def_bril) with
+ *   C(n) = -(c_SW / 2) sum_{mu<nu} sigma_mu,nu F_mu,nu(n),
+ *   sigma_mu,nu = (i/2) [gamma_mu, gamma_nu],
+ *   F_mu,nu(n) = (Q_mu,nu(n) - Q_mu,nu(n)^dag) / (8i),
+ * Q_mu,nu(n) the sum of the four plaquettes of the (mu,nu) plane with a corner
+ * at n, each traversed mu-step first, then nu-step (the clover-leaf field
+ * strength, which the paper uses without writing it out; no trace is
+ * subtracted).  V is the gauge field F is built from (device pointer, same
+ * layout and precisions as U in dirac_op_create; the paper builds it from a
+ * smeared field, and U itself may be passed).  Boundary phases do not enter
+ * (closed loops).  C is site diagonal and commutes with gamma5, so the
+ * dagger is gamma5 (D + C) gamma5 = D^dag + C.  The operator keeps C in its
+ * link precision as two 2N_c x 2N_c blocks per site (FP64 arithmetic for
+ * FP64 operators, FP32 otherwise); applying it adds 64 N_c^2 flops per site
+ * and RHS (App. E) and 4 N_c^2 link-precision complex numbers per site of
+ * traffic.  csw = 0 removes the term (V may then be NULL).  Wilson and
+ * Brillouin only (DIRAC_ERR_INVALID_ARG for staggered); dirac_op_update_links
+ * removes it, and dirac_force_wilson refuses an operator that carries it.
+ * Synchronises `stream` before returning. */
+int dirac_op_set_clover(dirac_op *op, double csw, const void *V, dirac_prec v_prec, void *stream);
 
 /* Copy the operator's W links W_s(n) (Brillouin only) into the device
  * buffer w_out (w_bytes long, not overlapping the operator), layout
@@ -124,8 +147,9 @@ int dirac_op_copy_w(const dirac_op *op, void *w_out, void *stream);
 void dirac_op_destroy(dirac_op *op);
 
 /* psi_out = D psi_in with bare mass m0 (Wilson Eq. app_wils, Brillouin
- * Eq. app_bril, staggered Eq. def_stag).  psi_in and psi_out are vectors of
- * the operator's kind and precision and must not overlap. */
+ * Eq. app_bril, staggered Eq. def_stag; plus the clover term when one is set,
+ * dirac_op_set_clover).  psi_in and psi_out are vectors of the operator's
+ * kind and precision and must not overlap. */
 int dirac_apply(const dirac_op *op, const void *psi_in, void *psi_out, double m0, void *stream);
 
 /* psi_out = D^dag psi_in: gamma5 D gamma5 for Wilson and Brillouin,
@@ -288,7 +312,8 @@ int dirac_solve_batched(int nsolves, dirac_op *const *ops, const void *const *b,
 
 /* ------------------------------------------------------------ fermion force
  * Derivative of S = sum_v Re phi_v^dag (D_W^dag D_W)^-1 phi_v with respect to
- * the links (the paper has no force; derived from Eq. app_wils).  Inputs:
+ * the links (the paper has no force; derived from Eq. app_wils, so an
+ * operator with a clover term is refused).  Inputs:
  * psi = (D^dag D)^-1 phi and chi = D psi, Wilson-type vectors of op (F64 or
  * F32).  Output: [site][mu][a][b] complex in op precision.
  *   mode DIRAC_FORCE_TA:   F_mu(n) = P_TA(U B - C U^dag), traceless
@@ -307,6 +332,9 @@ const char *dirac_error_string(int code);
 /* Flops per site per RHS (App. E): Wilson 128Nc^2+72Nc, Brillouin
  * 2560Nc^2+2376Nc, staggered 64Nc^2+2Nc; -1 for an invalid kind. */
 long dirac_flops_per_site(dirac_kind kind, int nc);
+/* Flops per site per RHS of the clover term as App. E counts it for the
+ * two-multiplication form: 64Nc^2 (576 for SU(3)). */
+long dirac_clover_flops_per_site(int nc);
 /* Compile-time library version (major*10000 + minor*100 + patch). */
 int dirac_version(void);
 

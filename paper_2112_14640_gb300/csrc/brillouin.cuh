@@ -7,7 +7,9 @@
 // order q, with the scale rho_k s_lead and the per-site layout of bril_dirs.h.  The derivative
 // carries every axis the offset moves along (sum_mu s_mu gamma_mu), the
 // reading of Eq. (def_ider).  sgn = +1 gives D_B, sgn = -1 gives
-// D_B^dag = gamma5 D_B gamma5 (the derivative part flips sign).
+// D_B^dag = gamma5 D_B gamma5 (the derivative part flips sign).  A clover
+// term, when the operator carries one, is added site by site at the end
+// (clover.cuh; Eq. def_bril).
 //
 // With the stored W~ = rho_k s_lead W_s every offset contributes
 //   sgn * W~ [ sum_{mu in M} e_mu gamma_mu psi(n+s) + d psi(n+s) ],
@@ -23,6 +25,7 @@
 // right-hand sides.
 #pragma once
 #include "bril_dirs.h"
+#include "clover.cuh"
 #include "internal.h"
 
 namespace dgb {
@@ -169,7 +172,7 @@ __device__ __forceinline__ void groups_from(const Ctx<NC, VR, E, EL, LAYOUT> &C,
 template <int NC, int VR, typename E, int MINB, int LAYOUT, typename EL>
 __global__ void __launch_bounds__(stencil_max_threads(MINB), (MINB > 1 ? 1 : 0))
     brillouin_kernel(const EL *__restrict__ W, const E *__restrict__ in, E *__restrict__ out, Lat g,
-                     typename Acc<E>::T centre, typename Acc<E>::T sgn) {
+                     typename Acc<E>::T centre, typename Acc<E>::T sgn, const EL *__restrict__ clov) {
     using A = typename Acc<E>::T;
     using L = Layout<LAYOUT>;
     const int nchunk = g.nv / VR;
@@ -213,22 +216,8 @@ __global__ void __launch_bounds__(stencil_max_threads(MINB), (MINB > 1 ? 1 : 0))
     int q = 0;
     bril::groups_from<1>(C, q, Wc, acc);
 
-    const long long cs = L::cs_stride(g);
     const long long base = 2 * (L::vec(g, n, NC * 4, 0) + (long long)j * VR);
-#pragma unroll
-    for (int a = 0; a < NC; ++a)
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            cx<A> p[VR], o[VR];
-            const long long off = base + 2LL * (a * 4 + s) * cs;
-            load_cx<E, VR, A>(in + off, p);
-#pragma unroll
-            for (int v = 0; v < VR; ++v) {
-                o[v] = cx<A>{centre * p[v].re, centre * p[v].im};
-                rmac(o[v], sgn, acc[a][s][v]);
-            }
-            store_cx<E, VR, A>(out + off, o);
-        }
+    write_site<-1, NC, VR, LAYOUT, E, A, EL>(in, out, clov, g, n, base, centre, sgn, acc);
 }
 
 template <typename E, int LAYOUT, typename EL>
@@ -247,7 +236,8 @@ int launch_brillouin_v(const dirac_op *op, const void *in, void *out, double m0,
                 // m0 - lambda_0 / 2 = m0 + 240/128
                 {
                 brillouin_kernel<NC, VR, E, MINB, LAYOUT, EL><<<grid_for(threads, block), block, 0, s>>>(
-                    (const EL *)op->w, (const E *)in, (E *)out, op->lat, (A)(m0 + 240.0 / 128.0), (A)sgn);
+                    (const EL *)op->w, (const E *)in, (E *)out, op->lat, (A)(m0 + 240.0 / 128.0), (A)sgn,
+                    (const EL *)op->clover);
                 return launch_check("brillouin_kernel");
                 }
             }

@@ -4,6 +4,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <cmath>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -86,6 +87,7 @@ static void op_free(dirac_op *op) {
         for (int k = 0; k < 2; ++k) op_free(op->inner[i][k]);
     cudaFree(op->links);
     cudaFree(op->w);
+    cudaFree(op->clover);
     cudaFree(op->scratch);
     cudaFree(op->stage_in);
     cudaFree(op->stage_out);
@@ -125,7 +127,7 @@ static int alloc(void **p, size_t bytes) {
 // Process-wide memory of autotuned launch variants, keyed by what decides
 // the kernel's behaviour.
 // (kind, layout, precision, link storage, N_c, N_v, volume)
-using TuneKey = std::tuple<int, int, int, int, int, int, long long>;
+using TuneKey = std::tuple<int, int, int, int, int, int, long long, int>;
 struct TuneVal {
     int vr, minb, block;
 };
@@ -133,7 +135,8 @@ static std::mutex g_tune_mu;
 static std::map<TuneKey, TuneVal> g_tune;
 
 static TuneKey tune_key(const dirac_op *op) {
-    return TuneKey{(int)op->kind, op->geom.layout, (int)op->prec, (int)link_prec(op), op->nc, op->nv, op->V};
+    return TuneKey{(int)op->kind, op->geom.layout, (int)op->prec, (int)link_prec(op), op->nc, op->nv, op->V,
+                   op->clover != nullptr};
 }
 
 static void remember_tuning(const dirac_op *op) {
@@ -198,7 +201,11 @@ int op_inner(const dirac_op *op, dirac_prec p, int link_storage, dirac_op **out,
         dirac_op *tw = nullptr;
         int rc = op_alloc(op->kind, &g, &tw);
         if (rc) return rc;
-        rc = launch_convert_links(op, tw, s);
+        if (op->clover) {
+            tw->csw = op->csw;
+            rc = alloc(&tw->clover, tw->link_bytes);
+        }
+        if (!rc) rc = launch_convert_links(op, tw, s);
         if (rc) {
             op_free(tw);
             return rc;
@@ -219,18 +226,26 @@ static int check_vec(const void *p) {
     return DIRAC_OK;
 }
 
+// twins built from older links or another clover term are stale
+static void drop_twins(dirac_op *op) {
+    for (int i = 0; i < 4; ++i)
+        for (int k = 0; k < 2; ++k) {
+            op_destroy(op->inner[i][k]);
+            op->inner[i][k] = nullptr;
+        }
+}
+
 static int load_links(dirac_op *op, const void *U, dirac_prec u_prec, cudaStream_t s) {
     if (!U) return DIRAC_ERR_INVALID_ARG;
     if (u_prec != DIRAC_F64 && u_prec != DIRAC_F32) return DIRAC_ERR_UNSUPPORTED_PREC;
     int rc = launch_phase_links(op, U, u_prec, s);
     if (!rc && op->kind == DIRAC_BRILLOUIN) rc = launch_build_w(op, U, u_prec, s);
     if (!rc) rc = cuda_check(cudaStreamSynchronize(s), "link setup");
-    // twins built from older links are stale now
-    for (int i = 0; i < 4; ++i)
-        for (int k = 0; k < 2; ++k) {
-            op_destroy(op->inner[i][k]);
-            op->inner[i][k] = nullptr;
-        }
+    // a clover term belongs to the old field
+    cudaFree(op->clover);
+    op->clover = nullptr;
+    op->csw = 0.0;
+    drop_twins(op);
     return rc;
 }
 
@@ -259,6 +274,36 @@ int dirac_op_create(dirac_kind kind, const dirac_geom *geom, const void *U, dira
 int dirac_op_update_links(dirac_op *op, const void *U, dirac_prec u_prec, void *stream) {
     if (!op) return DIRAC_ERR_INVALID_ARG;
     return load_links(op, U, u_prec, (cudaStream_t)stream);
+}
+
+int dirac_op_set_clover(dirac_op *op, double csw, const void *V, dirac_prec v_prec, void *stream) {
+    if (!op || op->kind == DIRAC_STAGGERED || !std::isfinite(csw)) return DIRAC_ERR_INVALID_ARG;
+    if (csw != 0.0) {
+        if (!V) return DIRAC_ERR_INVALID_ARG;
+        if (v_prec != DIRAC_F64 && v_prec != DIRAC_F32) return DIRAC_ERR_UNSUPPORTED_PREC;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    drop_twins(op);
+    if (csw == 0.0) {
+        int rc = op->clover ? cuda_check(cudaStreamSynchronize(s), "clover removal") : DIRAC_OK;
+        cudaFree(op->clover);
+        op->clover = nullptr;
+        op->csw = 0.0;
+        recall_tuning(op);
+        return rc;
+    }
+    int rc = op->clover ? DIRAC_OK : alloc(&op->clover, op->link_bytes);
+    if (rc) return rc;
+    op->csw = csw;
+    rc = launch_build_clover(op, V, v_prec, s);
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(s), "clover setup");
+    if (rc) {
+        cudaFree(op->clover);
+        op->clover = nullptr;
+        op->csw = 0.0;
+    }
+    recall_tuning(op);
+    return rc;
 }
 
 int dirac_op_copy_w(const dirac_op *op, void *w_out, void *stream) {
@@ -513,6 +558,8 @@ const char *dirac_error_string(int code) {
     }
     return "unknown code";
 }
+
+long dirac_clover_flops_per_site(int nc) { return 64L * nc * nc; }
 
 long dirac_flops_per_site(dirac_kind kind, int nc) {
     const long n = nc;

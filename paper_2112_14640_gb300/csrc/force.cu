@@ -130,6 +130,7 @@ extern "C" int dirac_force_wilson(const dirac_op *op, const void *psi, const voi
                                   void *stream) {
     if (!op || !psi || !chi || !force_out) return DIRAC_ERR_INVALID_ARG;
     if (op->kind != DIRAC_WILSON || (mode != 0 && mode != 1)) return DIRAC_ERR_INVALID_ARG;
+    if (op->clover) return DIRAC_ERR_INVALID_ARG;   // derived for D_W without the clover term
     if (((uintptr_t)psi & 15) || ((uintptr_t)chi & 15)) return DIRAC_ERR_ALIGNMENT;
     if (op->prec != DIRAC_F64 && op->prec != DIRAC_F32) return DIRAC_ERR_UNSUPPORTED_PREC;
     cudaStream_t s = (cudaStream_t)stream;

@@ -24,6 +24,8 @@ struct dirac_op {
     size_t w_bytes;        // bytes of the 80 W links per site (Brillouin)
     void *links;           // [V][4][nc][nc], boundary phases folded in
     void *w;               // [V][80][nc][nc] (Brillouin only)
+    void *clover;          // clover term (clover.cuh), links' shape and layout; null when c_SW = 0
+    double csw;            // c_SW folded into `clover`
     void *scratch;         // one vector: intermediate of D^dag D
     void *stage_in;        // host-apply staging buffers (lazy)
     void *stage_out;
@@ -184,6 +186,8 @@ int launch_brillouin(const dirac_op *op, const void *in, void *out, double m0, i
 // link preparation
 int launch_phase_links(dirac_op *op, const void *U, dirac_prec u_prec, cudaStream_t s);
 int launch_build_w(dirac_op *op, const void *U, dirac_prec u_prec, cudaStream_t s);
+// clover term of c_SW = op->csw from gauge field V into op->clover (allocated)
+int launch_build_clover(dirac_op *op, const void *V, dirac_prec v_prec, cudaStream_t s);
 // the stored W~ (order and scale of bril_dirs.h) back to W_s in the public order
 int launch_unpack_w(const dirac_op *op, void *out, cudaStream_t s);
 int launch_convert_links(const dirac_op *src, dirac_op *dst, cudaStream_t s);

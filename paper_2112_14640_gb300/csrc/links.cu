@@ -8,7 +8,12 @@
 //      W_s(n) = (1/k) sum_{mu: s_mu != 0} W_{s - s_mu mu}(n) V_{s_mu mu}(n + s - s_mu mu),
 //    evaluated level by level (k = 1..4) in shared memory, one thread block
 //    per site, in FP64 for FP64 operators and FP32 otherwise; the result is
-//    stored in the link precision.
+//    stored in the link precision;
+//  * build_clover: the clover term of Eq. (def_clov) in the block form of
+//    clover.cuh, from the clover-leaf field strength
+//      F_mu,nu(n) = (Q_mu,nu(n) - Q_mu,nu(n)^dag) / (8i),
+//    Q the sum of the four plaquettes of the (mu,nu) plane with a corner at
+//    n, all traversed the same way (mu-step first, then nu-step).
 #include "bril_dirs.h"
 #include "internal.h"
 
@@ -200,6 +205,143 @@ int launch_build_w(dirac_op *op, const void *U, dirac_prec u_prec, cudaStream_t 
     });
 }
 
+// ------------------------------------------------------------ clover term
+
+template <int NC, typename AB>
+__device__ __forceinline__ void mat_mul(const cx<AB> (&X)[NC][NC], const cx<AB> (&Y)[NC][NC], cx<AB> (&Z)[NC][NC]) {
+#pragma unroll
+    for (int a = 0; a < NC; ++a)
+#pragma unroll
+        for (int b = 0; b < NC; ++b) {
+            cx<AB> t = {0, 0};
+#pragma unroll
+            for (int q = 0; q < NC; ++q) cmac(t, X[a][q], Y[q][b]);
+            Z[a][b] = t;
+        }
+}
+
+__device__ __forceinline__ void step(int (&x)[4], const int ext[4], int mu, int sign) {
+    x[mu] = sign > 0 ? (x[mu] + 1 == ext[mu] ? 0 : x[mu] + 1) : (x[mu] == 0 ? ext[mu] - 1 : x[mu] - 1);
+}
+
+// F_mu,nu at site x0 from the four leaves (+mu,+nu), (+nu,-mu), (-mu,-nu),
+// (-nu,+mu); the leaf (a, b) is V_a(n) V_b(n+a) V_-a(n+a+b) V_-b(n+b).
+template <int NC, typename UE, typename AB>
+__device__ void field_strength(const UE *__restrict__ U, const Lat &g, const Phases &ph, const int x0[4], int mu,
+                               int nu, cx<AB> (&F)[NC][NC]) {
+    const int ext[4] = {g.nx, g.ny, g.nz, g.nt};
+    const int st[4][4] = {{mu, 1, nu, 1}, {nu, 1, mu, -1}, {mu, -1, nu, -1}, {nu, -1, mu, 1}};
+    cx<AB> Q[NC][NC];
+#pragma unroll
+    for (int a = 0; a < NC; ++a)
+#pragma unroll
+        for (int b = 0; b < NC; ++b) Q[a][b] = cx<AB>{0, 0};
+    for (int l = 0; l < 4; ++l) {
+        const int am = st[l][0], as = st[l][1], bm = st[l][2], bs = st[l][3];
+        int xa[4] = {x0[0], x0[1], x0[2], x0[3]};
+        step(xa, ext, am, as);
+        int xab[4] = {xa[0], xa[1], xa[2], xa[3]};
+        step(xab, ext, bm, bs);
+        int xb[4] = {x0[0], x0[1], x0[2], x0[3]};
+        step(xb, ext, bm, bs);
+        cx<AB> P[NC][NC], L[NC][NC], T[NC][NC];
+        signed_link<NC, UE, AB>(U, g, ph, x0, am, as, P);
+        signed_link<NC, UE, AB>(U, g, ph, xa, bm, bs, L);
+        mat_mul<NC, AB>(P, L, T);
+        signed_link<NC, UE, AB>(U, g, ph, xab, am, -as, L);
+        mat_mul<NC, AB>(T, L, P);
+        signed_link<NC, UE, AB>(U, g, ph, xb, bm, -bs, L);
+        mat_mul<NC, AB>(P, L, T);
+#pragma unroll
+        for (int a = 0; a < NC; ++a)
+#pragma unroll
+            for (int b = 0; b < NC; ++b) Q[a][b] = Q[a][b] + T[a][b];
+    }
+    // (Q - Q^dag) / (8i) = -i (Q - Q^dag) / 8
+#pragma unroll
+    for (int a = 0; a < NC; ++a)
+#pragma unroll
+        for (int b = 0; b < NC; ++b) {
+            const cx<AB> d = {Q[a][b].re - Q[b][a].re, Q[a][b].im + Q[b][a].im};
+            F[a][b] = cx<AB>{d.im / (AB)8, -d.re / (AB)8};
+        }
+}
+
+// One thread per (site, block k = 2 chi + w): block A (w = 0) of chirality chi
+// needs the planes (1,2), (3,4); block B (w = 1) the planes (1,4), (2,3),
+// (1,3), (2,4) (clover.cuh).  FP64 arithmetic for FP64 storage, FP32 otherwise.
+template <int NC, typename UE, typename E>
+__global__ void __launch_bounds__(128) build_clover_kernel(const UE *__restrict__ U, E *__restrict__ out, Lat g,
+                                                           Phases ph, double csw, int layout) {
+    using AB = std::conditional_t<sizeof(E) == 8, double, float>;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= g.V * 4) return;
+    const long long n = tid / 4;
+    const int k = (int)(tid % 4), chi = k >> 1, w = k & 1;
+    const AB e = chi == 0 ? (AB)1 : (AB)-1;
+    const Coord c = site_coords(g, n);
+    const int x0[4] = {c.x, c.y, c.z, c.t};
+    // (plane, complex coefficient) pairs of the block, planes as (mu, nu) 0-based
+    int planes[4][2];
+    cx<AB> coef[4];
+    int np;
+    if (w == 0) {   // -F_12 + e F_34
+        np = 2;
+        planes[0][0] = 0, planes[0][1] = 1, coef[0] = cx<AB>{-1, 0};
+        planes[1][0] = 2, planes[1][1] = 3, coef[1] = cx<AB>{e, 0};
+    } else {        // e F_14 - F_23 - i F_13 - i e F_24
+        np = 4;
+        planes[0][0] = 0, planes[0][1] = 3, coef[0] = cx<AB>{e, 0};
+        planes[1][0] = 1, planes[1][1] = 2, coef[1] = cx<AB>{-1, 0};
+        planes[2][0] = 0, planes[2][1] = 2, coef[2] = cx<AB>{0, -1};
+        planes[3][0] = 1, planes[3][1] = 3, coef[3] = cx<AB>{0, -e};
+    }
+    cx<AB> acc[NC][NC];
+#pragma unroll
+    for (int a = 0; a < NC; ++a)
+#pragma unroll
+        for (int b = 0; b < NC; ++b) acc[a][b] = cx<AB>{0, 0};
+    for (int i = 0; i < np; ++i) {
+        cx<AB> F[NC][NC];
+        field_strength<NC, UE, AB>(U, g, ph, x0, planes[i][0], planes[i][1], F);
+#pragma unroll
+        for (int a = 0; a < NC; ++a)
+#pragma unroll
+            for (int b = 0; b < NC; ++b) cmac(acc[a][b], coef[i], F[a][b]);
+    }
+    const double f = -0.5 * csw;
+    const int per = NC * NC;
+#pragma unroll
+    for (int a = 0; a < NC; ++a)
+#pragma unroll
+        for (int b = 0; b < NC; ++b) {
+            const int el = a * NC + b;
+            // the links' layout: [site][k][a][b] or [k][a][b][site]
+            const long long o = layout == 0 ? tid * per + el : ((long long)k * per + el) * g.V + n;
+            out[2 * o] = from_acc<E, double>(f * (double)acc[a][b].re);
+            out[2 * o + 1] = from_acc<E, double>(f * (double)acc[a][b].im);
+        }
+}
+
+int launch_build_clover(dirac_op *op, const void *V, dirac_prec v_prec, cudaStream_t s) {
+    return dispatch_uprec(v_prec, [&](auto utag) {
+        using UE = std::remove_pointer_t<decltype(utag)>;
+        return dispatch_prec(link_prec(op), [&](auto tag) {
+            using E = std::remove_pointer_t<decltype(tag)>;
+            return dispatch_nc(op->nc, [&](auto ncc) {
+                constexpr int NC = decltype(ncc)::value;
+                const long long threads = op->V * 4;
+                // closed loops do not see the boundary phases: leave them out
+                Phases none;
+                for (int m = 0; m < 4; ++m) none.bc[m] = 1;
+                build_clover_kernel<NC, UE, E><<<grid_for(threads, 128), 128, 0, s>>>(
+                    (const UE *)V, (E *)op->clover, op->lat, none, op->csw, op->geom.layout);
+                return launch_check("build_clover_kernel");
+            });
+        });
+    });
+}
+
 template <typename S, typename D>
 __global__ void convert_scalars_kernel(const S *__restrict__ src, D *__restrict__ dst, long long count) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -225,6 +367,10 @@ int launch_convert_links(const dirac_op *src, dirac_op *dst, cudaStream_t s) {
         // same order, scale and layout, element by element
         n = src->V * 80 * src->nc * src->nc * 2;
         rc = convert_array(src->w, link_prec(src), dst->w, link_prec(dst), n, s);
+    }
+    if (!rc && src->clover) {
+        n = src->V * 4 * src->nc * src->nc * 2;
+        rc = convert_array(src->clover, link_prec(src), dst->clover, link_prec(dst), n, s);
     }
     return rc;
 }

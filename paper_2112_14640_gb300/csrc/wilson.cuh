@@ -13,6 +13,7 @@
 // neighbouring bytes.  Every thread accumulates its whole output in
 // registers and writes it once (the paper's write-once "site" accumulator).
 #pragma once
+#include "clover.cuh"
 #include "internal.h"
 
 namespace dgb {
@@ -111,10 +112,10 @@ __device__ __forceinline__ void wilson_dir(cx<A> (&acc)[NC][4][VR], const EL *__
                                  in + 2 * (L::vec(g, bw, NC * 4, 0) + (long long)j * VR), cs, sgn);
 }
 
-template <int NC, int VR, typename E, int MINB, int LAYOUT, typename EL>
+template <int NC, int VR, typename E, int MINB, int LAYOUT, typename EL, int CLOV>
 __global__ void __launch_bounds__(stencil_max_threads(MINB), (MINB > 1 ? 1 : 0)) wilson_kernel(const EL *__restrict__ U, const E *__restrict__ in,
                                                      E *__restrict__ out, Lat g, typename Acc<E>::T diag,
-                                                     typename Acc<E>::T sgn) {
+                                                     typename Acc<E>::T sgn, const EL *__restrict__ clov) {
     using A = typename Acc<E>::T;
     const int nchunk = g.nv / VR;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -138,22 +139,7 @@ __global__ void __launch_bounds__(stencil_max_threads(MINB), (MINB > 1 ? 1 : 0))
     wilson_dir<3, NC, VR, LAYOUT, E, A, EL>(acc, U, in, g, n, c, j, sgn);
 
     const long long base = 2 * (Layout<LAYOUT>::vec(g, n, NC * 4, 0) + (long long)j * VR);
-    const long long cs = Layout<LAYOUT>::cs_stride(g);
-    const A mhalf = (A)-0.5;
-#pragma unroll
-    for (int a = 0; a < NC; ++a)
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            cx<A> p[VR], o[VR];
-            const long long off = base + 2LL * (a * 4 + s) * cs;
-            load_cx<E, VR, A>(in + off, p);
-#pragma unroll
-            for (int v = 0; v < VR; ++v) {
-                o[v] = diag * p[v];
-                rmac(o[v], mhalf, acc[a][s][v]);
-            }
-            store_cx<E, VR, A>(out + off, o);
-        }
+    write_site<CLOV, NC, VR, LAYOUT, E, A, EL>(in, out, clov, g, n, base, diag, (A)-0.5, acc);
 }
 
 template <typename E, int LAYOUT, typename EL>
@@ -166,15 +152,17 @@ int launch_wilson_v(const dirac_op *op, const void *in, void *out, double m0, in
         return dispatch_vr(vr, [&](auto vrc) {
             constexpr int VR = decltype(vrc)::value;
             return dispatch_minb<NC>(minb, [&](auto mbc) {
-            constexpr int MINB = decltype(mbc)::value;
-            {
+                constexpr int MINB = decltype(mbc)::value;
                 const long long threads = op->lat.nsites * (op->nv / VR);
-                {
-                wilson_kernel<NC, VR, E, MINB, LAYOUT, EL><<<grid_for(threads, block), block, 0, s>>>(
-                    (const EL *)op->links, (const E *)in, (E *)out, op->lat, (A)(4.0 + m0), (A)sgn);
-                return launch_check("wilson_kernel");
-                }
-            }
+                // the clover term is a compile-time switch here (no cost to D_W without it)
+                auto go = [&](auto cl) {
+                    wilson_kernel<NC, VR, E, MINB, LAYOUT, EL, decltype(cl)::value>
+                        <<<grid_for(threads, block), block, 0, s>>>((const EL *)op->links, (const E *)in, (E *)out,
+                                                                   op->lat, (A)(4.0 + m0), (A)sgn,
+                                                                   (const EL *)op->clover);
+                    return launch_check("wilson_kernel");
+                };
+                return op->clover ? go(std::integral_constant<int, 1>{}) : go(std::integral_constant<int, 0>{});
             });
         });
     });

@@ -67,6 +67,7 @@ SIGNATURES = {
     "dirac_op_create": (_I, [_I, ctypes.POINTER(Geom), _P, _I, _P, ctypes.POINTER(_P)]),
     "dirac_op_update_links": (_I, [_P, _P, _I, _P]),
     "dirac_op_copy_w": (_I, [_P, _P, _P]),
+    "dirac_op_set_clover": (_I, [_P, _D, _P, _I, _P]),
     "dirac_op_destroy": (None, [_P]),
     "dirac_apply": (_I, [_P, _P, _P, _D, _P]),
     "dirac_apply_dagger": (_I, [_P, _P, _P, _D, _P]),
@@ -88,6 +89,7 @@ SIGNATURES = {
                                  ctypes.POINTER(_D), ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats), _P]),
     "dirac_error_string": (ctypes.c_char_p, [_I]),
     "dirac_flops_per_site": (ctypes.c_long, [_I, _I]),
+    "dirac_clover_flops_per_site": (ctypes.c_long, [_I]),
     "dirac_version": (_I, []),
 }
 
@@ -118,6 +120,10 @@ def error_string(code):
 
 def flops_per_site(kind, nc):
     return int(lib().dirac_flops_per_site(int(kind), int(nc)))
+
+
+def clover_flops_per_site(nc):
+    return int(lib().dirac_clover_flops_per_site(int(nc)))
 
 
 def _check(rc, what):
@@ -157,6 +163,7 @@ class DiracOp:
         g.nc, g.nv, g.prec, g.layout, g.link_storage = self.nc, self.nv, self.prec, self.layout, int(link_storage)
         g.bc[:] = self.bc
         self._geom = g
+        self.csw = 0.0
         h = ctypes.c_void_p()
         u_prec = F64 if U.dtype == torch.complex128 else F32
         _check(lib().dirac_op_create(self.kind, ctypes.byref(g), _ptr(U), u_prec, _stream(stream),
@@ -176,9 +183,28 @@ class DiracOp:
             pass
 
     def update_links(self, U, stream=None):
+        """New gauge field; a clover term set before is removed."""
         u_prec = F64 if U.dtype == torch.complex128 else F32
         _check(lib().dirac_op_update_links(self._h, _ptr(U.contiguous()), u_prec, _stream(stream)),
                "dirac_op_update_links")
+        self.csw = 0.0
+
+    def set_clover(self, csw, V=None, stream=None):
+        """Add the clover term of Eq. (def_clov) with coefficient csw, its field
+        strength built from the gauge field V (a CUDA tensor shaped like U);
+        csw = 0 removes it."""
+        if V is None:
+            if csw != 0.0:
+                raise ValueError("V is required for a non-zero c_SW")
+            ptr, v_prec = ctypes.c_void_p(), F64
+        else:
+            if not V.is_cuda or V.dtype not in (torch.complex128, torch.complex64):
+                raise ValueError("V must be a complex128 or complex64 CUDA tensor")
+            V = V.contiguous()
+            ptr, v_prec = _ptr(V), (F64 if V.dtype == torch.complex128 else F32)
+        _check(lib().dirac_op_set_clover(self._h, float(csw), ptr, v_prec, _stream(stream)),
+               "dirac_op_set_clover")
+        self.csw = float(csw)
 
     # ---------------------------------------------------------------- shapes
     @property

@@ -89,3 +89,21 @@ def test_null_handles_are_rejected(lib):
     assert lib.dirac_solve(None, p, p, 0.0, None, None, None) == -1
     assert lib.dirac_vec_bytes(None) == 0
     lib.dirac_op_destroy(None)
+
+
+def test_set_clover_validates_without_device(lib):
+    """A null operator is refused before any CUDA call."""
+    assert lib.dirac_op_set_clover(None, 1.0, None, D.F64, None) == -1
+    assert lib.dirac_op_set_clover(None, 0.0, None, D.F64, None) == -1
+
+
+def test_clover_flop_count_matches_app_e(lib):
+    """dirac_clover_flops_per_site against the two-multiplication count App. E
+    prints (tests/golden/app_e_clover_flops.txt)."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "app_e_clover_flops.txt")
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    (form, nc, flops, poly, mults), = [r for r in rows if r[0] == "two_products"]
+    assert D.clover_flops_per_site(int(nc)) == int(flops)
+    for n in (1, 2, 3, 4):
+        assert D.clover_flops_per_site(n) == eval(poly.replace("^", "**"), {"nc": n})
