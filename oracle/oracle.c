@@ -377,6 +377,88 @@ void orc_brillouin_sites(const int d[4], int nc, int nv, const cplx *Wsites, dou
         brillouin_site(d, nc, nv, Wsites + i * 81 * (long)nc * nc, m0, in, sites[i], out + i * per_site);
 }
 
+/* ------------------------------------------------- Laplace operators (Sec. 6, 7)
+ * The "embedded" Laplace operators A = -1/2 Lap + m^2/2, acting trivially in
+ * spin: on ns = 4 spin components per colour (Wilson-type vectors, the
+ * paper's wlap/blap) or ns = 1 (colour-only vectors, wsuv/bsuv, App. F).
+ *   Eq. (app_wlap): (A psi)(n) = (4 + m^2/2) psi(n)
+ *        - 1/2 sum_mu [ U_mu(n) psi(n+mu) + U_mu(n-mu)^dag psi(n-mu) ]
+ *   Eq. (app_blap): (A psi)(n) = (m^2/2 - lambda_0/2) psi(n)
+ *        - 1/2 sum_{s != 0} lambda_k W_s(n) psi(n+s)
+ * Vectors are [site][colour][spin][v] (ns = 4) or [site][colour][v] (ns = 1). */
+
+static void wlap_site(const int d[4], int nc, int ns, int nv, const cplx *U, double m,
+                      const cplx *in, long n, cplx *o) {
+    const long per_site = (long)nc * ns * nv;
+    const cplx *c0 = in + n * per_site;
+    for (long e = 0; e < per_site; ++e) o[e] = (4.0 + 0.5 * m * m) * c0[e];
+    cplx L[64];
+    for (int mu = 0; mu < 4; ++mu)
+        for (int sign = 1; sign >= -1; sign -= 2) {
+            long nb = hop(d, n, mu, sign);
+            signed_link(d, nc, U, n, mu, sign, L);
+            const cplx *pm = in + nb * per_site;
+            for (int c = 0; c < nc; ++c)
+                for (int sp = 0; sp < ns; ++sp)
+                    for (int v = 0; v < nv; ++v) {
+                        cplx acc = 0;
+                        for (int c2 = 0; c2 < nc; ++c2) acc += L[c * nc + c2] * pm[((long)c2 * ns + sp) * nv + v];
+                        o[((long)c * ns + sp) * nv + v] -= 0.5 * acc;
+                    }
+        }
+}
+
+void orc_wlap(const int d[4], int nc, int ns, int nv, const cplx *U, double m, const cplx *in, cplx *out) {
+    const long V = vol4(d);
+#pragma omp parallel for
+    for (long n = 0; n < V; ++n) wlap_site(d, nc, ns, nv, U, m, in, n, out + n * (long)nc * ns * nv);
+}
+
+void orc_wlap_sites(const int d[4], int nc, int ns, int nv, const cplx *U, double m, const cplx *in,
+                    const long *sites, long nsites, cplx *out) {
+#pragma omp parallel for
+    for (long i = 0; i < nsites; ++i) wlap_site(d, nc, ns, nv, U, m, in, sites[i], out + i * (long)nc * ns * nv);
+}
+
+/* one output site n; Wn = the 81 W_s(n) of that site (centre = identity) */
+static void blap_site(const int d[4], int nc, int ns, int nv, const cplx *Wn, double m,
+                      const cplx *in, long n, cplx *o) {
+    const long per_site = (long)nc * ns * nv;
+    const long per = (long)nc * nc;
+    for (long e = 0; e < per_site; ++e) o[e] = 0;
+    for (int dir = 0; dir < 81; ++dir) {
+        int s[4];
+        orc_dir_offset(dir, s);
+        int k = abs(s[0]) + abs(s[1]) + abs(s[2]) + abs(s[3]);
+        double f = (k == 0) ? 0.5 * m * m - 0.5 * LAM[0] : -0.5 * LAM[k];
+        long nb = shifted(d, n, s);
+        const cplx *w = Wn + dir * per;
+        const cplx *pm = in + nb * per_site;
+        for (int c = 0; c < nc; ++c)
+            for (int sp = 0; sp < ns; ++sp)
+                for (int v = 0; v < nv; ++v) {
+                    cplx acc = 0;
+                    for (int c2 = 0; c2 < nc; ++c2) acc += w[c * nc + c2] * pm[((long)c2 * ns + sp) * nv + v];
+                    o[((long)c * ns + sp) * nv + v] += f * acc;
+                }
+    }
+}
+
+void orc_blap(const int d[4], int nc, int ns, int nv, const cplx *W, double m, const cplx *in, cplx *out) {
+    const long V = vol4(d);
+    const long per_site = (long)nc * ns * nv;
+#pragma omp parallel for
+    for (long n = 0; n < V; ++n) blap_site(d, nc, ns, nv, W + n * 81 * (long)nc * nc, m, in, n, out + n * per_site);
+}
+
+void orc_blap_sites(const int d[4], int nc, int ns, int nv, const cplx *Wsites, double m, const cplx *in,
+                    const long *sites, long nsites, cplx *out) {
+    const long per_site = (long)nc * ns * nv;
+#pragma omp parallel for
+    for (long i = 0; i < nsites; ++i)
+        blap_site(d, nc, ns, nv, Wsites + i * 81 * (long)nc * nc, m, in, sites[i], out + i * per_site);
+}
+
 /* ------------------------------------- clover-leaf field strength (Sec. 5)
  * Eq. (def_clov) needs the hermitian "clover-leaf" field strength F_mu,nu(n)
  * but the paper does not write it out.  Reading: Q_mu,nu(n) is the sum of the

@@ -31,7 +31,21 @@ from . import build as _build
 _lib = None
 
 WILSON, BRILLOUIN, STAGGERED = 0, 1, 2
-KIND_NAMES = {WILSON: "wilson", BRILLOUIN: "brillouin", STAGGERED: "staggered"}
+# Laplace operators A = -1/2 Lap + m^2/2 (Secs. 6, 7; App. F wlap, blap, wsuv, bsuv):
+# standard / Brillouin Laplacian on Wilson-type (4 spins) or colour-only vectors
+WLAP, BLAP, WSUV, BSUV = 3, 4, 5, 6
+KIND_NAMES = {WILSON: "wilson", BRILLOUIN: "brillouin", STAGGERED: "staggered",
+              WLAP: "wlap", BLAP: "blap", WSUV: "wsuv", BSUV: "bsuv"}
+LAPLACE = (WLAP, BLAP, WSUV, BSUV)
+
+
+def spins(kind):
+    """Spin components per colour of the kind's vectors."""
+    return 1 if kind in (STAGGERED, WSUV, BSUV) else 4
+
+
+def uses_w(kind):
+    return kind in (BRILLOUIN, BLAP, BSUV)
 
 
 def lib():
@@ -55,7 +69,12 @@ def lib():
         _lib.orc_brillouin_sites.argtypes = [I4, I, I, P, D, P, P, ctypes.c_long, P]
         _lib.orc_build_w_sites.argtypes = [I4, I, P, P, ctypes.c_long, P]
         _lib.orc_field_strength.argtypes = [I4, I, P, P]
-        for f in (_lib.orc_field_strength, _lib.orc_phase_links, _lib.orc_wilson, _lib.orc_staggered, _lib.orc_brillouin,
+        _lib.orc_wlap.argtypes = [I4, I, I, I, P, D, P, P]
+        _lib.orc_blap.argtypes = [I4, I, I, I, P, D, P, P]
+        _lib.orc_wlap_sites.argtypes = [I4, I, I, I, P, D, P, P, ctypes.c_long, P]
+        _lib.orc_blap_sites.argtypes = [I4, I, I, I, P, D, P, P, ctypes.c_long, P]
+        for f in (_lib.orc_wlap, _lib.orc_blap, _lib.orc_wlap_sites, _lib.orc_blap_sites,
+                  _lib.orc_field_strength, _lib.orc_phase_links, _lib.orc_wilson, _lib.orc_staggered, _lib.orc_brillouin,
                   _lib.orc_build_w, _lib.orc_gamma5, _lib.orc_epsilon, _lib.orc_gamma,
                   _lib.orc_wilson_sites, _lib.orc_staggered_sites, _lib.orc_brillouin_sites,
                   _lib.orc_build_w_sites):
@@ -130,6 +149,18 @@ def brillouin(W, m0, psi):
     return _stencil(lib().orc_brillouin, (nx, ny, nz, nt), nc, psi.shape[-1], W, m0, psi)
 
 
+def laplace(kind, field, m, v):
+    """A v for the Laplace kinds, Eq. (app_wlap) (field = phased links) or
+    Eq. (app_blap) (field = W from ``build_w``)."""
+    nt, nz, ny, nx = v.shape[:4]
+    nc, nv = v.shape[4], v.shape[-1]
+    v = np.ascontiguousarray(v, np.complex128)
+    out = np.empty_like(v)
+    fn = lib().orc_blap if uses_w(kind) else lib().orc_wlap
+    fn(_i4((nx, ny, nz, nt)), nc, spins(kind), nv, _p(np.ascontiguousarray(field)), float(m), _p(v), _p(out))
+    return out
+
+
 def _sites_arr(sites):
     a = np.ascontiguousarray(np.asarray(sites, dtype=np.int64))
     return a, ctypes.c_void_p(a.ctypes.data), len(a)
@@ -146,13 +177,19 @@ def build_w_sites(Up, sites):
 
 
 def stencil_sites(kind, field, m0, v, sites):
-    """(D v)(n) for n in sites; field = phased links (Wilson, staggered) or
-    build_w_sites(...) of the same sites (Brillouin).  Returns (len(sites),) + v.shape[4:]."""
+    """(D v)(n) for n in sites; field = phased links (Wilson, staggered, WLAP,
+    WSUV) or build_w_sites(...) of the same sites (Brillouin, BLAP, BSUV); for
+    the Laplace kinds m0 is the mass m of A.  Returns (len(sites),) + v.shape[4:]."""
     nt, nz, ny, nx = v.shape[:4]
     nc, nv = v.shape[4], v.shape[-1]
     v = np.ascontiguousarray(v, np.complex128)
     a, pa, ns = _sites_arr(sites)
     out = np.empty((ns,) + v.shape[4:], np.complex128)
+    if kind in LAPLACE:
+        fn = lib().orc_blap_sites if uses_w(kind) else lib().orc_wlap_sites
+        fn(_i4((nx, ny, nz, nt)), nc, spins(kind), nv, _p(np.ascontiguousarray(field)), float(m0), _p(v), pa, ns,
+           _p(out))
+        return out
     fn = {WILSON: lib().orc_wilson_sites, STAGGERED: lib().orc_staggered_sites,
           BRILLOUIN: lib().orc_brillouin_sites}[kind]
     fn(_i4((nx, ny, nz, nt)), nc, nv, _p(np.ascontiguousarray(field)), float(m0), _p(v), pa, ns, _p(out))
@@ -215,6 +252,8 @@ class Operator:
     With csw != 0 (Wilson and Brillouin) the clover term C of Eq. (def_clov),
     built from the field strength of the gauge field V (default: U), is added:
     v = (D + C) u, as in Eqs. (def_wils) and (def_bril).
+    The Laplace kinds (WLAP, BLAP, WSUV, BSUV) apply A = -1/2 Lap + m^2/2 with
+    m = m0; A is hermitian, so its dagger is A itself.
     """
 
     def __init__(self, kind, U, bc=(1, 1, 1, 1), m0=0.0, csw=0.0, V=None):
@@ -226,19 +265,21 @@ class Operator:
         self.csw = float(csw)
         self.F = None
         if self.csw != 0.0:
-            if kind == STAGGERED:
+            if kind not in (WILSON, BRILLOUIN):
                 raise ValueError("the clover term acts on Wilson-type vectors only")
             self.F = field_strength(U if V is None else V)
 
     @property
     def W(self):
-        """All 81 W links (Brillouin), built on first use."""
-        if self._W is None and self.kind == BRILLOUIN:
+        """All 81 W links (Brillouin-type kinds), built on first use."""
+        if self._W is None and uses_w(self.kind):
             self._W = build_w(self.Up)
         return self._W
 
     def apply(self, v, m0=None):
         m = self.m0 if m0 is None else m0
+        if self.kind in LAPLACE:
+            return laplace(self.kind, self.W if uses_w(self.kind) else self.Up, m, v)
         if self.kind == WILSON:
             out = wilson(self.Up, m, v)
         elif self.kind == BRILLOUIN:
@@ -252,10 +293,12 @@ class Operator:
     def apply_sites(self, v, sites, m0=None, dagger=False):
         """(D v)(n) or (D^dag v)(n) at the listed site indices only."""
         m = self.m0 if m0 is None else m0
-        if self.kind == BRILLOUIN:
+        if uses_w(self.kind):
             field = build_w_sites(self.Up, sites)
         else:
             field = self.Up
+        if self.kind in LAPLACE:
+            return stencil_sites(self.kind, field, m, v, sites)
         if not dagger:
             return stencil_sites(self.kind, field, m, v, sites) + self._clover_sites(v, sites)
         out = stencil_sites(self.kind, field, m, self._sandwich(v), sites) + \
@@ -281,6 +324,8 @@ class Operator:
         return epsilon(v) if self.kind == STAGGERED else gamma5(v)
 
     def apply_dagger(self, v, m0=None):
+        if self.kind in LAPLACE:
+            return self.apply(v, m0)
         return self._sandwich(self.apply(self._sandwich(v), m0))
 
     def apply_normal(self, v, m0=None):
@@ -556,7 +601,17 @@ def clover_flops_per_site(nc, multiplications=2):
 
 def flops_per_site(kind, nc):
     """Flops per site per RHS (App. E): Wilson 128Nc^2+72Nc, Brillouin
-    2560Nc^2+2376Nc, staggered 64Nc^2+2Nc."""
+    2560Nc^2+2376Nc, staggered 64Nc^2+2Nc; Laplace operators on Wilson-type
+    vectors 256Nc^2+8Nc (standard) and 2560Nc^2+648Nc (Brillouin), a quarter
+    of that on colour-only vectors."""
+    if kind == WLAP:
+        return 256 * nc * nc + 8 * nc
+    if kind == WSUV:
+        return 64 * nc * nc + 2 * nc
+    if kind == BLAP:
+        return 2560 * nc * nc + 648 * nc
+    if kind == BSUV:
+        return 640 * nc * nc + 162 * nc
     if kind == WILSON:
         return 128 * nc * nc + 72 * nc
     if kind == BRILLOUIN:

@@ -8,6 +8,7 @@ the App. E flop counts, the free-field spectral edges of Sec. 9), or a
 library routine on a dense brute-force matrix.
 """
 import itertools
+import os
 
 import numpy as np
 import pytest
@@ -599,3 +600,117 @@ def test_clover_flop_counts_app_e():
         assert O.clover_flops_per_site(int(nc), int(mults)) == int(flops)
         for n in (1, 2, 3, 4):
             assert O.clover_flops_per_site(n, int(mults)) == eval(poly.replace("^", "**"), {"nc": n})
+
+
+# ------------------------------------------------------- Laplace operators
+
+LAP_KINDS = [O.WLAP, O.BLAP, O.WSUV, O.BSUV]
+
+
+def laplace_symbol(kind, p, m):
+    """Free-field eigenvalue of A = -1/2 Lap + m^2/2 at momentum p: the
+    standard Laplacian gives sum_mu (1 - cos p_mu), the Brillouin one
+    2 (1 - prod_mu cos^2(p_mu / 2)) (its weights lambda_k sum to
+    4 prod cos^2(p/2) - 4 over the hypercube)."""
+    if kind in (O.WLAP, O.WSUV):
+        return 0.5 * m * m + np.sum(1 - np.cos(p))
+    return 0.5 * m * m + 2.0 * (1.0 - np.prod(np.cos(p / 2) ** 2))
+
+
+@pytest.mark.parametrize("bc", [(1, 1, 1, 1), (1, 1, 1, -1)])
+@pytest.mark.parametrize("kind", LAP_KINDS)
+def test_laplace_free_field_symbol(kind, bc):
+    dims, nc, m = (4, 4, 6, 4), 2, 0.3
+    op = O.Operator(kind, I.unit_gauge_field(dims, nc), bc)
+    rng = np.random.default_rng(61)
+    for p in momenta(dims, bc, rng, 5):
+        shape = (nc, 4, 3) if O.spins(kind) == 4 else (nc, 3)
+        chi = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+        psi = plane_wave(dims, p, chi)
+        got = op.apply(psi, m)
+        assert np.abs(got - laplace_symbol(kind, p, m) * psi).max() < 1e-12
+
+
+@pytest.mark.parametrize("kind", [O.WILSON, O.BRILLOUIN])
+def test_laplace_is_the_hermitian_part_of_the_dirac_operator(kind):
+    """gamma_mu nabla_mu is anti-hermitian, so (D + D^dag)/2 = -1/2 Lap + m0:
+    the Laplace operator at m^2/2 = m0 against the (pinned) Dirac operator and
+    its adjoint, on a random gauge field with twisted boundary phases."""
+    dims, nc, m = (4, 2, 4, 6), 3, 0.7
+    U = I.gauge_field(dims, nc, 0.5, seed=62)
+    bc = (1, -1, 1, -1)
+    psi = I.source(dims, nc, 3, seed=63)
+    Dop = O.Operator(kind, U, bc)
+    herm = 0.5 * (Dop.apply(psi, 0.5 * m * m) + Dop.apply_dagger(psi, 0.5 * m * m))
+    lap = O.Operator(O.WLAP if kind == O.WILSON else O.BLAP, U, bc).apply(psi, m)
+    assert np.abs(lap - herm).max() < 1e-12 * np.abs(herm).max()
+
+
+def test_colour_only_laplace_is_the_spin_diagonal_one():
+    dims, nc = (4, 2, 2, 4), 3
+    U = I.gauge_field(dims, nc, 0.5, seed=64)
+    psi = I.source(dims, nc, 2, seed=65)
+    for full, suv in ((O.WLAP, O.WSUV), (O.BLAP, O.BSUV)):
+        a = O.Operator(full, U, (1, 1, 1, -1)).apply(psi, 0.4)
+        b = O.Operator(suv, U, (1, 1, 1, -1))
+        for sp in range(4):
+            assert np.abs(a[..., sp, :] - b.apply(np.ascontiguousarray(psi[..., sp, :]), 0.4)).max() < 1e-13
+
+
+@pytest.mark.parametrize("kind", LAP_KINDS)
+def test_laplace_gauge_covariance(kind):
+    dims, nc = (4, 2, 4, 2), 3
+    U = I.gauge_field(dims, nc, 0.5, seed=66)
+    Om = I.gauge_transform(dims, nc, seed=67)
+    cols = O.spins(kind) == 1
+    psi = I.source(dims, nc, 2, seed=68, staggered=cols)
+    rot = (lambda v: np.einsum("...ab,...bv->...av", Om, v)) if cols else \
+          (lambda v: np.einsum("...ab,...bsv->...asv", Om, v))
+    bc = (1, -1, 1, -1)
+    lhs = O.Operator(kind, _transform_links(U, Om), bc).apply(rot(psi), 0.2)
+    rhs = rot(O.Operator(kind, U, bc).apply(psi, 0.2))
+    assert np.abs(lhs - rhs).max() < 1e-12 * np.abs(rhs).max()
+
+
+@pytest.mark.parametrize("kind", [O.WSUV, O.BSUV])
+def test_laplace_dense_hermitian_positive_and_cg(kind):
+    """Dense on 2^4 x N_c = 2: A is hermitian with spectrum >= m^2/2 (the paper
+    calls it hpd), and oracle CG on A x = b matches a dense solve."""
+    dims, nc, m = (2, 2, 2, 2), 2, 0.3
+    U = I.gauge_field(dims, nc, 0.8, seed=69)
+    op = O.Operator(kind, U, (1, 1, 1, -1))
+    n = 16 * nc
+    basis = np.moveaxis(np.eye(n, dtype=complex).reshape((n, 2, 2, 2, 2, nc)), 0, -1)
+    A = op.apply(basis, m).reshape(n, n)
+    assert np.abs(A - A.conj().T).max() < 1e-14
+    assert np.linalg.eigvalsh(A).min() >= 0.5 * m * m - 1e-12
+    b = I.source(dims, nc, 2, seed=70, staggered=True)
+    x, info = O.cg(lambda v: op.apply(v, m), b, tol=1e-12, maxit=500)
+    assert info["status"] == O.CONVERGED
+    want = np.linalg.solve(A, b.reshape(n, 2))
+    assert np.abs(x.reshape(n, 2) - want).max() < 1e-10 * np.abs(want).max()
+
+
+def test_laplace_sites_match_full_apply():
+    dims = (4, 2, 2, 4)
+    U = I.gauge_field(dims, 3, 0.5, seed=71)
+    sites = [0, 7, 21, 63]
+    for kind in LAP_KINDS:
+        cols = O.spins(kind) == 1
+        psi = I.source(dims, 3, 2, seed=72, staggered=cols)
+        op = O.Operator(kind, U, (1, 1, 1, -1))
+        full = op.apply(psi, 0.3).reshape((-1,) + psi.shape[4:])
+        assert np.abs(op.apply_sites(psi, sites, 0.3) - full[sites]).max() < 1e-13
+
+
+def test_laplace_flop_counts_app_e():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "app_e_laplace_flops.txt")
+    kinds = {"wlap": O.WLAP, "wsuv": O.WSUV, "blap": O.BLAP, "bsuv": O.BSUV}
+    rows = [ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 4
+    for name, nc, flops, f12, poly in rows:
+        assert O.flops_per_site(kinds[name], int(nc)) == int(flops)
+        if f12 != "-":
+            assert 12 * O.flops_per_site(kinds[name], int(nc)) == int(f12)
+        for n in (1, 2, 3, 4):
+            assert O.flops_per_site(kinds[name], n) == eval(poly.replace("^", "**"), {"nc": n})
