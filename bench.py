@@ -40,7 +40,7 @@ NC = 3
 NV = 12
 BC = (1, 1, 1, -1)
 EPS = 0.4
-MASS = {0: 0.1, 1: 0.1, 2: 0.05}
+MASS = {0: 0.1, 1: 0.1, 2: 0.05, 3: 0.1, 4: 0.1, 5: 0.1, 6: 0.1}   # Laplace kinds: m of A
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 
@@ -59,6 +59,7 @@ def parse():
     p.add_argument("--csw", type=float, default=0.0,
                    help="time D_W and D_B with the clover term of this c_SW (0: the plain operators)")
     p.add_argument("--no-clover", action="store_true", help="skip the separate clover-term measurement")
+    p.add_argument("--no-laplace", action="store_true", help="skip the separate Laplace-operator measurement")
     p.add_argument("--ops", default="wilson,brillouin,staggered",
                    help="profiling only: subset of operators to create and time")
     p.add_argument("--fixed", default=None,
@@ -81,9 +82,9 @@ def alg_bytes_per_site(kind, nc, nv, eb=4, clover=False):
     """Compulsory bytes per site and apply: spinor in + out once, links once
     (Brillouin: the 80 stored W links of this implementation), plus the four
     N_c x N_c clover blocks per site when the clover term is applied."""
-    spin = 1 if kind == 2 else 4
+    spin = 1 if kind in (2, 5, 6) else 4               # staggered, colour-only Laplace kinds
     vec = nc * spin * nv * 2 * eb
-    links = (80 if kind == 1 else 4) * nc * nc * 2 * eb
+    links = (80 if kind in (1, 4, 6) else 4) * nc * nc * 2 * eb   # Brillouin kinds: W links
     return 2 * vec + links + (4 * nc * nc * 2 * eb if clover else 0)
 
 
@@ -449,6 +450,9 @@ def main():
     if not args.ncu and not args.no_clover and not args.csw:
         line["clover"] = clover_measurement(D, U, ops, xs, ys, per_op, pk, fp32_peak, quick_ms)
 
+    if not args.ncu and not args.no_laplace:
+        line["laplace"] = laplace_measurement(D, U, pk, fp32_peak, quick_ms)
+
     if args.solve:
         line["solve"] = solver_comparison(D, I, torch)
     if args.batch:
@@ -489,6 +493,37 @@ def clover_measurement(D, U, ops, xs, ys, per_op, pk, fp32_peak, quick_ms, csw=1
             "hbm_frac": gbytes / (ms * 1e-3) / pk["hbm"], "alu_frac": flop / (ms * 1e-3) / 1e12 / fp32_peak,
             "launch": op.get_launch()}
         op.close()
+    return out
+
+
+def laplace_measurement(D, U, pk, fp32_peak, quick_ms, m=0.1):
+    """The Laplace operators A = -1/2 Lap + m^2/2 (wlap, blap on Wilson-type
+    vectors; wsuv, bsuv on colour-only vectors) on the timed workload
+    (16^3x32, N_c = 3, N_v = 12, FP32, site-inner, autotuned): time per
+    apply, Gflop/s with the App. E counts, algorithmic bandwidth, and the
+    fraction of the binding roof (FP32 peak for blap, HBM copy otherwise)."""
+    import numpy as np
+    import torch
+    V = int(np.prod(DIMS))
+    out = {"m": m}
+    for k in (D.WLAP, D.BLAP, D.WSUV, D.BSUV):
+        op = D.DiracOp(k, U, NV, BC, D.F32, layout=D.SITE_INNER)
+        x = op.new_vector()
+        x.real.normal_()
+        y = op.new_vector(zero=False)
+        op.autotune(m)
+        ms = quick_ms(op, x, y, m, reps=50)
+        flop = D.flops_per_site(k, NC) * V * NV
+        gbytes = alg_bytes_per_site(k, NC, NV) * V / 1e9
+        alu = k == D.BLAP
+        out[D.KIND_NAMES[k]] = {
+            "ms": ms, "gflops": flop / (ms * 1e-3) / 1e9, "alg_GBps": gbytes / (ms * 1e-3),
+            "bound": "alu" if alu else "hbm",
+            "frac": (flop / (ms * 1e-3) / 1e12 / fp32_peak) if alu else gbytes / (ms * 1e-3) / pk["hbm"],
+            "launch": op.get_launch()}
+        op.close()
+        del x, y
+        torch.cuda.empty_cache()
     return out
 
 

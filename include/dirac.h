@@ -39,7 +39,22 @@
 extern "C" {
 #endif
 
-typedef enum { DIRAC_WILSON = 0, DIRAC_BRILLOUIN = 1, DIRAC_STAGGERED = 2 } dirac_kind;
+/* Operator kinds.  The three Dirac operators, and the Laplace operators
+ * A = -1/2 Lap + m^2/2 of Secs. 6 and 7 (the paper's wlap, blap, wsuv and
+ * bsuv routines, App. F): the standard 9-point Laplacian, Eq. (app_wlap),
+ * and the Brillouin 81-point Laplacian, Eq. (app_blap), each on Wilson-type
+ * vectors (acting trivially on the 4 spin components) or on colour-only
+ * vectors (the staggered vector shape, without the staggered phases).  For
+ * the Laplace kinds the m0 argument of every call is the mass m of A; A is
+ * hermitian positive definite, so its dagger is A itself, and they exist in
+ * F64 and F32 only. */
+typedef enum {
+    DIRAC_WILSON = 0, DIRAC_BRILLOUIN = 1, DIRAC_STAGGERED = 2,
+    DIRAC_WLAP = 3,   /* -1/2 Lap_std + m^2/2 on Wilson-type vectors */
+    DIRAC_BLAP = 4,   /* -1/2 Lap_bri + m^2/2 on Wilson-type vectors (builds W) */
+    DIRAC_WSUV = 5,   /* -1/2 Lap_std + m^2/2 on colour-only vectors */
+    DIRAC_BSUV = 6    /* -1/2 Lap_bri + m^2/2 on colour-only vectors (builds W) */
+} dirac_kind;
 typedef enum { DIRAC_F64 = 0, DIRAC_F32 = 1, DIRAC_BF16 = 2, DIRAC_F16 = 3 } dirac_prec;
 
 enum {
@@ -98,14 +113,14 @@ typedef struct dirac_op dirac_op;   /* opaque */
 /* Create an operator on gauge field U (device pointer, layout above, in
  * precision u_prec = DIRAC_F64 or DIRAC_F32, no boundary phases applied).
  * The operator keeps its own copy of the phased links in geom->prec; for
- * DIRAC_BRILLOUIN it also builds and keeps the 80 off-centre W_s(n) of
+ * DIRAC_BRILLOUIN, DIRAC_BLAP and DIRAC_BSUV it also builds and keeps the 80 off-centre W_s(n) of
  * Tab. off-axis (computed from U in FP64 for FP64 operators and in FP32
  * otherwise, stored in the link precision).
  * Synchronises `stream` before returning.  U may be freed afterwards. */
 int dirac_op_create(dirac_kind kind, const dirac_geom *geom, const void *U,
                     dirac_prec u_prec, void *stream, dirac_op **out);
 
-/* Replace the gauge field (same geometry); rebuilds W for Brillouin and
+/* Replace the gauge field (same geometry); rebuilds W for the Brillouin kinds and
  * removes a clover term (dirac_op_set_clover builds it for the new field).
  * Synchronises `stream` before returning. */
 int dirac_op_update_links(dirac_op *op, const void *U, dirac_prec u_prec, void *stream);
@@ -204,7 +219,7 @@ int dirac_vec_norm2(const dirac_op *op, const void *v, double *out_dev, void *st
 int dirac_vec_dot(const dirac_op *op, const void *u, const void *v, double *out_dev, void *stream);
 /* y += alpha x per RHS (Eq. def_incr with complex alpha); alpha_dev: N_v (re, im) pairs. */
 int dirac_vec_axpy(const dirac_op *op, const double *alpha_dev, const void *x, void *y, void *stream);
-/* v = gamma5 v (Wilson-type) or epsilon v (staggered), in place. */
+/* v = gamma5 v (4 spin components) or epsilon v (colour-only vectors), in place. */
 int dirac_vec_gamma5(const dirac_op *op, void *v, void *stream);
 /* Convert a vector between precisions (same shape): src in src_prec, dst in dst_prec. */
 int dirac_vec_convert(const dirac_op *op, const void *src, dirac_prec src_prec, void *dst,
@@ -238,7 +253,9 @@ int dirac_vec_norm2_noalloc(const void *v, dirac_prec prec, long long rows, int 
 typedef enum {
     DIRAC_CG_NORMAL = 0,   /* CG on D^dag D x = D^dag b (Sec. 9, A = D^dag D) */
     DIRAC_BICGSTAB = 1,    /* BiCGstab on D x = b (Sec. 9) */
-    DIRAC_CG_HPD = 2       /* CG on D^dag D x = b, b given directly (pseudofermion solves) */
+    DIRAC_CG_HPD = 2       /* CG on D^dag D x = b, b given directly (pseudofermion solves);
+                              for the Laplace kinds CG on A x = b with A itself (the
+                              paper's cg_wlap / cg_blap), the only CG they accept */
 } dirac_solver;
 
 typedef struct {
@@ -330,7 +347,9 @@ int dirac_force_wilson(const dirac_op *op, const void *psi, const void *chi, voi
 /* ------------------------------------------------------------- utilities */
 const char *dirac_error_string(int code);
 /* Flops per site per RHS (App. E): Wilson 128Nc^2+72Nc, Brillouin
- * 2560Nc^2+2376Nc, staggered 64Nc^2+2Nc; -1 for an invalid kind. */
+ * 2560Nc^2+2376Nc, staggered 64Nc^2+2Nc; Laplace operators: WLAP
+ * 256Nc^2+8Nc, BLAP 2560Nc^2+648Nc, WSUV 64Nc^2+2Nc, BSUV 640Nc^2+162Nc;
+ * -1 for an invalid kind. */
 long dirac_flops_per_site(dirac_kind kind, int nc);
 /* Flops per site per RHS of the clover term as App. E counts it for the
  * two-multiplication form: 64Nc^2 (576 for SU(3)). */

@@ -105,6 +105,7 @@ extern "C" int dirac_solve_batched(int nsolves, dirac_op *const *ops, const void
         if (!ops[i] || !b[i] || !x[i]) return DIRAC_ERR_INVALID_ARG;
         if (((uintptr_t)b[i] & 15) || ((uintptr_t)x[i] & 15)) return DIRAC_ERR_ALIGNMENT;
         if (prm->inner_prec != ops[i]->prec) return DIRAC_ERR_UNSUPPORTED_PREC;   // one precision per solve
+        if (is_laplace(ops[i]->kind) && prm->solver == DIRAC_CG_NORMAL) return DIRAC_ERR_INVALID_ARG;
         for (int j = 0; j < i; ++j)
             if (ops[j] == ops[i]) return DIRAC_ERR_INVALID_ARG;   // each solve owns its workspace
     }
@@ -162,7 +163,7 @@ extern "C" int dirac_solve_batched(int nsolves, dirac_op *const *ops, const void
         if (prm->solver == DIRAC_CG_NORMAL) TRYB(op_apply(op, b[i], rhs, m0[i], -1, main));
         else TRYB(blas_axpby(op, p, rhs, b[i], nullptr, 1.0, nullptr, nullptr, 0.0, nullptr, main));
         TRYB(blas_norm2(op, p, rhs, nb, main));
-        TRYB(op_apply_normal(op, x[i], q, m0[i], main));
+        TRYB(op_apply_cg(op, x[i], q, m0[i], main));
         TRYB(blas_axpby(op, p, r, rhs, nullptr, 1.0, q, nullptr, -1.0, rr, main));
         TRYB(blas_axpby(op, p, pv, r, nullptr, 1.0, nullptr, nullptr, 0.0, nullptr, main));
         batch_check_kernel<<<1, 64, 0, main>>>(nv, rr, nb, tol2, act, dstate + i, 0);
@@ -202,7 +203,7 @@ extern "C" int dirac_solve_batched(int nsolves, dirac_op *const *ops, const void
                     // last iteration of the segment: x += alpha p, then replace r by
                     // the true residual and build the next direction from it
                     TRYB(blas_axpby(op, p, x[i], x[i], nullptr, 1.0, pv, alpha, 1.0, nullptr, s));
-                    TRYB(op_apply_normal(op, x[i], q, m0[i], s));
+                    TRYB(op_apply_cg(op, x[i], q, m0[i], s));
                     TRYB(blas_axpby(op, p, r, rhs, nullptr, 1.0, q, nullptr, -1.0, rr_new, s));
                     batch_beta_kernel<<<1, 64, 0, s>>>(nv, rr_new, rr, act, beta);
                     TRYB(blas_axpby(op, p, pv, r, nullptr, 1.0, pv, beta, 1.0, nullptr, s));

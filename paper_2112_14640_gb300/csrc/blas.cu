@@ -488,7 +488,7 @@ int blas_gamma5(const dirac_op *op, dirac_prec p, void *v, cudaStream_t s) {
     return dispatch_prec(p, [&](auto tag) {
         using E = std::remove_pointer_t<decltype(tag)>;
         const long long n = op->rows * op->nv;
-        gamma5_kernel<E><<<grid_for(n, 256), 256, 0, s>>>((E *)v, op->lat, op->nc, op->kind == DIRAC_STAGGERED,
+        gamma5_kernel<E><<<grid_for(n, 256), 256, 0, s>>>((E *)v, op->lat, op->nc, spins_of(op->kind) == 1,
                                                           op->geom.layout);
         return launch_check("gamma5_kernel");
     });

@@ -35,6 +35,10 @@ int op_apply(const dirac_op *op, const void *in, void *out, double m0, int sgn, 
     case DIRAC_WILSON: return launch_wilson(op, in, out, m0, sgn, s);
     case DIRAC_BRILLOUIN: return launch_brillouin(op, in, out, m0, sgn, s);
     case DIRAC_STAGGERED: return launch_staggered(op, in, out, m0, sgn, s);
+    case DIRAC_WLAP:
+    case DIRAC_BLAP:
+    case DIRAC_WSUV:
+    case DIRAC_BSUV: return launch_laplace(op, in, out, m0, s);   // hermitian: sgn is irrelevant
     }
     return DIRAC_ERR_INVALID_ARG;
 }
@@ -44,6 +48,10 @@ int op_apply_normal(const dirac_op *op, const void *in, void *out, double m0, cu
     int rc = op_apply(op, in, op->scratch, m0, +1, s);
     if (rc) return rc;
     return op_apply(op, op->scratch, out, m0, -1, s);
+}
+
+int op_apply_cg(const dirac_op *op, const void *in, void *out, double m0, cudaStream_t s) {
+    return is_laplace(op->kind) ? op_apply(op, in, out, m0, +1, s) : op_apply_normal(op, in, out, m0, s);
 }
 
 static void pipe_free(dirac_host_pipe *p) {
@@ -98,7 +106,7 @@ static void op_free(dirac_op *op) {
 
 static int validate_geom(dirac_kind kind, const dirac_geom *g) {
     if (!g) return DIRAC_ERR_INVALID_ARG;
-    if (kind != DIRAC_WILSON && kind != DIRAC_BRILLOUIN && kind != DIRAC_STAGGERED) return DIRAC_ERR_INVALID_ARG;
+    if (kind < DIRAC_WILSON || kind > DIRAC_BSUV) return DIRAC_ERR_INVALID_ARG;
     for (int m = 0; m < 4; ++m) {
         if (g->dims[m] < 2) return DIRAC_ERR_INVALID_ARG;
         if (g->bc[m] != 1 && g->bc[m] != -1) return DIRAC_ERR_INVALID_ARG;
@@ -112,6 +120,7 @@ static int validate_geom(dirac_kind kind, const dirac_geom *g) {
     if (g->link_storage != DIRAC_LINKS_NATIVE && g->link_storage != DIRAC_LINKS_F32) return DIRAC_ERR_INVALID_ARG;
     if (g->link_storage == DIRAC_LINKS_F32 && g->prec != DIRAC_BF16 && g->prec != DIRAC_F16)
         return DIRAC_ERR_UNSUPPORTED_PREC;
+    if (is_laplace(kind) && g->prec != DIRAC_F64 && g->prec != DIRAC_F32) return DIRAC_ERR_UNSUPPORTED_PREC;
     return DIRAC_OK;
 }
 
@@ -165,11 +174,11 @@ int op_alloc(dirac_kind kind, const dirac_geom *g, dirac_op **out) {
     op->prec = g->prec;
     op->V = (long long)g->dims[0] * g->dims[1] * g->dims[2] * g->dims[3];
     op->lat = Lat{g->dims[0], g->dims[1], g->dims[2], g->dims[3], g->nv, op->V, 0, op->V};
-    op->rows = op->V * op->nc * (kind == DIRAC_STAGGERED ? 1 : 4);
+    op->rows = op->V * op->nc * spins_of(kind);
     const size_t eb = elem_bytes(op->prec), lb = elem_bytes(link_prec(op));
     op->vec_bytes = (size_t)op->rows * op->nv * 2 * eb;
     op->link_bytes = (size_t)op->V * 4 * op->nc * op->nc * 2 * lb;
-    op->w_bytes = kind == DIRAC_BRILLOUIN ? (size_t)op->V * 80 * op->nc * op->nc * 2 * lb : 0;
+    op->w_bytes = uses_w(kind) ? (size_t)op->V * 80 * op->nc * op->nc * 2 * lb : 0;
     // one reduction block per 2 SMs' worth of work, at most 1216 blocks
     long long want = (op->rows + 255) / 256;
     op->red_blocks = (int)(want < 1216 ? (want < 1 ? 1 : want) : 1216);
@@ -239,7 +248,7 @@ static int load_links(dirac_op *op, const void *U, dirac_prec u_prec, cudaStream
     if (!U) return DIRAC_ERR_INVALID_ARG;
     if (u_prec != DIRAC_F64 && u_prec != DIRAC_F32) return DIRAC_ERR_UNSUPPORTED_PREC;
     int rc = launch_phase_links(op, U, u_prec, s);
-    if (!rc && op->kind == DIRAC_BRILLOUIN) rc = launch_build_w(op, U, u_prec, s);
+    if (!rc && uses_w(op->kind)) rc = launch_build_w(op, U, u_prec, s);
     if (!rc) rc = cuda_check(cudaStreamSynchronize(s), "link setup");
     // a clover term belongs to the old field
     cudaFree(op->clover);
@@ -277,7 +286,8 @@ int dirac_op_update_links(dirac_op *op, const void *U, dirac_prec u_prec, void *
 }
 
 int dirac_op_set_clover(dirac_op *op, double csw, const void *V, dirac_prec v_prec, void *stream) {
-    if (!op || op->kind == DIRAC_STAGGERED || !std::isfinite(csw)) return DIRAC_ERR_INVALID_ARG;
+    if (!op || (op->kind != DIRAC_WILSON && op->kind != DIRAC_BRILLOUIN) || !std::isfinite(csw))
+        return DIRAC_ERR_INVALID_ARG;
     if (csw != 0.0) {
         if (!V) return DIRAC_ERR_INVALID_ARG;
         if (v_prec != DIRAC_F64 && v_prec != DIRAC_F32) return DIRAC_ERR_UNSUPPORTED_PREC;
@@ -307,7 +317,7 @@ int dirac_op_set_clover(dirac_op *op, double csw, const void *V, dirac_prec v_pr
 }
 
 int dirac_op_copy_w(const dirac_op *op, void *w_out, void *stream) {
-    if (!op || !w_out || op->kind != DIRAC_BRILLOUIN) return DIRAC_ERR_INVALID_ARG;
+    if (!op || !w_out || !uses_w(op->kind)) return DIRAC_ERR_INVALID_ARG;
     return launch_unpack_w(op, w_out, (cudaStream_t)stream);
 }
 
@@ -567,6 +577,10 @@ long dirac_flops_per_site(dirac_kind kind, int nc) {
     case DIRAC_WILSON: return 128 * n * n + 72 * n;
     case DIRAC_BRILLOUIN: return 2560 * n * n + 2376 * n;
     case DIRAC_STAGGERED: return 64 * n * n + 2 * n;
+    case DIRAC_WLAP: return 256 * n * n + 8 * n;
+    case DIRAC_BLAP: return 2560 * n * n + 648 * n;
+    case DIRAC_WSUV: return 64 * n * n + 2 * n;
+    case DIRAC_BSUV: return 640 * n * n + 162 * n;
     }
     return -1;
 }

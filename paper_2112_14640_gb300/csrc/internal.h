@@ -149,6 +149,13 @@ int dispatch_minb(int minb, F &&f) {
     }
 }
 
+// kind properties: the Laplace operators -1/2 Lap + m^2/2 (hermitian), the
+// number of spin components per colour of the kind's vectors, and whether the
+// kind stencils with the 80 Brillouin W links
+inline bool is_laplace(dirac_kind k) { return k >= DIRAC_WLAP && k <= DIRAC_BSUV; }
+inline int spins_of(dirac_kind k) { return (k == DIRAC_STAGGERED || k == DIRAC_WSUV || k == DIRAC_BSUV) ? 1 : 4; }
+inline bool uses_w(dirac_kind k) { return k == DIRAC_BRILLOUIN || k == DIRAC_BLAP || k == DIRAC_BSUV; }
+
 // (vr, minb, block) an operator launches with: its tuned choice or the default.
 inline void launch_variant(const dirac_op *op, int &vr, int &minb, int &block) {
     if (op->vr) {
@@ -167,7 +174,7 @@ inline void launch_variant(const dirac_op *op, int &vr, int &minb, int &block) {
             minb = vr == 4 ? 3 : 4;
         } else if (op->kind == DIRAC_STAGGERED) {
             minb = 3;
-        } else if (vr <= 2) {   // Brillouin
+        } else if (op->kind == DIRAC_BRILLOUIN && vr <= 2) {
             minb = 3;
             block = 384;
         }
@@ -182,6 +189,8 @@ inline unsigned grid_for(long long threads, int block) {
 int launch_wilson(const dirac_op *op, const void *in, void *out, double m0, int sgn, cudaStream_t s);
 int launch_staggered(const dirac_op *op, const void *in, void *out, double m0, int sgn, cudaStream_t s);
 int launch_brillouin(const dirac_op *op, const void *in, void *out, double m0, int sgn, cudaStream_t s);
+// A = -1/2 Lap + m^2/2 for the Laplace kinds (laplace.cuh); m is the mass of A
+int launch_laplace(const dirac_op *op, const void *in, void *out, double m, cudaStream_t s);
 
 // link preparation
 int launch_phase_links(dirac_op *op, const void *U, dirac_prec u_prec, cudaStream_t s);
@@ -212,6 +221,8 @@ int blas_convert(const dirac_op *op, const void *src, dirac_prec sp, void *dst, 
 // operator handle helpers (capi.cu)
 int op_apply(const dirac_op *op, const void *in, void *out, double m0, int sgn, cudaStream_t s);
 int op_apply_normal(const dirac_op *op, const void *in, void *out, double m0, cudaStream_t s);
+// the operator CG iterates with: D^dag D, or A itself for the (hermitian) Laplace kinds
+int op_apply_cg(const dirac_op *op, const void *in, void *out, double m0, cudaStream_t s);
 int op_alloc(dirac_kind kind, const dirac_geom *g, dirac_op **out);
 int op_inner(const dirac_op *op, dirac_prec p, int link_storage, dirac_op **out, cudaStream_t s);
 void op_destroy(dirac_op *op);

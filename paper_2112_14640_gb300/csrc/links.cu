@@ -363,7 +363,7 @@ int launch_convert_links(const dirac_op *src, dirac_op *dst, cudaStream_t s) {
     long long n = src->V * 4 * src->nc * src->nc * 2;
     int rc = convert_array(src->links, link_prec(src), dst->links, link_prec(dst), n, s);
     if (rc) return rc;
-    if (src->kind == DIRAC_BRILLOUIN) {
+    if (src->w) {
         // same order, scale and layout, element by element
         n = src->V * 80 * src->nc * src->nc * 2;
         rc = convert_array(src->w, link_prec(src), dst->w, link_prec(dst), n, s);

@@ -249,9 +249,10 @@ static void lanczos_extremes(const std::vector<double> &al, const std::vector<do
     lmax = 0.5 * (a + b);
 }
 
-// A = D^dag D (normal = true) applied through the operator scratch.
+// The CG operator: D^dag D through the operator scratch, or A itself for the
+// hermitian positive definite Laplace kinds.
 static int apply_A(const dirac_op *op, const void *in, void *out, double m0, cudaStream_t s) {
-    return op_apply_normal(op, in, out, m0, s);
+    return op_apply_cg(op, in, out, m0, s);
 }
 
 // q = D^dag D p through the operator scratch, with pq = Re <p, q> per RHS.
@@ -261,8 +262,8 @@ static int apply_A(const dirac_op *op, const void *in, void *out, double m0, cud
 // the true residual then grows until the 1% rule stops the solve (measured on
 // staggered solves at cond ~ 2e3).
 static int apply_A_pq(const dirac_op *op, const void *p, void *q, double *pq, double m0, cudaStream_t s) {
-    int rc = op_apply(op, p, op->scratch, m0, +1, s);
-    if (!rc) rc = op_apply(op, op->scratch, q, m0, -1, s);
+    int rc = op_apply(op, p, is_laplace(op->kind) ? q : op->scratch, m0, +1, s);
+    if (!rc && !is_laplace(op->kind)) rc = op_apply(op, op->scratch, q, m0, -1, s);
     if (!rc) rc = blas_dot_re(op, op->prec, p, q, pq, s);
     return rc;
 }
@@ -699,7 +700,7 @@ static int mixed_solve(const dirac_op *op, const void *b, void *x, double m0, co
     st->status = DIRAC_NOT_CONVERGED;
     for (;;) {
         // r = rhs - A x (operator precision)
-        if (cg) TRY(op_apply_normal(op, x, tmp, m0, s));
+        if (cg) TRY(op_apply_cg(op, x, tmp, m0, s));
         else TRY(op_apply(op, x, tmp, m0, +1, s));
         TRY(blas_axpby(op, ph, r, rhs, nullptr, 1.0, tmp, nullptr, -1.0, wh.rr, s));
         TRY(to_host(rr, wh.rr, nv, s));
@@ -842,10 +843,10 @@ int solve(const dirac_op *op, const void *b, void *x, double m0, const dirac_sol
         rc = reliable_solve(op, b, x, m0, prm, &st, s);
     else rc = mixed_solve(op, b, x, m0, prm, &st, s);
     if (rc) return rc;
-    // true residual ||b - D x|| / ||b|| (||b - D^dag D x|| / ||b|| for CG_HPD)
+    // true residual ||b - D x|| / ||b|| (||b - A x|| / ||b|| for CG_HPD)
     Ws w;
     TRY(get_ws(op, w));
-    if (prm->solver == DIRAC_CG_HPD) TRY(op_apply_normal(op, x, w.v[7], m0, s));
+    if (prm->solver == DIRAC_CG_HPD) TRY(op_apply_cg(op, x, w.v[7], m0, s));
     else TRY(op_apply(op, x, w.v[7], m0, +1, s));
     TRY(blas_axpby(op, op->prec, w.v[6], b, nullptr, 1.0, w.v[7], nullptr, -1.0, w.rr, s));
     TRY(blas_norm2(op, op->prec, b, w.nb, s));
@@ -868,6 +869,10 @@ extern "C" int dirac_solve(const dirac_op *op, const void *b, void *x, double m0
         return DIRAC_ERR_INVALID_ARG;
     if (params->inner_prec < DIRAC_F64 || params->inner_prec > DIRAC_F16) return DIRAC_ERR_UNSUPPORTED_PREC;
     if (!(params->tol > 0) || params->maxit < 1) return DIRAC_ERR_INVALID_ARG;
+    if (dgb::is_laplace(op->kind)) {   // A is already hpd; FP64 / FP32 only
+        if (params->solver == DIRAC_CG_NORMAL) return DIRAC_ERR_INVALID_ARG;
+        if (params->inner_prec != DIRAC_F64 && params->inner_prec != DIRAC_F32) return DIRAC_ERR_UNSUPPORTED_PREC;
+    }
     if (params->mixed_mode != DIRAC_MIXED_RELIABLE && params->mixed_mode != DIRAC_MIXED_RESTART &&
         params->mixed_mode != DIRAC_MIXED_ADAPTIVE)
         return DIRAC_ERR_INVALID_ARG;

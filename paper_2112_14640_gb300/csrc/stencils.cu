@@ -1,4 +1,4 @@
-// stencils.cu -- dispatch of the three stencil launchers over storage
+// stencils.cu -- dispatch of the stencil launchers over storage
 // precision, vector layout and link storage.  The kernels live in
 // wilson.cuh, staggered.cuh and brillouin.cuh; every combination is
 // instantiated in its own small translation unit so the library builds in
@@ -13,6 +13,12 @@ template <typename E, int LAYOUT, typename EL>
 int launch_staggered_v(const dirac_op *op, const void *in, void *out, double m0, int sgn, cudaStream_t s);
 template <typename E, int LAYOUT, typename EL>
 int launch_brillouin_v(const dirac_op *op, const void *in, void *out, double m0, int sgn, cudaStream_t s);
+template <typename E, int LAYOUT>
+int launch_laplace_v(const dirac_op *op, const void *in, void *out, double m, cudaStream_t s);
+extern template int launch_laplace_v<double, 0>(const dirac_op *, const void *, void *, double, cudaStream_t);
+extern template int launch_laplace_v<double, 1>(const dirac_op *, const void *, void *, double, cudaStream_t);
+extern template int launch_laplace_v<float, 0>(const dirac_op *, const void *, void *, double, cudaStream_t);
+extern template int launch_laplace_v<float, 1>(const dirac_op *, const void *, void *, double, cudaStream_t);
 
 extern template int launch_wilson_v<double, 0, double>(const dirac_op *, const void *, void *, double, int, cudaStream_t);
 extern template int launch_wilson_v<double, 1, double>(const dirac_op *, const void *, void *, double, int, cudaStream_t);
@@ -91,6 +97,16 @@ int launch_staggered(const dirac_op *op, const void *in, void *out, double m0, i
 
 int launch_brillouin(const dirac_op *op, const void *in, void *out, double m0, int sgn, cudaStream_t s) {
     return dispatch_all<BrillouinTag>(op, [&](auto t) { return decltype(t)::run(op, in, out, m0, sgn, s); });
+}
+
+// The Laplace kinds exist in FP64 and FP32 (links in the vector precision).
+int launch_laplace(const dirac_op *op, const void *in, void *out, double m, cudaStream_t s) {
+    const int lay = op->geom.layout;
+    if (op->prec == DIRAC_F64)
+        return lay ? launch_laplace_v<double, 1>(op, in, out, m, s) : launch_laplace_v<double, 0>(op, in, out, m, s);
+    if (op->prec == DIRAC_F32)
+        return lay ? launch_laplace_v<float, 1>(op, in, out, m, s) : launch_laplace_v<float, 0>(op, in, out, m, s);
+    return DIRAC_ERR_UNSUPPORTED_PREC;
 }
 
 }  // namespace dgb

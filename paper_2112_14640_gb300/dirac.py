@@ -6,9 +6,10 @@ There is no fallback: if libdirac.so is missing or no GPU is present the
 calls raise.
 
 Vector tensors (device, C-contiguous), layout SITE_OUTER (the paper's order):
-  F64  complex128  Wilson-type (Nt, Nz, Ny, Nx, Nc, 4, Nv), staggered (Nt, Nz, Ny, Nx, Nc, Nv)
+  F64  complex128  Wilson-type (Nt, Nz, Ny, Nx, Nc, 4, Nv), colour-only (Nt, Nz, Ny, Nx, Nc, Nv)
   F32  complex64   same shapes
-layout SITE_INNER: Wilson-type (Nc, 4, Nt, Nz, Ny, Nx, Nv), staggered (Nc, Nt, Nz, Ny, Nx, Nv).
+layout SITE_INNER: Wilson-type (Nc, 4, Nt, Nz, Ny, Nx, Nv), colour-only (Nc, Nt, Nz, Ny, Nx, Nv).
+Wilson-type: WILSON, BRILLOUIN, WLAP, BLAP; colour-only: STAGGERED, WSUV, BSUV.
   BF16 bfloat16    same shapes + trailing (re, im) axis of length 2
   F16  float16     same shapes + trailing (re, im) axis of length 2
 Gauge field U: complex128 or complex64, (Nt, Nz, Ny, Nx, 4, Nc, Nc), no boundary phases.
@@ -21,12 +22,17 @@ import torch
 from . import build as _build
 
 WILSON, BRILLOUIN, STAGGERED = 0, 1, 2
+# Laplace operators A = -1/2 Lap + m^2/2 (standard / Brillouin Laplacian) on
+# Wilson-type vectors (WLAP, BLAP) or colour-only vectors (WSUV, BSUV)
+WLAP, BLAP, WSUV, BSUV = 3, 4, 5, 6
+LAPLACE = (WLAP, BLAP, WSUV, BSUV)
 F64, F32, BF16, F16 = 0, 1, 2, 3
 CG_NORMAL, BICGSTAB, CG_HPD = 0, 1, 2
 MIXED_RELIABLE, MIXED_RESTART, MIXED_ADAPTIVE = 0, 1, 2
 FORCE_TA, FORCE_GRAD = 0, 1
 PREC_NAMES = {F64: "f64", F32: "f32", BF16: "bf16", F16: "f16"}
-KIND_NAMES = {WILSON: "wilson", BRILLOUIN: "brillouin", STAGGERED: "staggered"}
+KIND_NAMES = {WILSON: "wilson", BRILLOUIN: "brillouin", STAGGERED: "staggered",
+              WLAP: "wlap", BLAP: "blap", WSUV: "wsuv", BSUV: "bsuv"}
 _TORCH_DTYPE = {F64: torch.complex128, F32: torch.complex64, BF16: torch.bfloat16, F16: torch.float16}
 
 
@@ -211,10 +217,15 @@ class DiracOp:
     def staggered(self):
         return self.kind == STAGGERED
 
+    @property
+    def colour_only(self):
+        """Vectors without spin components (staggered, WSUV, BSUV)."""
+        return self.kind in (STAGGERED, WSUV, BSUV)
+
     def vector_shape(self, prec=None):
         prec = self.prec if prec is None else prec
         nx, ny, nz, nt = self.dims
-        internal = (self.nc,) if self.staggered else (self.nc, 4)
+        internal = (self.nc,) if self.colour_only else (self.nc, 4)
         if self.layout == SITE_OUTER:
             shape = (nt, nz, ny, nx) + internal + (self.nv,)
         else:
@@ -223,7 +234,7 @@ class DiracOp:
 
     def _perm(self):
         # axes of a site-outer vector in site-inner order
-        return (4, 0, 1, 2, 3, 5) if self.staggered else (4, 5, 0, 1, 2, 3, 6)
+        return (4, 0, 1, 2, 3, 5) if self.colour_only else (4, 5, 0, 1, 2, 3, 6)
 
     def from_site_outer(self, v):
         """Reorder a complex tensor given in the paper's site-outer order into this operator's layout."""

@@ -46,7 +46,7 @@ def test_flop_counts_match_app_e(lib):
         assert D.flops_per_site(kinds[name], nc) == flops
         for n in (1, 2, 3, 4):
             assert D.flops_per_site(kinds[name], n) == eval(poly.replace("^", "**"), {"nc": n})
-    assert D.flops_per_site(7, 3) == -1
+    assert D.flops_per_site(9, 3) == -1
 
 
 def test_error_strings(lib):
@@ -107,3 +107,28 @@ def test_clover_flop_count_matches_app_e(lib):
     assert D.clover_flops_per_site(int(nc)) == int(flops)
     for n in (1, 2, 3, 4):
         assert D.clover_flops_per_site(n) == eval(poly.replace("^", "**"), {"nc": n})
+
+
+def test_laplace_kinds_flops_and_validation(lib):
+    """dirac_flops_per_site for the Laplace kinds against App. E
+    (tests/golden/app_e_laplace_flops.txt); 16-bit Laplace operators are
+    refused before any CUDA call."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "app_e_laplace_flops.txt")
+    kinds = {"wlap": D.WLAP, "wsuv": D.WSUV, "blap": D.BLAP, "bsuv": D.BSUV}
+    for name, nc, flops, f12, poly in (ln.split() for ln in open(path) if ln.strip() and not ln.startswith("#")):
+        assert D.flops_per_site(kinds[name], int(nc)) == int(flops)
+        for n in (1, 2, 3, 4):
+            assert D.flops_per_site(kinds[name], n) == eval(poly.replace("^", "**"), {"nc": n})
+    out = ctypes.c_void_p()
+    g = D.Geom()
+    g.dims[:] = (4, 4, 4, 4)
+    g.nc, g.nv = 3, 4
+    g.bc[:] = (1, 1, 1, 1)
+    for kind in (D.WLAP, D.BLAP, D.WSUV, D.BSUV):
+        for prec in (D.BF16, D.F16):
+            g.prec = prec
+            assert lib.dirac_op_create(kind, ctypes.byref(g), ctypes.c_void_p(1 << 20), D.F64, None,
+                                       ctypes.byref(out)) == -3
+    g.prec = D.F32
+    assert lib.dirac_op_create(7, ctypes.byref(g), ctypes.c_void_p(1 << 20), D.F64, None, ctypes.byref(out)) == -1
