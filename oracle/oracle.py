@@ -226,6 +226,53 @@ def clover(F, csw, psi):
     return -0.5 * csw * out
 
 
+def _shift_links(U, mu, k):
+    """U(n + k mu-hat) for a field shaped (Nt, Nz, Ny, Nx, ...)."""
+    return np.roll(U, -k, axis=3 - mu)
+
+
+def _dag(M):
+    return np.conj(np.swapaxes(M, -1, -2))
+
+
+def _expi_herm(Q):
+    """exp(i Q) of hermitian matrices by eigendecomposition (numpy eigh)."""
+    w, v = np.linalg.eigh(Q)
+    return np.einsum("...ij,...j,...kj->...ik", v, np.exp(1j * w), v.conj())
+
+
+def stout_smear(U, rho=0.12, nsteps=3):
+    """nsteps steps of stout smearing (Morningstar and Peardon, the smearing the
+    paper's V comes from, Sec. 2 and App. F), all links updated at once:
+      C_mu(n) = rho sum_{nu != mu} [ U_nu(n) U_mu(n+nu) U_nu(n+mu)^dag
+                                   + U_nu(n-nu)^dag U_mu(n-nu) U_nu(n-nu+mu) ],
+      Omega = C_mu(n) U_mu(n)^dag,
+      Q = (i/2)(Omega^dag - Omega) - (i/2N) Tr(Omega^dag - Omega),
+      U_mu(n) <- exp(i Q) U_mu(n).
+    Periodic field without boundary phases (closed loops make the step commute
+    with them)."""
+    V = np.array(U, np.complex128)
+    nc = V.shape[-1]
+    for _ in range(nsteps):
+        new = np.empty_like(V)
+        for mu in range(4):
+            Umu = V[..., mu, :, :]
+            C = np.zeros_like(Umu)
+            for nu in range(4):
+                if nu == mu:
+                    continue
+                Unu = V[..., nu, :, :]
+                C += Unu @ _shift_links(Umu, nu, 1) @ _dag(_shift_links(Unu, mu, 1))
+                Unu_b = _shift_links(Unu, nu, -1)
+                C += _dag(Unu_b) @ _shift_links(Umu, nu, -1) @ _shift_links(_shift_links(Unu, nu, -1), mu, 1)
+            Om = rho * C @ _dag(Umu)
+            D = _dag(Om) - Om
+            Q = 0.5j * D - (0.5j / nc) * np.trace(D, axis1=-2, axis2=-1)[..., None, None] * np.eye(nc)
+            new[..., mu, :, :] = _expi_herm(Q) @ Umu
+        V = new
+    return V
+
+
 def gamma5(psi):
     nt, nz, ny, nx, nc, _, nv = psi.shape
     psi = np.ascontiguousarray(psi, np.complex128)

@@ -714,3 +714,95 @@ def test_laplace_flop_counts_app_e():
             assert 12 * O.flops_per_site(kinds[name], int(nc)) == int(f12)
         for n in (1, 2, 3, 4):
             assert O.flops_per_site(kinds[name], n) == eval(poly.replace("^", "**"), {"nc": n})
+
+
+# ------------------------------------------------------------ stout smearing
+
+def test_stout_identity_cases_and_pure_gauge():
+    """rho = 0 or no step leaves U alone; a pure gauge U_mu(n) = g(n) g(n+mu)^dag
+    has every staple equal to its link, so Omega is a multiple of 1 and Q = 0."""
+    dims = (4, 2, 2, 4)
+    U = I.gauge_field(dims, 3, 0.5, seed=81)
+    assert np.array_equal(O.stout_smear(U, 0.12, 0), U)
+    assert np.abs(O.stout_smear(U, 0.0, 2) - U).max() < 1e-15
+    g = I.gauge_transform(dims, 3, seed=82)
+    P = _transform_links(I.unit_gauge_field(dims, 3), g)
+    assert np.abs(O.stout_smear(P, 0.12, 3) - P).max() < 1e-13
+
+
+def test_stout_unitary_covariant_and_phase_commuting():
+    dims = (4, 2, 4, 2)
+    U = I.gauge_field(dims, 3, 0.6, seed=83)
+    V = O.stout_smear(U, 0.12, 3)
+    eye = np.eye(3)
+    assert np.abs(V @ np.conj(np.swapaxes(V, -1, -2)) - eye).max() < 1e-13
+    assert np.abs(np.linalg.det(V) - 1).max() < 1e-13
+    assert np.abs(V - U).max() > 0.05
+    g = I.gauge_transform(dims, 3, seed=84)
+    assert np.abs(O.stout_smear(_transform_links(U, g), 0.12, 3) - _transform_links(V, g)).max() < 1e-12
+    bc = (1, -1, 1, -1)
+    assert np.abs(O.stout_smear(O.phase_links(U, bc), 0.12, 2) -
+                  O.phase_links(O.stout_smear(U, 0.12, 2), bc)).max() < 1e-13
+
+
+def test_stout_abelian_closed_form():
+    """Diagonal links exp(i theta_c) (theta_3 = -theta_1 - theta_2): Omega is
+    diagonal and one step moves every angle by rho sum_nu [sin(forward staple
+    angle - theta) + sin(backward staple angle - theta)], minus the colour
+    average of that shift (the traceless projection); summed here from the
+    link angles with np.roll."""
+    dims = (4, 3, 2, 5)
+    rng = np.random.Generator(np.random.PCG64(85))
+    th = rng.uniform(-1.0, 1.0, (dims[3], dims[2], dims[1], dims[0], 4, 3))
+    th[..., 2] = -th[..., 0] - th[..., 1]
+    U = np.zeros(th.shape[:5] + (3, 3), complex)
+    for c in range(3):
+        U[..., c, c] = np.exp(1j * th[..., c])
+    rho = 0.12
+    V = O.stout_smear(U, rho, 1)
+    axis = {0: 3, 1: 2, 2: 1, 3: 0}
+
+    def sh(a, mu, k):
+        return np.roll(a, -k, axis=axis[mu])
+
+    shift = np.zeros_like(th)
+    for mu in range(4):
+        t = th[..., mu, :]
+        acc = np.zeros_like(t)
+        for nu in range(4):
+            if nu == mu:
+                continue
+            tn = th[..., nu, :]
+            fwd = tn + sh(t, nu, 1) - sh(tn, mu, 1)
+            bwd = -sh(tn, nu, -1) + sh(t, nu, -1) + sh(sh(tn, nu, -1), mu, 1)
+            acc += np.sin(fwd - t) + np.sin(bwd - t)
+        shift[..., mu, :] = rho * acc - rho * acc.mean(axis=-1, keepdims=True)
+    want = np.zeros_like(U)
+    for c in range(3):
+        want[..., c, c] = np.exp(1j * (th[..., c] + shift[..., c]))
+    assert np.abs(V - want).max() < 1e-13
+
+
+def test_stout_smooths_the_plaquette():
+    """Stout smearing raises the average plaquette of a rough field (the
+    purpose of a fat-link background): a sanity property of the oracle."""
+    dims = (4, 4, 4, 4)
+    U = I.gauge_field(dims, 3, 0.6, seed=86)
+
+    def fwd(a, mu):                      # a(n + mu-hat), field axes (t, z, y, x)
+        return np.roll(a, -1, axis=3 - mu)
+
+    def dag(a):
+        return np.conj(np.swapaxes(a, -1, -2))
+
+    def plaq(X):
+        F = 0.0
+        for mu in range(4):
+            for nu in range(mu + 1, 4):
+                P = X[..., mu, :, :] @ fwd(X[..., nu, :, :], mu) @ dag(fwd(X[..., mu, :, :], nu)) @ \
+                    dag(X[..., nu, :, :])
+                F += np.trace(P, axis1=-2, axis2=-1).real.mean() / 3
+        return F / 6
+
+    p0, p3 = plaq(U), plaq(O.stout_smear(U, 0.12, 3))
+    assert p3 > p0 + 0.05
