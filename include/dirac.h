@@ -147,6 +147,23 @@ int dirac_op_update_links(dirac_op *op, const void *U, dirac_prec u_prec, void *
  * Synchronises `stream` before returning. */
 int dirac_op_set_clover(dirac_op *op, double csw, const void *V, dirac_prec v_prec, void *stream);
 
+/* Stout smearing of a gauge field (the fat links V the paper builds D and F
+ * from, Sec. 2 and App. F; rho = 0.12, nsteps = 3 are the paper's defaults,
+ * nsteps = 0 gives V = U).  Each step updates all links at once:
+ *   C_mu(n) = rho sum_{nu != mu} [U_nu(n) U_mu(n+nu) U_nu(n+mu)^dag
+ *                                + U_nu(n-nu)^dag U_mu(n-nu) U_nu(n-nu+mu)],
+ *   Omega = C_mu(n) U_mu(n)^dag,
+ *   Q = (i/2)(Omega^dag - Omega) - (i/2N_c) Tr(Omega^dag - Omega),
+ *   U_mu(n) <- exp(iQ) U_mu(n)
+ * (Morningstar and Peardon).  U_in, V_out: device fields [site][mu][a][b]
+ * complex in prec (F64 or F32), periodic, no boundary phases (the step
+ * commutes with them); they may be the same buffer.  Arithmetic in FP64;
+ * exp(iQ) by scaling and squaring of the Taylor series, for any N_c.  Uses
+ * one temporary field of the same size (allocated and freed here).
+ * Synchronises `stream` before returning. */
+int dirac_stout_smear(const void *U_in, void *V_out, const int dims[4], int nc, dirac_prec prec, double rho,
+                      int nsteps, void *stream);
+
 /* Copy the operator's W links W_s(n) (Brillouin only) into the device
  * buffer w_out (w_bytes long, not overlapping the operator), layout
  * [site][80][a][b] (SITE_OUTER) or [80][a][b][site] (SITE_INNER) in the

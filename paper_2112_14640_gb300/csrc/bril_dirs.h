@@ -54,31 +54,5 @@ __host__ __device__ inline long long w_index(int q, int e, long long n, int nc) 
     return (n * 80 + q) * nc * nc + e;
 }
 
-// The offsets in storage order with the weight of the Brillouin Laplacian on
-// the stored W~: -lambda_k/2 W_s = -c_k s_lead W~_q (Eq. app_blap).
-struct OffsetTable {
-    signed char s[80][4];
-    double lap[80];
-};
-__host__ __device__ constexpr OffsetTable make_offset_table() {
-    OffsetTable t{};
-    int q = 0;
-    for (int m = 1; m < 16; ++m) {
-        const int k = popc4(m);
-        for (int b = 0; b < (1 << k); ++b, ++q) {
-            int j = 0;
-            for (int mu = 0; mu < 4; ++mu) {
-                t.s[q][mu] = 0;
-                if ((m >> mu) & 1) {
-                    t.s[q][mu] = ((b >> j) & 1) ? -1 : 1;
-                    ++j;
-                }
-            }
-            t.lap[q] = -c_lambda(k) * (double)t.s[q][lead_axis(m)];
-        }
-    }
-    return t;
-}
-
 }  // namespace bril
 }  // namespace dgb

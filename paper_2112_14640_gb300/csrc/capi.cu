@@ -316,6 +316,43 @@ int dirac_op_set_clover(dirac_op *op, double csw, const void *V, dirac_prec v_pr
     return rc;
 }
 
+int dirac_stout_smear(const void *U_in, void *V_out, const int dims[4], int nc, dirac_prec prec, double rho,
+                      int nsteps, void *stream) {
+    if (!U_in || !V_out || !dims || nsteps < 0 || nsteps > 1000 || !std::isfinite(rho)) return DIRAC_ERR_INVALID_ARG;
+    for (int m = 0; m < 4; ++m)
+        if (dims[m] < 2) return DIRAC_ERR_INVALID_ARG;
+    if (nc < 1 || nc > 4) return DIRAC_ERR_UNSUPPORTED_NC;
+    if (prec != DIRAC_F64 && prec != DIRAC_F32) return DIRAC_ERR_UNSUPPORTED_PREC;
+    const long long V = (long long)dims[0] * dims[1] * dims[2] * dims[3];
+    if (V > (1LL << 31)) return DIRAC_ERR_INVALID_ARG;
+    const size_t bytes = (size_t)V * 4 * nc * nc * 2 * elem_bytes(prec);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (nsteps == 0)
+        return U_in == V_out ? DIRAC_OK
+                             : cuda_check(cudaMemcpyAsync(V_out, U_in, bytes, cudaMemcpyDeviceToDevice, s), "stout copy");
+    const Lat g{dims[0], dims[1], dims[2], dims[3], 1, V, 0, V};
+    void *tmp = nullptr;
+    int rc = alloc(&tmp, bytes);
+    if (rc) return rc;
+    // steps alternate between V_out and tmp and never write the buffer they
+    // read; an in-place call starts from a copy
+    const void *src = U_in;
+    if (U_in == V_out) {
+        rc = cuda_check(cudaMemcpyAsync(tmp, U_in, bytes, cudaMemcpyDeviceToDevice, s), "stout copy");
+        src = tmp;
+    }
+    for (int i = 0; i < nsteps && !rc; ++i) {
+        void *dst = (src == V_out) ? tmp : V_out;
+        rc = launch_stout_step(src, dst, g, nc, prec, rho, s);
+        src = dst;
+    }
+    if (!rc && src != V_out)
+        rc = cuda_check(cudaMemcpyAsync(V_out, src, bytes, cudaMemcpyDeviceToDevice, s), "stout copy");
+    if (!rc) rc = cuda_check(cudaStreamSynchronize(s), "stout smear");
+    cudaFree(tmp);
+    return rc;
+}
+
 int dirac_op_copy_w(const dirac_op *op, void *w_out, void *stream) {
     if (!op || !w_out || !uses_w(op->kind)) return DIRAC_ERR_INVALID_ARG;
     return launch_unpack_w(op, w_out, (cudaStream_t)stream);

@@ -17,6 +17,35 @@
 #include "internal.h"
 
 namespace dgb {
+namespace bril {
+
+// The offsets in storage order with the weight of the Brillouin Laplacian on
+// the stored W~: -lambda_k/2 W_s = -c_k s_lead W~_q (Eq. app_blap).
+struct OffsetTable {
+    signed char s[80][4];
+    double lap[80];
+};
+__host__ __device__ constexpr OffsetTable make_offset_table() {
+    OffsetTable t{};
+    int q = 0;
+    for (int m = 1; m < 16; ++m) {
+        const int k = popc4(m);
+        for (int b = 0; b < (1 << k); ++b, ++q) {
+            int j = 0;
+            for (int mu = 0; mu < 4; ++mu) {
+                t.s[q][mu] = 0;
+                if ((m >> mu) & 1) {
+                    t.s[q][mu] = ((b >> j) & 1) ? -1 : 1;
+                    ++j;
+                }
+            }
+            t.lap[q] = -c_lambda(k) * (double)t.s[q][lead_axis(m)];
+        }
+    }
+    return t;
+}
+
+}  // namespace bril
 
 static __constant__ bril::OffsetTable kLapOffsets = bril::make_offset_table();
 

@@ -74,6 +74,7 @@ SIGNATURES = {
     "dirac_op_update_links": (_I, [_P, _P, _I, _P]),
     "dirac_op_copy_w": (_I, [_P, _P, _P]),
     "dirac_op_set_clover": (_I, [_P, _D, _P, _I, _P]),
+    "dirac_stout_smear": (_I, [_P, _P, ctypes.POINTER(_I), _I, _I, _D, _I, _P]),
     "dirac_op_destroy": (None, [_P]),
     "dirac_apply": (_I, [_P, _P, _P, _D, _P]),
     "dirac_apply_dagger": (_I, [_P, _P, _P, _D, _P]),
@@ -126,6 +127,23 @@ def error_string(code):
 
 def flops_per_site(kind, nc):
     return int(lib().dirac_flops_per_site(int(kind), int(nc)))
+
+
+def stout_smear(U, rho=0.12, nsteps=3, out=None, stream=None):
+    """nsteps steps of stout smearing of the gauge field U (CUDA tensor,
+    complex128 or complex64, (Nt, Nz, Ny, Nx, 4, Nc, Nc), no boundary
+    phases); returns V (a new tensor, or ``out``, which may be U itself)."""
+    if not U.is_cuda or U.dtype not in (torch.complex128, torch.complex64) or not U.is_contiguous():
+        raise ValueError("U must be a contiguous complex128 or complex64 CUDA tensor")
+    nt, nz, ny, nx = U.shape[:4]
+    out = torch.empty_like(U) if out is None else out
+    if out.shape != U.shape or out.dtype != U.dtype or not out.is_contiguous():
+        raise ValueError("out must match U")
+    dims = (ctypes.c_int * 4)(nx, ny, nz, nt)
+    prec = F64 if U.dtype == torch.complex128 else F32
+    _check(lib().dirac_stout_smear(_ptr(U), _ptr(out), dims, int(U.shape[-1]), prec, float(rho), int(nsteps),
+                                   _stream(stream)), "dirac_stout_smear")
+    return out
 
 
 def clover_flops_per_site(nc):

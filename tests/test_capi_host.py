@@ -132,3 +132,14 @@ def test_laplace_kinds_flops_and_validation(lib):
                                        ctypes.byref(out)) == -3
     g.prec = D.F32
     assert lib.dirac_op_create(7, ctypes.byref(g), ctypes.c_void_p(1 << 20), D.F64, None, ctypes.byref(out)) == -1
+
+
+def test_stout_smear_validates_without_device(lib):
+    dims = (ctypes.c_int * 4)(4, 4, 4, 4)
+    bad = (ctypes.c_int * 4)(4, 1, 4, 4)
+    p = ctypes.c_void_p(1 << 20)
+    assert lib.dirac_stout_smear(None, p, dims, 3, D.F64, 0.12, 3, None) == -1
+    assert lib.dirac_stout_smear(p, p, bad, 3, D.F64, 0.12, 3, None) == -1
+    assert lib.dirac_stout_smear(p, p, dims, 3, D.F64, 0.12, -1, None) == -1
+    assert lib.dirac_stout_smear(p, p, dims, 5, D.F64, 0.12, 3, None) == -2
+    assert lib.dirac_stout_smear(p, p, dims, 3, D.BF16, 0.12, 3, None) == -3
