@@ -98,8 +98,10 @@ def ncu_traffic(op_name):
     try:
         text = open(prof).read()
         h = hashlib.sha256()
-        srcs = ("%s.cuh" % op_name,) + (("bril_dirs.h",) if op_name == "brillouin" else ()) + \
-            (("clover.cuh",) if op_name != "staggered" else ()) + ("common.cuh",)
+        srcs = {"wilson": ("wilson.cuh", "clover.cuh"), "staggered": ("staggered.cuh",),
+                "brillouin": ("brillouin.cuh", "bril_dirs.h", "clover.cuh"),
+                "wlap": ("laplace.cuh", "bril_dirs.h"), "blap": ("laplace.cuh", "bril_dirs.h")}[op_name] + \
+            ("common.cuh",)
         for f in srcs:
             h.update(open(os.path.join(csrc, f), "rb").read())
         fields = dict(l.split(":", 1) for l in text.splitlines() if ":" in l and not l.startswith(("#", " ", "|")))
@@ -268,7 +270,7 @@ def main():
     U = torch.from_numpy(U_np).cuda()
     names = {v: k for k, v in D.KIND_NAMES.items()}
     kinds = tuple(names[o] for o in args.ops.split(","))
-    sources = {k: I.source(DIMS, NC, NV, 4321 + k, staggered=(k == D.STAGGERED)) for k in kinds}
+    sources = {k: I.source(DIMS, NC, NV, 4321 + k, staggered=(k in (D.STAGGERED, D.WSUV, D.BSUV))) for k in kinds}
     ops, xs, ys = {}, {}, {}
     launch, layout_ms = {}, {}
     stream0 = torch.cuda.current_stream()
@@ -520,6 +522,7 @@ def laplace_measurement(D, U, pk, fp32_peak, quick_ms, m=0.1):
             "ms": ms, "gflops": flop / (ms * 1e-3) / 1e9, "alg_GBps": gbytes / (ms * 1e-3),
             "bound": "alu" if alu else "hbm",
             "frac": (flop / (ms * 1e-3) / 1e12 / fp32_peak) if alu else gbytes / (ms * 1e-3) / pk["hbm"],
+            "traffic": ncu_traffic(D.KIND_NAMES[k]) if k in (D.WLAP, D.BLAP) else None,
             "launch": op.get_launch()}
         op.close()
         del x, y
