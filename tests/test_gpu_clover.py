@@ -224,3 +224,20 @@ def test_clover_lifetime_and_refusals():
     with pytest.raises(D.DiracError):
         st.set_clover(1.0, Ut)
     st.close()
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("prec", [D.F64, D.F32])
+def test_clover_extreme_shapes(kind, prec):
+    """N_v = 64 on the 2^4 lattice (every plaquette leaf wraps onto the same
+    links; forward and backward neighbours coincide), and one RHS with N_c = 4
+    on a lattice long in t, both layouts."""
+    for layout in LAYOUTS:
+        for dims, nc, nv, bc in (((2, 2, 2, 2), 3, 64, (1, 1, 1, -1)), ((2, 2, 2, 34), 4, 1, (-1, 1, 1, -1))):
+            op, ref, src = make(kind, dims, nc, nv, bc, prec, csw=1.5, layout=layout)
+            x = to_device(op, src)
+            for dag in (False, True):
+                got = to_numpy(op, op.apply(x, m0=0.1, dagger=dag))
+                want = ref.apply_dagger(src, 0.1) if dag else ref.apply(src, 0.1)
+                assert rel_l2(got, want) <= TOL[prec], (kind, dims, nv, dag, layout)
+            op.close()

@@ -185,3 +185,16 @@ def test_laplace_argument_rules():
     assert torch.equal(a.copy_w(), b.copy_w())
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("prec", [D.F64, D.F32])
+def test_laplace_extreme_shapes(kind, prec):
+    """N_v = 64 on the 2^4 lattice and one RHS with N_c = 4 on a lattice long
+    in t, both layouts."""
+    for layout in LAYOUTS:
+        for dims, nc, nv, bc in (((2, 2, 2, 2), 3, 64, (1, 1, 1, -1)), ((2, 2, 2, 34), 4, 1, (-1, 1, 1, -1))):
+            op, ref, src = make(kind, dims, nc, nv, bc, prec, layout=layout)
+            x = to_device(op, src)
+            assert rel_l2(to_numpy(op, op.apply(x, m0=0.2)), ref.apply(src, 0.2)) <= TOL[prec], (kind, dims, layout)
+            op.close()

@@ -65,3 +65,12 @@ def test_operators_on_smeared_field_with_clover(kind):
         want = ref.apply_dagger(src, -0.1) if dag else ref.apply(src, -0.1)
         assert rel_l2(got, want) <= TOL[D.F64]
     op.close()
+
+
+def test_stout_extent_two():
+    """Extent 2 in every direction: a link's forward and backward staples
+    share links, and n + mu - nu wraps twice."""
+    U = I.gauge_field((2, 2, 2, 2), 3, 0.7, seed=97)
+    want = O.stout_smear(U, 0.12, 3)
+    got = D.stout_smear(torch.from_numpy(U).cuda(), 0.12, 3).cpu().numpy()
+    assert rel_l2(got, want) < 1e-12
