@@ -603,6 +603,44 @@ def wilson_force_terms(op, psi, chi):
     return B, C
 
 
+def staggered_force_terms(op, phi, chi):
+    """(B, C) per link for S = sum_v Re phi_v^dag (D_S^dag D_S)^-1 phi_v, from
+    psi = (D^dag D)^-1 phi (here ``phi``) and chi = D psi, derived from
+    Eq. (def_stag): dS = -2 Re <chi, dD psi> and the two hops through U_mu(n)
+    give dS = Re sum tr[dU (B + C^dag)] with
+      B_mu(n) = -eta_mu(n) sum_v psi(n+mu) chi(n)^dag,
+      C_mu(n) =  eta_mu(n) sum_v psi(n) chi(n+mu)^dag
+    (eta_mu depends only on the coordinates before mu, so eta_mu(n+mu) =
+    eta_mu(n)).  Colour-vector fields (Nt, Nz, Ny, Nx, Nc, Nv)."""
+    nt, nz, ny, nx = phi.shape[:4]
+    t, z, y, x = np.meshgrid(np.arange(nt), np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    co = [x, y, z, t]
+    sh = phi.shape[:4] + (4, phi.shape[4], phi.shape[4])
+    B = np.empty(sh, np.complex128)
+    C = np.empty(sh, np.complex128)
+    for mu in range(4):
+        e = sum(co[nu] + 1 for nu in range(mu))
+        eta = np.where(np.asarray(e) % 2 == 1, -1.0, 1.0)[..., None, None]
+        fwd = lambda v: np.roll(v, -1, axis=3 - mu)
+        B[..., mu, :, :] = -eta * np.einsum("...av,...bv->...ab", fwd(phi), np.conj(chi))
+        C[..., mu, :, :] = eta * np.einsum("...av,...bv->...ab", phi, np.conj(fwd(chi)))
+    return B, C
+
+
+def staggered_force(op, psi, chi):
+    """F_mu(n) = P_TA(U B - C U^dag) with the staggered B, C and phased links."""
+    B, C = staggered_force_terms(op, psi, chi)
+    U = op.Up
+    return project_ta(U @ B - C @ np.conj(np.swapaxes(U, -1, -2)))
+
+
+def staggered_action_gradient(op, psi, chi):
+    """G with dS = Re sum conj(G) dU for the unphased links: bc-phase * (B^dag + C)."""
+    B, C = staggered_force_terms(op, psi, chi)
+    ph = phase_links(np.ones(op.Up.shape, np.complex128), op.bc)
+    return (np.conj(np.swapaxes(B, -1, -2)) + C) * ph
+
+
 def project_ta(M):
     """Traceless anti-hermitian part of each colour matrix."""
     A = 0.5 * (M - np.conj(np.swapaxes(M, -1, -2)))

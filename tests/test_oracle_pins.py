@@ -806,3 +806,47 @@ def test_stout_smooths_the_plaquette():
 
     p0, p3 = plaq(U), plaq(O.stout_smear(U, 0.12, 3))
     assert p3 > p0 + 0.05
+
+
+# ------------------------------------------------------ staggered fermion force
+
+@pytest.mark.parametrize("bc", [(1, 1, 1, 1), (1, 1, 1, -1)])
+def test_staggered_force_matches_finite_differences(bc):
+    """S = sum Re phi^dag (D_S^dag D_S)^-1 phi: dS/deps along U -> exp(eps X) U
+    equals Re sum tr[X F] (central differences, eps = 1e-4, FP64 solves; the
+    mass keeps the O(eps^2) truncation of the difference below 1e-6)."""
+    dims = (4, 2, 2, 4)
+    m0 = 0.4
+    U = I.gauge_field(dims, 3, 0.4, seed=121)
+    phi = I.source(dims, 3, 2, seed=122, staggered=True)
+    op = O.Operator(O.STAGGERED, U, bc, m0)
+    S0, psi = O.pseudofermion_action(op, phi)
+    F = O.staggered_force(op, psi, op.apply(psi))
+    assert np.allclose(F, -np.conj(np.swapaxes(F, -1, -2)), atol=1e-14)
+    assert np.abs(np.trace(F, axis1=-2, axis2=-1)).max() < 1e-13
+    eps = 1e-4
+    for seed in range(4):
+        X = I.su_n_direction(dims, 3, seed=300 + seed)
+        Sp, _ = O.pseudofermion_action(O.Operator(O.STAGGERED, _expm_ah(eps * X) @ U, bc, m0), phi)
+        Sm, _ = O.pseudofermion_action(O.Operator(O.STAGGERED, _expm_ah(-eps * X) @ U, bc, m0), phi)
+        fd = (Sp - Sm) / (2 * eps)
+        an = np.sum(np.real(np.einsum("...ab,...ba->...", X, F)))
+        assert abs(fd - an) < 1e-6 * max(abs(an), 1.0), (seed, fd, an)
+
+
+def test_staggered_action_gradient_matches_finite_differences():
+    dims = (2, 2, 2, 4)
+    m0, bc = 0.3, (1, 1, 1, -1)
+    U = I.gauge_field(dims, 3, 0.4, seed=131)
+    phi = I.source(dims, 3, 1, seed=132, staggered=True)
+    op = O.Operator(O.STAGGERED, U, bc, m0)
+    S0, psi = O.pseudofermion_action(op, phi)
+    G = O.staggered_action_gradient(op, psi, op.apply(psi))
+    rng = np.random.default_rng(6)
+    dU = rng.standard_normal(U.shape) + 1j * rng.standard_normal(U.shape)
+    eps = 1e-5
+    Sp, _ = O.pseudofermion_action(O.Operator(O.STAGGERED, U + eps * dU, bc, m0), phi)
+    Sm, _ = O.pseudofermion_action(O.Operator(O.STAGGERED, U - eps * dU, bc, m0), phi)
+    fd = (Sp - Sm) / (2 * eps)
+    an = float(np.sum(np.real(np.conj(G) * dU)))
+    assert abs(fd - an) < 1e-6 * abs(an)
