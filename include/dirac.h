@@ -345,19 +345,24 @@ int dirac_solve_batched(int nsolves, dirac_op *const *ops, const void *const *b,
                         void *stream);
 
 /* ------------------------------------------------------------ fermion force
- * Derivative of S = sum_v Re phi_v^dag (D_W^dag D_W)^-1 phi_v with respect to
- * the links (the paper has no force; derived from Eq. app_wils, so an
- * operator with a clover term is refused).  Inputs:
- * psi = (D^dag D)^-1 phi and chi = D psi, Wilson-type vectors of op (F64 or
- * F32).  Output: [site][mu][a][b] complex in op precision.
+ * Derivative of S = sum_v Re phi_v^dag (D^dag D)^-1 phi_v with respect to
+ * the links, for D = D_W (Eq. app_wils) or D_S (Eq. def_stag) (the paper has
+ * no force; derived here, without the clover term, so an operator carrying
+ * one is refused).  Inputs: psi = (D^dag D)^-1 phi and chi = D psi, vectors of
+ * op (F64 or F32).  Output: [site][mu][a][b] complex in op precision.
  *   mode DIRAC_FORCE_TA:   F_mu(n) = P_TA(U B - C U^dag), traceless
  *                          anti-hermitian, with dS/deps = Re sum tr[X F] for
  *                          U -> exp(eps X) U, X in su(Nc);
  *   mode DIRAC_FORCE_GRAD: G with dS = Re sum conj(G) dU for an arbitrary
  *                          complex change dU of the caller's (unphased) links,
- * where B_mu(n) = sum psi(n+mu) [(1-gamma_mu) chi(n)]^dag and
- * C_mu(n) = sum psi(n) [(1+gamma_mu) chi(n+mu)]^dag, summed over spin and RHS. */
+ * where, summed over spin and RHS,
+ *   D_W: B_mu(n) = sum psi(n+mu) [(1-gamma_mu) chi(n)]^dag,
+ *        C_mu(n) = sum psi(n) [(1+gamma_mu) chi(n+mu)]^dag;
+ *   D_S: B_mu(n) = -eta_mu(n) sum psi(n+mu) chi(n)^dag,
+ *        C_mu(n) =  eta_mu(n) sum psi(n) chi(n+mu)^dag. */
 enum { DIRAC_FORCE_TA = 0, DIRAC_FORCE_GRAD = 1 };
+int dirac_force(const dirac_op *op, const void *psi, const void *chi, void *force_out, int mode, void *stream);
+/* dirac_force restricted to D_W (DIRAC_ERR_INVALID_ARG for other kinds). */
 int dirac_force_wilson(const dirac_op *op, const void *psi, const void *chi, void *force_out, int mode,
                        void *stream);
 

@@ -1,14 +1,14 @@
 """torch.autograd wrapper of the pseudofermion action
 
-    S(U, phi) = sum_v Re phi_v^dag (D_W^dag D_W)^-1 phi_v
+    S(U, phi) = sum_v Re phi_v^dag (D^dag D)^-1 phi_v,   D = D_W or D_S
 
-(the paper has no differentiation; this grows its Wilson operator and CG
-solver into a differentiable layer).  Forward: one CG solve of
+(the paper has no differentiation; this grows its Wilson and staggered
+operators and CG solver into a differentiable layer).  Forward: one CG solve of
 D^dag D psi = phi (``dirac_solve`` with DIRAC_CG_HPD) and S = Re <phi, psi>
 from the library's dot product.  Backward: the adjoint solve, recomputed
 instead of stored (D^dag D is Hermitian, so the adjoint system is the forward
 one; no Krylov vectors are kept between the passes), then chi = D psi and the
-link gradient from ``dirac_force_wilson``:
+link gradient from ``dirac_force``:
 
     dS/dU   = G   with dS = Re sum conj(G) dU     (torch's convention for complex inputs)
     dS/dphi = 2 psi
@@ -51,12 +51,16 @@ class _Action(torch.autograd.Function):
 
 
 class PseudofermionAction:
-    """Differentiable S(U, phi) for the Wilson operator on one lattice shape.
+    """Differentiable S(U, phi) for the Wilson (default) or staggered operator
+    on one lattice shape.
 
     The operator handle is created on first use and its links refreshed from
     U on every call (``dirac_op_update_links``)."""
 
-    def __init__(self, m0, bc=(1, 1, 1, 1), prec=D.F32, tol=1e-8, maxit=20000, save_solution=False):
+    def __init__(self, m0, bc=(1, 1, 1, 1), prec=D.F32, tol=1e-8, maxit=20000, save_solution=False, kind=D.WILSON):
+        if kind not in (D.WILSON, D.STAGGERED):
+            raise ValueError("the force is derived for D_W and D_S")
+        self.kind = kind
         self.m0, self.bc, self.prec = float(m0), tuple(bc), prec
         self.tol, self.maxit, self.save_solution = tol, maxit, save_solution
         self.op = None
@@ -65,7 +69,7 @@ class PseudofermionAction:
     def op_for(self, U, phi, prec, bc):
         nv = phi.shape[-1]
         if self.op is None or self.op.nv != nv or self.op.dims != (U.shape[3], U.shape[2], U.shape[1], U.shape[0]):
-            self.op = D.DiracOp(D.WILSON, U.detach(), nv, bc, prec)
+            self.op = D.DiracOp(self.kind, U.detach(), nv, bc, prec)
         else:
             self.op.update_links(U.detach())
         return self.op

@@ -11,6 +11,11 @@
 //            caller's (unphased) links.
 // One thread per (site, mu); the (1 +- gamma_mu) projections use the chiral
 // gammas of App. A; everything accumulates in the operator's arithmetic type.
+//
+// The staggered operator (Eq. def_stag) gives the same final form with
+//   B_mu(n) = -eta_mu(n) sum psi(n+mu) chi(n)^dag,  C_mu(n) = eta_mu(n) sum psi(n) chi(n+mu)^dag
+// (colour vectors, RHS summed; eta_mu(n+mu) = eta_mu(n) because eta_mu only
+// depends on the coordinates before mu).
 #include "internal.h"
 
 namespace dgb {
@@ -46,43 +51,14 @@ __device__ __forceinline__ void apply_proj(int mu, A a, const cx<A> p[4], cx<A> 
     }
 }
 
+// F = P_TA(U B - C U^dag) (mode 0) or G = bc (B^dag + C) (mode 1) for link (n, mu)
 template <int NC, typename E, int LAYOUT>
-__global__ void force_kernel(const E *__restrict__ U, const E *__restrict__ psi, const E *__restrict__ chi,
-                             E *__restrict__ out, Lat g, int bc0, int bc1, int bc2, int bc3, int mode) {
+__device__ __forceinline__ void force_out(const E *__restrict__ U, E *__restrict__ out, const Lat &g, long long tid,
+                                          long long n, int mu, const Coord &c, const cx<typename Acc<E>::T> (&B)[NC][NC],
+                                          const cx<typename Acc<E>::T> (&C)[NC][NC], int bc0, int bc1, int bc2, int bc3,
+                                          int mode) {
     using L = Layout<LAYOUT>;
     using A = typename Acc<E>::T;
-    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid >= g.V * 4) return;
-    const long long n = tid / 4;
-    const int mu = (int)(tid % 4);
-    const Coord c = site_coords(g, n);
-    const long long m = neighbour(g, n, c, mu, +1);
-    const long long csd = L::cs_stride(g);
-    cx<A> B[NC][NC], C[NC][NC];
-    for (int a = 0; a < NC; ++a)
-        for (int b = 0; b < NC; ++b) B[a][b] = C[a][b] = cx<A>{0, 0};
-    for (int v = 0; v < g.nv; ++v) {
-        cx<A> pn[NC][4], pm[NC][4], qn[NC][4], qm[NC][4];
-        for (int a = 0; a < NC; ++a) {
-            cx<A> cn[4], cm[4];
-            for (int s = 0; s < 4; ++s) {
-                const long long on = 2 * (L::vec(g, n, NC * 4, 0) + (long long)(a * 4 + s) * csd + v);
-                const long long om = 2 * (L::vec(g, m, NC * 4, 0) + (long long)(a * 4 + s) * csd + v);
-                pn[a][s] = ld1<E, A>(psi + on);
-                pm[a][s] = ld1<E, A>(psi + om);
-                cn[s] = ld1<E, A>(chi + on);
-                cm[s] = ld1<E, A>(chi + om);
-            }
-            apply_proj<A>(mu, (A)-1, cn, qn[a]);   // (1 - gamma_mu) chi(n)
-            apply_proj<A>(mu, (A)1, cm, qm[a]);    // (1 + gamma_mu) chi(n+mu)
-        }
-        for (int a = 0; a < NC; ++a)
-            for (int b = 0; b < NC; ++b)
-                for (int s = 0; s < 4; ++s) {
-                    cmac(B[a][b], pm[a][s], conj(qn[b][s]));
-                    cmac(C[a][b], pn[a][s], conj(qm[b][s]));
-                }
-    }
     E *o = out + 2 * (tid * NC * NC);
     if (mode == 1) {   // G = bc (B^dag + C)
         const int coord = mu == 0 ? c.x : mu == 1 ? c.y : mu == 2 ? c.z : c.t;
@@ -122,18 +98,102 @@ __global__ void force_kernel(const E *__restrict__ U, const E *__restrict__ psi,
         }
 }
 
+template <int NC, typename E, int LAYOUT>
+__global__ void force_kernel(const E *__restrict__ U, const E *__restrict__ psi, const E *__restrict__ chi,
+                             E *__restrict__ out, Lat g, int bc0, int bc1, int bc2, int bc3, int mode) {
+    using L = Layout<LAYOUT>;
+    using A = typename Acc<E>::T;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= g.V * 4) return;
+    const long long n = tid / 4;
+    const int mu = (int)(tid % 4);
+    const Coord c = site_coords(g, n);
+    const long long m = neighbour(g, n, c, mu, +1);
+    const long long csd = L::cs_stride(g);
+    cx<A> B[NC][NC], C[NC][NC];
+    for (int a = 0; a < NC; ++a)
+        for (int b = 0; b < NC; ++b) B[a][b] = C[a][b] = cx<A>{0, 0};
+    for (int v = 0; v < g.nv; ++v) {
+        cx<A> pn[NC][4], pm[NC][4], qn[NC][4], qm[NC][4];
+        for (int a = 0; a < NC; ++a) {
+            cx<A> cn[4], cm[4];
+            for (int s = 0; s < 4; ++s) {
+                const long long on = 2 * (L::vec(g, n, NC * 4, 0) + (long long)(a * 4 + s) * csd + v);
+                const long long om = 2 * (L::vec(g, m, NC * 4, 0) + (long long)(a * 4 + s) * csd + v);
+                pn[a][s] = ld1<E, A>(psi + on);
+                pm[a][s] = ld1<E, A>(psi + om);
+                cn[s] = ld1<E, A>(chi + on);
+                cm[s] = ld1<E, A>(chi + om);
+            }
+            apply_proj<A>(mu, (A)-1, cn, qn[a]);   // (1 - gamma_mu) chi(n)
+            apply_proj<A>(mu, (A)1, cm, qm[a]);    // (1 + gamma_mu) chi(n+mu)
+        }
+        for (int a = 0; a < NC; ++a)
+            for (int b = 0; b < NC; ++b)
+                for (int s = 0; s < 4; ++s) {
+                    cmac(B[a][b], pm[a][s], conj(qn[b][s]));
+                    cmac(C[a][b], pn[a][s], conj(qm[b][s]));
+                }
+    }
+    force_out<NC, E, LAYOUT>(U, out, g, tid, n, mu, c, B, C, bc0, bc1, bc2, bc3, mode);
+}
+
+template <int NC, typename E, int LAYOUT>
+__global__ void force_stag_kernel(const E *__restrict__ U, const E *__restrict__ psi, const E *__restrict__ chi,
+                                  E *__restrict__ out, Lat g, int bc0, int bc1, int bc2, int bc3, int mode) {
+    using L = Layout<LAYOUT>;
+    using A = typename Acc<E>::T;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= g.V * 4) return;
+    const long long n = tid / 4;
+    const int mu = (int)(tid % 4);
+    const Coord c = site_coords(g, n);
+    const long long m = neighbour(g, n, c, mu, +1);
+    const long long csd = L::cs_stride(g);
+    // eta_mu(n) = (-1)^(sum_{nu<mu} (x_nu + 1)), the paper's 1-based convention
+    const int e[4] = {0, c.x + 1, c.x + c.y + 2, c.x + c.y + c.z + 3};
+    const A eta = (e[mu] & 1) ? (A)-1 : (A)1;
+    cx<A> B[NC][NC], C[NC][NC];
+    for (int a = 0; a < NC; ++a)
+        for (int b = 0; b < NC; ++b) B[a][b] = C[a][b] = cx<A>{0, 0};
+    for (int v = 0; v < g.nv; ++v) {
+        cx<A> pn[NC], pm[NC], cn[NC], cm[NC];
+        for (int a = 0; a < NC; ++a) {
+            const long long on = 2 * (L::vec(g, n, NC, 0) + (long long)a * csd + v);
+            const long long om = 2 * (L::vec(g, m, NC, 0) + (long long)a * csd + v);
+            pn[a] = ld1<E, A>(psi + on);
+            pm[a] = ld1<E, A>(psi + om);
+            cn[a] = ld1<E, A>(chi + on);
+            cm[a] = ld1<E, A>(chi + om);
+        }
+        for (int a = 0; a < NC; ++a)
+            for (int b = 0; b < NC; ++b) {
+                cmac(B[a][b], pm[a], conj(cn[b]));
+                cmac(C[a][b], pn[a], conj(cm[b]));
+            }
+    }
+    for (int a = 0; a < NC; ++a)
+        for (int b = 0; b < NC; ++b) {
+            B[a][b] = (-eta) * B[a][b];
+            C[a][b] = eta * C[a][b];
+        }
+    force_out<NC, E, LAYOUT>(U, out, g, tid, n, mu, c, B, C, bc0, bc1, bc2, bc3, mode);
+}
+
 }  // namespace dgb
 
 using namespace dgb;
 
-extern "C" int dirac_force_wilson(const dirac_op *op, const void *psi, const void *chi, void *force_out, int mode,
-                                  void *stream) {
+extern "C" int dirac_force(const dirac_op *op, const void *psi, const void *chi, void *force_out, int mode,
+                           void *stream) {
     if (!op || !psi || !chi || !force_out) return DIRAC_ERR_INVALID_ARG;
-    if (op->kind != DIRAC_WILSON || (mode != 0 && mode != 1)) return DIRAC_ERR_INVALID_ARG;
-    if (op->clover) return DIRAC_ERR_INVALID_ARG;   // derived for D_W without the clover term
+    if ((op->kind != DIRAC_WILSON && op->kind != DIRAC_STAGGERED) || (mode != 0 && mode != 1))
+        return DIRAC_ERR_INVALID_ARG;
+    if (op->clover) return DIRAC_ERR_INVALID_ARG;   // derived without the clover term
     if (((uintptr_t)psi & 15) || ((uintptr_t)chi & 15)) return DIRAC_ERR_ALIGNMENT;
     if (op->prec != DIRAC_F64 && op->prec != DIRAC_F32) return DIRAC_ERR_UNSUPPORTED_PREC;
     cudaStream_t s = (cudaStream_t)stream;
+    const bool stag = op->kind == DIRAC_STAGGERED;
     return dispatch_prec(op->prec, [&](auto tag) {
         using E = std::remove_pointer_t<decltype(tag)>;
         if constexpr (sizeof(E) == 2) {
@@ -144,12 +204,24 @@ extern "C" int dirac_force_wilson(const dirac_op *op, const void *psi, const voi
                 return dispatch_layout(op->geom.layout, [&](auto lyc) {
                     constexpr int LAYOUT = decltype(lyc)::value;
                     const long long threads = op->V * 4;
-                    force_kernel<NC, E, LAYOUT><<<grid_for(threads, 128), 128, 0, s>>>(
-                        (const E *)op->links, (const E *)psi, (const E *)chi, (E *)force_out, op->lat,
-                        op->geom.bc[0], op->geom.bc[1], op->geom.bc[2], op->geom.bc[3], mode);
-                    return launch_check("force_kernel");
+                    const int *bc = op->geom.bc;
+                    if (stag)
+                        force_stag_kernel<NC, E, LAYOUT><<<grid_for(threads, 128), 128, 0, s>>>(
+                            (const E *)op->links, (const E *)psi, (const E *)chi, (E *)force_out, op->lat, bc[0],
+                            bc[1], bc[2], bc[3], mode);
+                    else
+                        force_kernel<NC, E, LAYOUT><<<grid_for(threads, 128), 128, 0, s>>>(
+                            (const E *)op->links, (const E *)psi, (const E *)chi, (E *)force_out, op->lat, bc[0],
+                            bc[1], bc[2], bc[3], mode);
+                    return launch_check(stag ? "force_stag_kernel" : "force_kernel");
                 });
             });
         }
     });
+}
+
+extern "C" int dirac_force_wilson(const dirac_op *op, const void *psi, const void *chi, void *force_out, int mode,
+                                  void *stream) {
+    if (op && op->kind != DIRAC_WILSON) return DIRAC_ERR_INVALID_ARG;
+    return dirac_force(op, psi, chi, force_out, mode, stream);
 }

@@ -92,6 +92,7 @@ SIGNATURES = {
     "dirac_vec_norm2_noalloc": (_I, [_P, _I, ctypes.c_longlong, _I, _P, _P]),
     "dirac_solve": (_I, [_P, _P, _P, _D, ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats), _P]),
     "dirac_force_wilson": (_I, [_P, _P, _P, _P, _I, _P]),
+    "dirac_force": (_I, [_P, _P, _P, _P, _I, _P]),
     "dirac_solve_batched": (_I, [_I, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P),
                                  ctypes.POINTER(_D), ctypes.POINTER(SolveParams), ctypes.POINTER(SolveStats), _P]),
     "dirac_error_string": (ctypes.c_char_p, [_I]),
@@ -377,12 +378,12 @@ class DiracOp:
         return dst
 
     def force(self, psi, chi, mode=FORCE_TA, stream=None):
-        """Link derivative of S = sum Re phi^dag (D^dag D)^-1 phi (Wilson only):
+        """Link derivative of S = sum Re phi^dag (D^dag D)^-1 phi (Wilson or staggered):
         (Nt, Nz, Ny, Nx, 4, Nc, Nc) complex, from psi = (D^dag D)^-1 phi, chi = D psi."""
         nx, ny, nz, nt = self.dims
         out = torch.empty((nt, nz, ny, nx, 4, self.nc, self.nc), dtype=_TORCH_DTYPE[self.prec], device=self.device)
-        _check(lib().dirac_force_wilson(self._h, self._vec(psi, "psi"), self._vec(chi, "chi"), _ptr(out), int(mode),
-                                        _stream(stream)), "dirac_force_wilson")
+        _check(lib().dirac_force(self._h, self._vec(psi, "psi"), self._vec(chi, "chi"), _ptr(out), int(mode),
+                                 _stream(stream)), "dirac_force")
         return out
 
     # ---------------------------------------------------------------- solve

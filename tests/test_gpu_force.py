@@ -83,3 +83,54 @@ def test_config5_finite_differences_16x16x16x32():
         fd = (Sp - Sm) / (2 * eps)
         an = torch.einsum("...ab,...ba->...", X, F64).real.sum().item()
         assert abs(fd - an) < 1e-5 * abs(an), (k, fd, an)
+
+
+@pytest.mark.parametrize("layout", [D.SITE_OUTER, D.SITE_INNER])
+@pytest.mark.parametrize("prec,tol", [(D.F64, 1e-10), (D.F32, 1e-5)])
+@pytest.mark.parametrize("bc", [(1, 1, 1, 1), (1, -1, 1, -1)])
+def test_staggered_force_kernel_matches_oracle(prec, tol, bc, layout):
+    """The staggered force (derived from Eq. def_stag) against the oracle's,
+    both modes, on the same solution vector."""
+    dims, nc, nv, m0 = (4, 4, 2, 6), 3, 3, 0.2
+    U = I.gauge_field(dims, nc, 0.4, 43)
+    op = D.DiracOp(D.STAGGERED, torch.from_numpy(U).cuda(), nv, bc, prec, layout=layout)
+    ref = O.Operator(D.STAGGERED, U, bc)
+    psi = I.source(dims, nc, nv, 44, staggered=True)
+    x = to_device(op, psi)
+    chi = op.apply(x, m0=m0)
+    got_ta = op.force(x, chi, D.FORCE_TA).to(torch.complex128).cpu().numpy()
+    got_g = op.force(x, chi, D.FORCE_GRAD).to(torch.complex128).cpu().numpy()
+    chi_ref = ref.apply(psi, m0)
+    assert rel_l2(got_ta, O.staggered_force(ref, psi, chi_ref)) <= tol
+    assert rel_l2(got_g, O.staggered_action_gradient(ref, psi, chi_ref)) <= tol
+    op.close()
+
+
+def test_staggered_autograd_and_finite_differences():
+    """Autograd of S = sum Re phi^dag (D_S^dag D_S)^-1 phi against the oracle's
+    gradient, and the GPU force against central differences of the GPU action
+    along random su(3) directions (FP64, 8^4, N_v = 3)."""
+    dims, nc, nv, m0, bc = (8, 8, 8, 8), 3, 3, 0.3, (1, 1, 1, -1)
+    U_np = I.gauge_field(dims, nc, 0.4, 53)
+    phi_np = I.source(dims, nc, nv, 54, staggered=True)
+    U = torch.from_numpy(U_np).cuda().requires_grad_(True)
+    phi = torch.from_numpy(phi_np).cuda().requires_grad_(True)
+    act = PseudofermionAction(m0, bc, prec=D.F64, tol=1e-13, kind=D.STAGGERED)
+    S = act(U, phi)
+    gU, gphi = torch.autograd.grad(S, (U, phi))
+    ref = O.Operator(D.STAGGERED, U_np, bc)
+    S_ref, psi = O.pseudofermion_action(ref, phi_np, m0)
+    assert abs(S.item() - S_ref) < 1e-11 * abs(S_ref)
+    assert rel_l2(gU.cpu().numpy(), O.staggered_action_gradient(ref, psi, ref.apply(psi, m0))) < 1e-10
+    assert rel_l2(gphi.cpu().numpy(), 2 * psi) < 1e-10
+    F = act.force(U.detach(), phi.detach()).cpu().numpy()
+    eps = 1e-4
+    for seed in range(4):
+        X = I.su_n_direction(dims, nc, seed=400 + seed)
+        wv, vv = np.linalg.eigh(-1j * eps * X)
+        E = np.einsum("...ij,...j,...kj->...ik", vv, np.exp(1j * wv), vv.conj())
+        Sp = act(torch.from_numpy(E @ U_np).cuda(), phi.detach()).item()
+        Sm = act(torch.from_numpy(np.conj(np.swapaxes(E, -1, -2)) @ U_np).cuda(), phi.detach()).item()
+        fd = (Sp - Sm) / (2 * eps)
+        an = float(np.sum(np.real(np.einsum("...ab,...ba->...", X, F))))
+        assert abs(fd - an) < 1e-5 * max(abs(an), 1.0), (seed, fd, an)
