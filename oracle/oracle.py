@@ -10,7 +10,8 @@ this module adds the composite operators the paper builds from them
 (D^dagger = gamma5 D gamma5 or epsilon D epsilon, D^dagger D), textbook CG and
 BiCGstab with the paper's recompute/exit rules (Sec. 9), the Lanczos
 condition estimate of the ``cond`` module (App. F), the App. E flop counts,
-the clover term of Eq. (def_clov) and the fermion force of S = phi^dag (D_W^dag D_W)^-1 phi (derived here; the
+the clover term of Eq. (def_clov), the Laplace operators, stout smearing and
+the fermion forces of S = phi^dag (D^dag D)^-1 phi for D_W, D_S and D_B (derived here; the
 paper has none).
 
 Array shapes (complex128, C order):
@@ -22,6 +23,8 @@ Array shapes (complex128, C order):
 ``dims`` is always (Nx, Ny, Nz, Nt).
 """
 import ctypes
+import itertools
+import math
 import os
 
 import numpy as np
@@ -639,6 +642,85 @@ def staggered_action_gradient(op, psi, chi):
     B, C = staggered_force_terms(op, psi, chi)
     ph = phase_links(np.ones(op.Up.shape, np.complex128), op.bc)
     return (np.conj(np.swapaxes(B, -1, -2)) + C) * ph
+
+
+def _roll_sites(A, o):
+    """A(n + o) for a field with leading axes (t, z, y, x) and an offset o = (ox, oy, oz, ot)."""
+    return np.roll(A, shift=(-o[3], -o[2], -o[1], -o[0]), axis=(0, 1, 2, 3))
+
+
+def brillouin_force_terms(op, psi, chi):
+    """K_mu(n) with dS = Re sum tr[dU_mu(n) K_mu(n)] for S = sum_v Re phi_v^dag
+    (D_B^dag D_B)^-1 phi_v, psi = (D^dag D)^-1 phi, chi = D_B psi (derived here;
+    the paper has no force).  From Eq. (app_bril), dS = -2 Re <chi, dD psi> and
+    dD psi(n) = sum_s S_s (x) dW_s(n) psi(n+s) with the spin factor
+    S_s = rho_k sum_mu s_mu gamma_mu - lambda_k/2, so
+      dS = -2 Re sum_{n,s} tr[dW_s(n) M_s(n)],  M_s(n) = sum_v (S_s psi(n+s)) chi(n)^dag
+    (spin contracted).  W_s(n) is the average of the k! hop orderings of
+    Tab. off-axis; the derivative of one ordering's product P_1 ... P_k is
+    sum_j P_<j dV_j P_>j, so link j of the path receives (-2/k!) P_>j M_s P_<j
+    for a forward hop (V = U_mu(m)) and its dagger for a backward hop
+    (V = U_mu(m - mu)^dag).  Uses the operator's phased links."""
+    Up = op.Up
+    nc = Up.shape[-1]
+    g = [gamma(mu) for mu in range(4)]
+    K = np.zeros_like(Up)
+    dag = lambda A: np.conj(np.swapaxes(A, -1, -2))
+    eye = np.broadcast_to(np.eye(nc, dtype=np.complex128), Up.shape[:4] + (nc, nc))
+    for s in itertools.product((-1, 0, 1), repeat=4):
+        s = s[::-1]   # (sx, sy, sz, st) with st slowest, any order will do
+        axes = [mu for mu in range(4) if s[mu] != 0]
+        k = len(axes)
+        if k == 0:
+            continue
+        S = sum(RHO_B[k] * s[mu] * g[mu] for mu in axes) - 0.5 * LAM_B[k] * np.eye(4)
+        Spsi = np.einsum("ab,...cbv->...cav", S, _roll_sites(psi, s))
+        M = np.einsum("...bav,...cav->...bc", Spsi, np.conj(chi))      # colour (b, c)
+        for order in itertools.permutations(axes):
+            hops, o = [], [0, 0, 0, 0]
+            for mu in order:
+                sg = s[mu]
+                if sg > 0:
+                    V = _roll_sites(Up[..., mu, :, :], o)
+                else:
+                    om = list(o)
+                    om[mu] -= 1
+                    V = dag(_roll_sites(Up[..., mu, :, :], om))
+                hops.append((mu, sg, list(o), V))
+                o[mu] += sg
+            pre = [eye]
+            for (_, _, _, V) in hops:
+                pre.append(pre[-1] @ V)
+            post = [eye]
+            for (_, _, _, V) in reversed(hops):
+                post.append(V @ post[-1])
+            post = post[::-1]   # post[j] = product of hops j .. k-1
+            c = -2.0 / math.factorial(k)
+            for j, (mu, sg, oj, V) in enumerate(hops):
+                X = post[j + 1] @ M @ pre[j]
+                if sg > 0:   # link U_mu at n + o_j: value at site m is X(m - o_j)
+                    K[..., mu, :, :] += c * _roll_sites(X, [-a for a in oj])
+                else:        # link U_mu at n + o_j - mu, entering as its dagger
+                    om = [-a for a in oj]
+                    om[mu] += 1
+                    K[..., mu, :, :] += c * dag(_roll_sites(X, om))
+    return K
+
+
+def brillouin_force(op, psi, chi):
+    """F_mu(n) = P_TA(U K): dS/deps = Re sum tr[X F] for U -> exp(eps X) U."""
+    return project_ta(op.Up @ brillouin_force_terms(op, psi, chi))
+
+
+def brillouin_action_gradient(op, psi, chi):
+    """G with dS = Re sum conj(G) dU for the unphased links: bc-phase * K^dag."""
+    K = brillouin_force_terms(op, psi, chi)
+    ph = phase_links(np.ones(op.Up.shape, np.complex128), op.bc)
+    return np.conj(np.swapaxes(K, -1, -2)) * ph
+
+
+RHO_B = {1: 64.0 / 432.0, 2: 16.0 / 432.0, 3: 4.0 / 432.0, 4: 1.0 / 432.0}
+LAM_B = {1: 8.0 / 64.0, 2: 4.0 / 64.0, 3: 2.0 / 64.0, 4: 1.0 / 64.0}
 
 
 def project_ta(M):

@@ -850,3 +850,49 @@ def test_staggered_action_gradient_matches_finite_differences():
     fd = (Sp - Sm) / (2 * eps)
     an = float(np.sum(np.real(np.conj(G) * dU)))
     assert abs(fd - an) < 1e-6 * abs(an)
+
+
+# ------------------------------------------------------ Brillouin fermion force
+
+@pytest.mark.parametrize("bc", [(1, 1, 1, 1), (1, -1, 1, -1)])
+def test_brillouin_force_matches_finite_differences(bc):
+    """S = sum Re phi^dag (D_B^dag D_B)^-1 phi with the force through the W
+    path averages: dS/deps along U -> exp(eps X) U against Re sum tr[X F]
+    (central differences, eps = 1e-4, FP64 solves)."""
+    dims = (4, 2, 2, 4)
+    m0 = 0.4
+    U = I.gauge_field(dims, 3, 0.4, seed=141)
+    phi = I.source(dims, 3, 2, seed=142)
+    op = O.Operator(O.BRILLOUIN, U, bc, m0)
+    S0, psi = O.pseudofermion_action(op, phi)
+    F = O.brillouin_force(op, psi, op.apply(psi))
+    assert np.allclose(F, -np.conj(np.swapaxes(F, -1, -2)), atol=1e-14)
+    assert np.abs(np.trace(F, axis1=-2, axis2=-1)).max() < 1e-13
+    eps = 1e-4
+    for seed in range(3):
+        X = I.su_n_direction(dims, 3, seed=500 + seed)
+        Sp, _ = O.pseudofermion_action(O.Operator(O.BRILLOUIN, _expm_ah(eps * X) @ U, bc, m0), phi)
+        Sm, _ = O.pseudofermion_action(O.Operator(O.BRILLOUIN, _expm_ah(-eps * X) @ U, bc, m0), phi)
+        fd = (Sp - Sm) / (2 * eps)
+        an = np.sum(np.real(np.einsum("...ab,...ba->...", X, F)))
+        assert abs(fd - an) < 1e-6 * max(abs(an), 1.0), (seed, fd, an)
+
+
+def test_brillouin_action_gradient_matches_finite_differences():
+    """The complex gradient along an arbitrary complex dU (off the group, so
+    every path product's dependence on every link is exercised)."""
+    dims = (2, 2, 2, 4)
+    m0, bc = 0.4, (1, 1, 1, -1)
+    U = I.gauge_field(dims, 3, 0.4, seed=151)
+    phi = I.source(dims, 3, 1, seed=152)
+    op = O.Operator(O.BRILLOUIN, U, bc, m0)
+    S0, psi = O.pseudofermion_action(op, phi)
+    G = O.brillouin_action_gradient(op, psi, op.apply(psi))
+    rng = np.random.default_rng(7)
+    dU = rng.standard_normal(U.shape) + 1j * rng.standard_normal(U.shape)
+    eps = 1e-5
+    Sp, _ = O.pseudofermion_action(O.Operator(O.BRILLOUIN, U + eps * dU, bc, m0), phi)
+    Sm, _ = O.pseudofermion_action(O.Operator(O.BRILLOUIN, U - eps * dU, bc, m0), phi)
+    fd = (Sp - Sm) / (2 * eps)
+    an = float(np.sum(np.real(np.conj(G) * dU)))
+    assert abs(fd - an) < 1e-6 * abs(an)
