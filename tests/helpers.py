@@ -14,6 +14,28 @@ def rel_l2(got, want):
     return float(np.linalg.norm((got - want).ravel()) / max(np.linalg.norm(want.ravel()), 1e-300))
 
 
+def site_err(got, want, site_axes=4):
+    """Largest per-site error: max over sites of |got_n - want_n| divided by the
+    root-mean-square over sites of |want_n| (a site = the first `site_axes`
+    axes; the rest, colour, spin and RHS, form the site's vector).  A single
+    wrong site shows here even when the global relative L2 error hides it."""
+    got = np.asarray(got)
+    want = np.asarray(want)
+    nsite = int(np.prod(want.shape[:site_axes]))
+    d = np.linalg.norm((got - want).reshape(nsite, -1), axis=1)
+    w = np.linalg.norm(want.reshape(nsite, -1), axis=1)
+    return float(d.max() / max(np.sqrt(np.mean(w ** 2)), 1e-300))
+
+
+def check(got, want, prec, *ctx, site_axes=4, tol=None):
+    """Parity bar: global relative L2 <= tol (TOL[prec] by default) and
+    per-site error (site_err) <= 2 tol."""
+    tol = TOL[prec] if tol is None else tol
+    e, es = rel_l2(got, want), site_err(got, want, site_axes)
+    assert e <= tol and es <= 2 * tol, (ctx, e, es)
+    return e
+
+
 def to_device(op, v_np, prec=None):
     """numpy complex128 vector in the paper's site-outer order -> device tensor
     in the op's layout and (or the given) precision."""

@@ -15,7 +15,7 @@ import pytest
 import torch
 
 import oracle as O
-from helpers import TOL, rel_l2, to_device, to_numpy
+from helpers import TOL, check, rel_l2, to_device, to_numpy
 from paper_2112_14640_gb300 import dirac as D
 from paper_2112_14640_gb300 import inputs as I
 
@@ -64,9 +64,8 @@ def test_clover_apply_dagger_normal(kind, prec, case, layout):
     for dag in (False, True):
         got = to_numpy(op, op.apply(x, m0=m0, dagger=dag))
         want = ref.apply_dagger(src, m0) if dag else ref.apply(src, m0)
-        err = rel_l2(got, want)
-        assert err <= TOL[prec], (kind, prec, dims, nc, nv, dag, err)
-    assert rel_l2(to_numpy(op, op.apply_normal(x, m0=m0)), ref.apply_normal(src, m0)) <= TOL[prec]
+        check(got, want, prec, kind, dims, nc, nv, dag)
+    check(to_numpy(op, op.apply_normal(x, m0=m0)), ref.apply_normal(src, m0), prec, kind, "normal")
     op.close()
 
 
@@ -96,7 +95,7 @@ def test_clover_low_precision_storage(kind, prec, links):
     for dag in (False, True):
         got = to_numpy(op, op.apply(x, m0=0.1, dagger=dag))
         want = ref.apply_dagger(src, 0.1) if dag else ref.apply(src, 0.1)
-        assert rel_l2(got, want) <= TOL[prec], (kind, prec, links, dag)
+        check(got, want, prec, kind, links, dag)
     op.close()
 
 
@@ -116,7 +115,7 @@ def test_clover_every_launch_variant(kind):
                     continue
                 tried += 1
                 got = to_numpy(op, op.apply(x, m0=0.1))
-                assert rel_l2(got, want) <= TOL[D.F32], (kind, layout, vr, minb)
+                check(got, want, D.F32, kind, layout, vr, minb)
         assert tried >= 8
         op.close()
 
@@ -135,7 +134,7 @@ def test_clover_full_size_sampled_sites(kind):
     for dag in (False, True):
         got = to_numpy(op, op.apply(x, m0=0.1, dagger=dag)).reshape((V,) + src.shape[4:])[sites]
         want = ref.apply_sites(src, sites, 0.1, dagger=dag)
-        assert rel_l2(got, want) <= TOL[D.F32], (kind, dag)
+        check(got, want, D.F32, kind, dag, site_axes=1)
     op.close()
 
 
@@ -239,5 +238,5 @@ def test_clover_extreme_shapes(kind, prec):
             for dag in (False, True):
                 got = to_numpy(op, op.apply(x, m0=0.1, dagger=dag))
                 want = ref.apply_dagger(src, 0.1) if dag else ref.apply(src, 0.1)
-                assert rel_l2(got, want) <= TOL[prec], (kind, dims, nv, dag, layout)
+                check(got, want, prec, kind, dims, nv, dag, layout)
             op.close()

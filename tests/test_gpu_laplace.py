@@ -14,7 +14,7 @@ import pytest
 import torch
 
 import oracle as O
-from helpers import TOL, rel_l2, to_device, to_numpy
+from helpers import TOL, check, rel_l2, to_device, to_numpy
 from paper_2112_14640_gb300 import dirac as D
 from paper_2112_14640_gb300 import inputs as I
 
@@ -59,7 +59,7 @@ def test_laplace_apply(kind, prec, case, layout):
     want = ref.apply(src, m)
     for dag in (False, True):   # hermitian: the dagger is A itself
         got = to_numpy(op, op.apply(x, m0=m, dagger=dag))
-        assert rel_l2(got, want) <= TOL[prec], (kind, prec, dims, nc, nv, dag)
+        check(got, want, prec, kind, dims, nc, nv, dag)
     assert rel_l2(to_numpy(op, op.apply_normal(x, m0=m)), ref.apply(want, m)) <= TOL[prec]
     op.close()
 

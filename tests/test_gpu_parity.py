@@ -12,7 +12,7 @@ import pytest
 import torch
 
 import oracle as O
-from helpers import TOL, rel_l2, to_device, to_numpy
+from helpers import TOL, check, rel_l2, to_device, to_numpy
 from paper_2112_14640_gb300 import dirac as D
 from paper_2112_14640_gb300 import inputs as I
 
@@ -59,10 +59,9 @@ def test_apply_and_dagger(kind, prec, case, layout):
     for dag in (False, True):
         got = to_numpy(op, op.apply(x, m0=m0, dagger=dag))
         want = ref.apply_dagger(src, m0) if dag else ref.apply(src, m0)
-        err = rel_l2(got, want)
-        assert err <= TOL[prec], (kind, prec, dims, nc, nv, dag, err)
+        check(got, want, prec, kind, dims, nc, nv, dag)
     got = to_numpy(op, op.apply_normal(x, m0=m0))
-    assert rel_l2(got, ref.apply_normal(src, m0)) <= TOL[prec]
+    check(got, ref.apply_normal(src, m0), prec, kind, "normal")
     op.close()
 
 
@@ -78,7 +77,7 @@ def test_apply_low_precision_storage(kind, prec, layout, links):
     for dag in (False, True):
         got = to_numpy(op, op.apply(x, m0=m0, dagger=dag))
         want = ref.apply_dagger(src, m0) if dag else ref.apply(src, m0)
-        assert rel_l2(got, want) <= TOL[prec]
+        check(got, want, prec, kind, layout, links, dag)
     op.close()
 
 
@@ -124,7 +123,7 @@ def test_full_size_sampled_sites(kind, layout):
     for dag in (False, True):
         got = to_numpy(op, op.apply(x, m0=m0, dagger=dag)).reshape((V,) + src.shape[4:])[sites]
         want = ref.apply_sites(src, sites, m0, dagger=dag)
-        assert rel_l2(got, want) <= TOL[D.F32], (kind, dag)
+        check(got, want, D.F32, kind, dag, site_axes=1)
     op.close()
 
 
@@ -244,7 +243,7 @@ def test_every_launch_variant_matches_the_oracle(kind):
                         continue
                     tried += 1
                     got = to_numpy(op, op.apply(x, m0=m0))
-                    assert rel_l2(got, want) <= TOL[D.F32], (kind, layout, vr, minb, block)
+                    check(got, want, D.F32, kind, layout, vr, minb, block)
         assert tried >= 20
         op.close()
 
@@ -308,7 +307,7 @@ def test_extreme_shapes(kind, prec):
         for dag in (False, True):
             got = to_numpy(op, op.apply(x, m0=m0, dagger=dag))
             want = ref.apply_dagger(src, m0) if dag else ref.apply(src, m0)
-            assert rel_l2(got, want) <= TOL[prec], (kind, dims, nv, dag)
+            check(got, want, prec, kind, dims, nv, dag)
         n2 = op.norm2(x).cpu().numpy()
         assert np.allclose(n2, O.norm2(src if prec == D.F64 else src.astype(np.complex64).astype(np.complex128)),
                            rtol=1e-12)

@@ -896,3 +896,218 @@ def test_brillouin_action_gradient_matches_finite_differences():
     fd = (Sp - Sm) / (2 * eps)
     an = float(np.sum(np.real(np.conj(G) * dU)))
     assert abs(fd - an) < 1e-6 * abs(an)
+
+
+# ------------------------------------- W path average for non-commuting links
+
+def _su3_directions(rng):
+    """Four random traceless anti-hermitian 3x3 matrices X_mu (su(3))."""
+    out = []
+    for _ in range(4):
+        A = rng.standard_normal((3, 3)) + 1j * rng.standard_normal((3, 3))
+        H = (A + A.conj().T) / 2
+        H -= np.trace(H) / 3 * np.eye(3)
+        out.append(1j * H)
+    return out
+
+
+def _constant_links(X, eps, dims=(3, 3, 3, 3)):
+    from scipy.linalg import expm
+    U = np.zeros(tuple(dims[::-1]) + (4, 3, 3), complex)
+    for mu in range(4):
+        U[..., mu, :, :] = expm(eps * X[mu])
+    return U
+
+
+def _eps3_ratios(w_of_eps, X, eps=0.04):
+    """For constant links U_mu = exp(eps X_mu) every hop ordering of offset s
+    is a product of exp(+-eps X_mu); by Baker-Campbell-Hausdorff the average
+    over all k! orderings (Tab. off-axis) is exp(eps sum_mu s_mu X_mu) + O(eps^3):
+    the O(eps^2) commutator terms cancel pairwise.  Returns, per offset with
+    k >= 2 hops, the ratio of the deviations at eps and eps/2 (8 for an
+    O(eps^3) deviation, 4 for an O(eps^2) one)."""
+    from scipy.linalg import expm
+    out = {}
+    W1, W2 = w_of_eps(eps), w_of_eps(eps / 2)
+    for d in range(81):
+        s = _offset(d)
+        if int(np.abs(s).sum()) < 2:
+            continue
+        S = sum(s[mu] * X[mu] for mu in range(4))
+        e1 = np.abs(W1[d] - expm(eps * S)).max()
+        e2 = np.abs(W2[d] - expm(eps / 2 * S)).max()
+        out[d] = e1 / e2
+    return out
+
+
+def _w_const_subset(X, eps, orderings):
+    """W_s for constant links averaged over the hop orderings `orderings(hops)`
+    returns (a planted mistake when that is not all k! of them)."""
+    from scipy.linalg import expm
+    Wd = {}
+    for d in range(81):
+        s = _offset(d)
+        hops = [mu for mu in range(4) if s[mu]]
+        perms = orderings(hops)
+        acc = np.zeros((3, 3), complex)
+        for perm in perms:
+            M = np.eye(3, dtype=complex)
+            for mu in perm:
+                M = M @ expm(s[mu] * eps * X[mu])
+            acc += M
+        Wd[d] = acc / len(perms)
+    return Wd
+
+
+def _cyclic(hops):
+    return [hops[i:] + hops[:i] for i in range(len(hops))] if hops else [[]]
+
+
+def test_w_all_orderings_average_is_exp_sum_to_third_order():
+    """Pins the completeness of the k!-ordering average of Tab. off-axis for
+    k = 2, 3, 4 with non-commuting links: the deviation from
+    exp(eps sum s_mu X_mu) must fall as eps^3.  An average over only the k
+    cyclic orderings (a plausible enumeration mistake) falls as eps^2 and is
+    rejected by the same check."""
+    rng = np.random.default_rng(17)
+    X = _su3_directions(rng)
+
+    def oracle_w(eps):
+        W = O.build_w(O.phase_links(_constant_links(X, eps), (1, 1, 1, 1)))
+        return {d: W[1, 2, 0, 1, d] for d in range(81)}
+
+    ratios = _eps3_ratios(oracle_w, X)
+    for k in (2, 3, 4):
+        rk = [r for d, r in ratios.items() if int(np.abs(_offset(d)).sum()) == k]
+        assert len(rk) == {2: 24, 3: 32, 4: 16}[k]
+        assert all(6.5 < r < 9.5 for r in rk), (k, min(rk), max(rk))
+    # the full enumeration written here agrees with the oracle (constant links)
+    full = _w_const_subset(X, 0.04, lambda h: [list(p) for p in itertools.permutations(h)] or [[]])
+    W = oracle_w(0.04)
+    assert max(np.abs(full[d] - W[d]).max() for d in range(81)) < 1e-14
+    # planted mistake: cyclic orderings only -> O(eps^2) for k = 3, 4
+    bad = _eps3_ratios(lambda e: _w_const_subset(X, e, _cyclic), X)
+    worst = [r for d, r in bad.items() if int(np.abs(_offset(d)).sum()) >= 3]
+    assert not all(6.5 < r < 9.5 for r in worst)
+    assert min(worst) < 5.0
+
+
+# ------------------------------------ element-wise dense matrices (2^4, 3x3x2x2)
+# Built here from the equations, entry by entry, without the oracle's code:
+# the links are phased here, W is enumerated here, the gammas are the
+# tensor-product forms above.
+
+def _site(c, dims):
+    x, y, z, t = c
+    return ((t * dims[2] + z) * dims[1] + y) * dims[0] + x
+
+
+def _phased_here(U, bc, dims):
+    Up = U.copy()
+    for mu, ax in enumerate((3, 2, 1, 0)):
+        idx = [slice(None)] * 4
+        idx[ax] = dims[mu] - 1
+        Up[tuple(idx) + (mu,)] *= bc[mu]
+    return Up
+
+
+def _link(Up, c, mu):
+    x, y, z, t = c
+    return Up[t, z, y, x, mu]
+
+
+def _step(c, mu, sgn, dims):
+    c = list(c)
+    c[mu] = (c[mu] + sgn) % dims[mu]
+    return tuple(c)
+
+
+def _w_here(Up, c, s, dims):
+    hops = [mu for mu in range(4) if s[mu]]
+    nc = Up.shape[-1]
+    if not hops:
+        return np.eye(nc, dtype=complex)
+    acc = np.zeros((nc, nc), complex)
+    perms = list(itertools.permutations(hops))
+    for perm in perms:
+        pos, M = c, np.eye(nc, dtype=complex)
+        for mu in perm:
+            if s[mu] > 0:
+                M = M @ _link(Up, pos, mu)
+                pos = _step(pos, mu, +1, dims)
+            else:
+                pos = _step(pos, mu, -1, dims)
+                M = M @ _link(Up, pos, mu).conj().T
+        acc += M
+    return acc / len(perms)
+
+
+def _dense_elementwise(kind, U, bc, m0, dims, rho, lam):
+    nc = U.shape[-1]
+    ns = 1 if kind == O.STAGGERED else 4
+    blk = nc * ns
+    V = int(np.prod(dims))
+    Up = _phased_here(U, bc, dims)
+    Dm = np.zeros((V * blk, V * blk), complex)
+    I4 = np.eye(4)
+    for c in itertools.product(*[range(d) for d in dims]):
+        n = _site(c, dims)
+        rows = slice(n * blk, (n + 1) * blk)
+
+        def add(m, M):
+            Dm[rows, m * blk:(m + 1) * blk] += M
+
+        if kind == O.WILSON:
+            add(n, (4 + m0) * np.eye(blk))
+            for mu in range(4):
+                fw, bw = _step(c, mu, +1, dims), _step(c, mu, -1, dims)
+                add(_site(fw, dims), -0.5 * np.kron(_link(Up, c, mu), I4 - GAMMA[mu]))
+                add(_site(bw, dims), -0.5 * np.kron(_link(Up, bw, mu).conj().T, I4 + GAMMA[mu]))
+        elif kind == O.STAGGERED:
+            add(n, m0 * np.eye(blk))
+            for mu in range(4):
+                eta = (-1) ** sum(c[nu] + 1 for nu in range(mu))
+                fw, bw = _step(c, mu, +1, dims), _step(c, mu, -1, dims)
+                add(_site(fw, dims), 0.5 * eta * _link(Up, c, mu))
+                add(_site(bw, dims), -0.5 * eta * _link(Up, bw, mu).conj().T)
+        else:
+            for s in itertools.product((-1, 0, 1), repeat=4):
+                k = sum(1 for a in s if a)
+                if k == 0:
+                    S = (m0 - 0.5 * lam[0]) * I4
+                else:
+                    S = rho[k] * sum(s[mu] * GAMMA[mu] for mu in range(4)) - 0.5 * lam[k] * I4
+                m = c
+                for mu in range(4):
+                    m = _step(m, mu, s[mu], dims)
+                add(_site(m, dims), np.kron(_w_here(Up, c, s, dims), S))
+    return Dm
+
+
+def _printed_weights():
+    w = {}
+    for name, *rest in _golden("brillouin_weights.txt"):
+        nums = rest[:rest.index("/")]
+        den = float(rest[-1])
+        w[name] = [float(a) / den for a in nums]
+    return [None] + w["rho"], w["lambda"]
+
+
+@pytest.mark.parametrize("kind", [O.WILSON, O.BRILLOUIN, O.STAGGERED])
+@pytest.mark.parametrize("dims,nc", [((2, 2, 2, 2), 3), ((3, 3, 2, 2), 2), ((4, 2, 2, 2), 3)])
+def test_dense_elementwise_matches_oracle_apply(kind, dims, nc):
+    """The whole matrix of D, written entry by entry from Eqs. (app_wils,
+    app_bril, def_stag) with the printed Brillouin weights, equals the matrix
+    of the oracle's apply; on 2^4 every offset aliases onto another site, so
+    the summation over offsets is checked too."""
+    if kind == O.STAGGERED and any(d % 2 for d in dims):
+        pytest.skip("staggered needs even extents")
+    rho, lam = _printed_weights()
+    U = I.gauge_field(dims, nc, 0.5, seed=71)
+    bc = (1, -1, 1, -1)
+    m0 = 0.05 if kind == O.STAGGERED else 0.1
+    op = O.Operator(kind, U, bc, m0)
+    shape = tuple(dims[::-1]) + ((nc, 1) if kind == O.STAGGERED else (nc, 4, 1))
+    want = _dense_elementwise(kind, U, bc, m0, dims, rho, lam)
+    got = dense(op.apply, shape)
+    assert np.abs(got - want).max() < 1e-13 * np.abs(want).max()
