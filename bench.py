@@ -41,8 +41,11 @@ NV = 12
 BC = (1, 1, 1, -1)
 EPS = 0.4
 MASS = {0: 0.1, 1: 0.1, 2: 0.05, 3: 0.1, 4: 0.1, 5: 0.1, 6: 0.1}   # Laplace kinds: m of A
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
+# bare masses of the precision study (32^3x64, eps = 0.6, gauge seed 99)
+# that put cond(D^dag D) near 1e6, from a Lanczos scan of FP32 CG on that
+# field; every solve reports the Lanczos estimate it actually saw
+SOLVE_MASS = {"staggered": 0.00265, "wilson": -1.961}
 
 
 def parse():
@@ -53,7 +56,11 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-sweep", action="store_true")
-    p.add_argument("--solve", action="store_true", help="add the config-3 mixed-precision solver comparison")
+    p.add_argument("--solve", action="store_true", help="full config-3 study: every sloppy precision and mode")
+    p.add_argument("--no-solve", action="store_true", help="skip the default config-3 FP32 vs mixed comparison")
+    p.add_argument("--solve-budget", type=float, default=240.0,
+                   help="wall-clock seconds the default solver comparison may use")
+    p.add_argument("--no-large", action="store_true", help="skip the 32^3x64 operator timing")
     p.add_argument("--batch", action="store_true", help="add the config-4 batched-solve measurement")
     p.add_argument("--ncu", action="store_true", help="short run for profiler launch lists (no extras)")
     p.add_argument("--csw", type=float, default=0.0,
@@ -363,7 +370,11 @@ def main():
     value = job_rate(step_flop, world, ms_step) / 1e9
 
     per_op = {}
-    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * pk["sm_max"] * 1e6 / 1e12   # TFLOP/s
+    # the ALU roof: the FMA probe kernel measured on this device (best of 3),
+    # next to the nominal count from the device's own SM count
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32_peak = max(D.measure_fp32_peak()[0] for _ in range(3))        # TFLOP/s
+    fp32_nominal = sm_count * FP32_LANES_PER_SM * 2 * pk["sm_max"] * 1e6 / 1e12
     for i, k in enumerate(kinds):
         times = [evs[s][i].elapsed_time(evs[s][i + 1]) for s in range(K)]
         t_ms = statistics.mean(times)
@@ -382,7 +393,9 @@ def main():
         roof = {"bound": "alu", "achieved": d["gflops"] / 1e3, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": d["gflops"] / 1e3 / fp32_peak, "traffic": ncu_traffic("brillouin"),
                 "traffic_unit": "bytes/launch", "kernel": "brillouin_kernel",
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x %.0f MHz" % pk["sm_max"]}
+                "peak_source": "measured: FMA probe kernel (dirac_measure_fp32_peak) on %d SMs; nominal "
+                               "%d x 128 lanes x 2 x %.0f MHz = %.1f TFLOP/s" % (sm_count, sm_count, pk["sm_max"],
+                                                                               fp32_nominal)}
     else:
         roof = {"bound": "hbm", "achieved": d["alg_GBps"], "peak": pk["hbm"], "unit": "GB/s",
                 "frac": d["hbm_frac"], "traffic": ncu_traffic(D.KIND_NAMES[dom]), "traffic_unit": "bytes/launch",
@@ -405,7 +418,9 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
             "gpu_launches": K * len(kinds), "roofline": roof, "rooflines": rooflines, "per_op": per_op,
-            "clocks": clk, "peaks_source": pk["source"], "launch_variants": launch, "layouts": layout_ms}
+            "clocks": clk, "peaks_source": pk["source"], "launch_variants": launch, "layouts": layout_ms,
+            "device": {"sm_count": sm_count, "fp32_peak_measured_tflops": fp32_peak,
+                       "fp32_peak_nominal_tflops": fp32_nominal}}
 
     if not args.ncu:
         # end to end through the C ABI from pinned host memory, copies included
@@ -421,7 +436,8 @@ def main():
         dt = (time.perf_counter() - t0) / Ke
         nbytes = sum(ops[k].vec_bytes() for k in kinds)
         line["e2e"] = {"value": step_flop / dt / 1e9, "unit": "Gflop/s", "h2d_bytes_per_step": nbytes,
-                       "d2h_bytes_per_step": nbytes, "ms_per_step": dt * 1e3}
+                       "d2h_bytes_per_step": nbytes, "ms_per_step": dt * 1e3,
+                       "pinned_copy": pinned_copy_rate(torch, ops[kinds[0]].vec_bytes())}
 
     if not args.ncu and not args.no_sweep:
         sweep = {}
@@ -455,8 +471,14 @@ def main():
     if not args.ncu and not args.no_laplace:
         line["laplace"] = laplace_measurement(D, U, pk, fp32_peak, quick_ms)
 
+    if not args.ncu and not args.no_large:
+        line["large_lattice"] = large_lattice_timing(D, I, torch, pk, fp32_peak)
+    if not args.ncu:
+        line["force"] = force_timing(D, I, torch)
     if args.solve:
         line["solve"] = solver_comparison(D, I, torch)
+    elif not args.ncu and not args.no_solve:
+        line["solve"] = solve_default(D, I, torch, args.solve_budget)
     if args.batch:
         line["batch"] = batch_measurement(D, I, torch)
 
@@ -468,6 +490,162 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def pinned_copy_rate(torch, nbytes, reps=5):
+    """Plain copies of one vector's bytes between pinned host memory and the
+    device (one cudaMemcpyAsync each), GB/s per direction: the link rate the
+    end-to-end apply's copies are measured against."""
+    h = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    st = torch.cuda.current_stream()
+    out = {"bytes": nbytes}
+    for name, fn in (("h2d_GBps", lambda: d.copy_(h, non_blocking=True)),
+                     ("d2h_GBps", lambda: h.copy_(d, non_blocking=True))):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        out[name] = nbytes * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    del h, d
+    return out
+
+
+def large_lattice_timing(D, I, torch, pk, fp32_peak, dims=(32, 32, 32, 64)):
+    """D_W, D_B and D_S at 32^3x64 (16x the benchmark volume: every operand is
+    larger than L2), N_v = 12, FP32, site-inner, autotuned there; two input
+    and output vector sets alternate between applies."""
+    import numpy as np
+    V = int(np.prod(dims))
+    U = torch.from_numpy(I.gauge_field(dims, NC, EPS, 4242)).cuda()
+    st = torch.cuda.current_stream()
+    out = {"lattice": "x".join(map(str, dims)), "nv": NV}
+    for k in (D.WILSON, D.STAGGERED, D.BRILLOUIN):
+        op = D.DiracOp(k, U, NV, BC, D.F32, layout=D.SITE_INNER)
+        op.autotune(MASS[k])
+        xs = [op.new_vector() for _ in range(2)]
+        for x in xs:
+            x.real.normal_()
+        ys = [op.new_vector(zero=False) for _ in range(2)]
+        reps = 4 if k == D.BRILLOUIN else 20
+        for i in range(2):
+            op.apply(xs[i], ys[i], m0=MASS[k])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for i in range(reps):
+            op.apply(xs[i % 2], ys[i % 2], m0=MASS[k])
+        e1.record(st)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / reps * 1e-3
+        flop = D.flops_per_site(k, NC) * V * NV
+        gbytes = alg_bytes_per_site(k, NC, NV) * V / 1e9
+        row = {"ms": t * 1e3, "gflops": flop / t / 1e9, "alg_GBps": gbytes / t, "launch": op.get_launch()}
+        if k == D.BRILLOUIN:
+            row["alu_frac"] = flop / t / 1e12 / fp32_peak
+        else:
+            row["hbm_frac"] = gbytes / t / pk["hbm"]
+        out[D.KIND_NAMES[k]] = row
+        op.close()
+        del xs, ys
+        torch.cuda.empty_cache()
+    del U
+    torch.cuda.empty_cache()
+    return out
+
+
+def force_timing(D, I, torch, dims=(16, 16, 16, 32), nv=4):
+    """The fermion-force kernel of the differentiation workload (16^3x32,
+    N_v = 4, FP32, Wilson and staggered): time per call and the algorithmic
+    bytes it moves (psi and chi read once, links read once, the force
+    written once)."""
+    import numpy as np
+    V = int(np.prod(dims))
+    U = torch.from_numpy(I.gauge_field(dims, NC, EPS, 7)).cuda()
+    st = torch.cuda.current_stream()
+    out = {"lattice": "x".join(map(str, dims)), "nv": nv}
+    for k in (D.WILSON, D.STAGGERED):
+        op = D.DiracOp(k, U, nv, BC, D.F32)
+        psi, chi = op.new_vector(), op.new_vector()
+        psi.real.normal_()
+        chi.real.normal_()
+        op.force(psi, chi)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 20
+        e0.record(st)
+        for _ in range(reps):
+            op.force(psi, chi)
+        e1.record(st)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / reps * 1e-3
+        spin = 1 if k == D.STAGGERED else 4
+        gbytes = V * (2 * NC * spin * nv * 8 + 2 * 4 * NC * NC * 8) / 1e9
+        out[D.KIND_NAMES[k]] = {"ms": t * 1e3, "alg_GBps": gbytes / t, "hbm_frac": gbytes / t / peaks()["hbm"]}
+        op.close()
+    return out
+
+
+def solve_default(D, I, torch, budget_s):
+    """The precision comparison of the metric, bounded in time: CG on D^dag D
+    to an FP64 residual of 1e-10 (32^3x64, N_c = 3, N_v = 12, eps = 0.6,
+    masses at cond(D^dag D) ~ 1e6), the FP32 sloppy iteration (the baseline)
+    against the adaptive FP16 (FP32 links) sloppy iteration, reliable updates
+    in FP64.  The two modes alternate, up to three times each per operator,
+    while the wall-clock budget lasts; every time is reported."""
+    dims = (32, 32, 32, 64)
+    U = torch.from_numpy(I.gauge_field(dims, NC, 0.6, 99)).cuda()
+    out = {"lattice": "32x32x32x64", "nv": NV, "eps": 0.6, "tol": 1e-10, "budget_s": budget_s}
+    t_start = time.perf_counter()
+    modes = (("f32", D.F32, D.LINKS_NATIVE, D.MIXED_RELIABLE), ("f16+f32links+adaptive", D.F16, D.LINKS_F32,
+                                                               D.MIXED_ADAPTIVE))
+    per_kind = budget_s / 2
+    for kind in (D.STAGGERED, D.WILSON):
+        t_kind = time.perf_counter()
+        name = D.KIND_NAMES[kind]
+        m0 = SOLVE_MASS[name]
+        op = D.DiracOp(kind, U, NV, BC, D.F64, layout=D.SITE_INNER)
+        for prec, links in ((D.F32, D.LINKS_NATIVE), (D.F16, D.LINKS_F32)):
+            tw = D.DiracOp(kind, U, NV, BC, prec, layout=D.SITE_INNER, link_storage=links)
+            tw.autotune(m0)
+            tw.close()
+        b = op.to_prec(op.from_site_outer(torch.from_numpy(
+            I.source(dims, NC, NV, 5, staggered=(kind == D.STAGGERED))).cuda()))
+        row = {"m0": m0}
+        for rep in range(3):
+            for mname, inner, links, mode in modes:
+                if rep > 0 and time.perf_counter() - t_kind > per_kind:
+                    break
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                x, st = op.solve(b, m0=m0, solver=D.CG_NORMAL, tol=1e-10, maxit=60000, inner_prec=inner,
+                                 sloppy_links=links, mixed_mode=mode)
+                torch.cuda.synchronize()
+                r = row.setdefault(mname, {"seconds": [], "iters": [], "status": [], "max_true_relres": [],
+                                           "cond_lanczos": None})
+                r["seconds"].append(time.perf_counter() - t0)
+                r["iters"].append(st["iters"])
+                r["status"].append(st["status"])
+                r["max_true_relres"].append(max(st["true_relres"]))
+                r["max_normal_relres"] = max(st["relres"])
+                r["cond_lanczos"] = max(st["lambda_max"]) / max(min(st["lambda_min"]), 1e-300)
+                del x
+        for mname, *_ in modes:
+            if mname in row:
+                sec = row[mname]["seconds"]
+                row[mname]["median_s"] = statistics.median(sec)
+                row[mname]["spread_s"] = max(sec) - min(sec)
+        if "f32" in row and modes[1][0] in row:
+            row["mixed_over_f32"] = row[modes[1][0]]["median_s"] / row["f32"]["median_s"]
+        out[name] = row
+        op.close()
+        torch.cuda.empty_cache()
+    out["wall_s"] = time.perf_counter() - t_start
+    del U
+    torch.cuda.empty_cache()
+    return out
 
 
 def clover_measurement(D, U, ops, xs, ys, per_op, pk, fp32_peak, quick_ms, csw=1.0):

@@ -76,7 +76,9 @@ enum {
 /* Lattice geometry and storage precision of an operator.
  * dims   : extents, each >= 2; staggered operators need all four even
  *          (the eta phases of Eq. def_stag are periodic only then).
- * nc     : number of colours N_c (1..4 compiled; 3 is the physical case).
+ * nc     : number of colours N_c: 1..8 for F64/F32 storage, 1..4 for BF16/F16
+ *          (DIRAC_ERR_UNSUPPORTED_NC otherwise); 3 is the physical case and has
+ *          the tuned launch variants, N_c >= 5 runs one RHS per thread.
  * nv     : number of right-hand sides N_v, 1..64.
  * bc     : +1 periodic / -1 antiperiodic per direction.  The phase multiplies
  *          U_mu(n) on the links with n_mu = N_mu - 1 before anything else
@@ -244,10 +246,11 @@ int dirac_vec_convert(const dirac_op *op, const void *src, dirac_prec src_prec, 
 
 /* Per-RHS squared 2-norms of a [rows][nv] complex vector in precision prec,
  * written to out_dev (nv doubles), for callers that cannot allocate device
- * memory: code running where cudaMalloc is unavailable or forbidden, such as
- * inside CUDA stream capture of a graph they do not own, in a host callback,
- * under a custom allocator that must not be bypassed, or in a real-time loop
- * that forbids allocation.  It needs no operator handle and allocates nothing:
+ * memory: code whose device memory is all owned by a pooling or caching
+ * allocator that must not be bypassed, latency-critical loops that cannot
+ * afford the implicit device synchronisation cudaMalloc/cudaFree may cause,
+ * and programs running so close to the memory limit that a late allocation
+ * could fail mid-solve.  It needs no operator handle and allocates nothing:
  * the partial sums live in a fixed device array inside the library
  * (DIRAC_NOALLOC_MAX_BLOCKS x 64 doubles = 256 KiB, held by every GPU that
  * loads the library until the process exits).  The paper has no counterpart;
@@ -255,7 +258,7 @@ int dirac_vec_convert(const dirac_op *op, const void *src, dirac_prec src_prec, 
  * the sum over a different number of blocks).
  *   v        device pointer, 16-byte aligned, rows*nv complex numbers
  *   rows     >= 1 (any size; the reduction is a grid-stride loop)
- *   nv       1..64, else DIRAC_ERR_CAPACITY
+ *   nv       1..64: nv < 1 gives DIRAC_ERR_INVALID_ARG, nv > 64 DIRAC_ERR_CAPACITY
  * The first call on each device looks up the array's device address (with
  * that device current), so make that first call before any stream capture.
  * All calls share the one array: calls whose work overlaps on the GPU (other
@@ -319,6 +322,8 @@ typedef struct {
     double seconds;            /* wall time of the call */
     double lambda_min[64];     /* CG only: Lanczos estimates of the extreme eigenvalues */
     double lambda_max[64];     /* of D^dag D from the CG coefficients (App. F "cond"); 0 otherwise */
+    int host_launches;         /* dirac_solve_batched: graph launches issued by the host (1 when the
+                                  whole convergence loop ran as one graph with a device-side loop) */
 } dirac_solve_stats;
 
 /* Solve for N_v right-hand sides b (operator precision); x holds the initial
@@ -335,8 +340,11 @@ int dirac_solve(const dirac_op *op, const void *b, void *x, double m0,
  * limit of params (inner_prec must equal every operator's precision).
  * Coefficients and convergence masks stay on the device; segments of
  * recompute_every (default 20) iterations followed by a true-residual
- * recompute run for all solves as one CUDA graph, replayed until every solve
- * has converged.  stats (host array of nsolves, may be NULL) receive per-solve
+ * recompute run for all solves inside one CUDA graph whose device-side while
+ * node repeats them (each solve behind its own conditional node, skipped once
+ * converged) until every solve has converged or maxit is reached: one graph
+ * launch by the host (a host replay of a one-segment graph where conditional
+ * nodes are unavailable).  stats (host array of nsolves, may be NULL) receive per-solve
  * iterations (segment granularity), final residuals and the device-timed
  * seconds from the batch start to that solve's completion.  Blocks until done.
  * Returns 0 when all converged, DIRAC_NOT_CONVERGED otherwise. */
@@ -346,10 +354,11 @@ int dirac_solve_batched(int nsolves, dirac_op *const *ops, const void *const *b,
 
 /* ------------------------------------------------------------ fermion force
  * Derivative of S = sum_v Re phi_v^dag (D^dag D)^-1 phi_v with respect to
- * the links, for D = D_W (Eq. app_wils) or D_S (Eq. def_stag) (the paper has
- * no force; derived here, without the clover term, so an operator carrying
- * one is refused).  Inputs: psi = (D^dag D)^-1 phi and chi = D psi, vectors of
- * op (F64 or F32).  Output: [site][mu][a][b] complex in op precision.
+ * the links, for D = D_W (Eq. app_wils), D_S (Eq. def_stag) or D_B (Eq.
+ * app_bril, through the path-averaged W links of Tab. off-axis) (the paper
+ * has no force; derived here, without the clover term, so an operator
+ * carrying one is refused).  Inputs: psi = (D^dag D)^-1 phi and chi = D psi,
+ * vectors of op (F64 or F32).  Output: [site][mu][a][b] complex in op precision.
  *   mode DIRAC_FORCE_TA:   F_mu(n) = P_TA(U B - C U^dag), traceless
  *                          anti-hermitian, with dS/deps = Re sum tr[X F] for
  *                          U -> exp(eps X) U, X in su(Nc);
@@ -359,7 +368,12 @@ int dirac_solve_batched(int nsolves, dirac_op *const *ops, const void *const *b,
  *   D_W: B_mu(n) = sum psi(n+mu) [(1-gamma_mu) chi(n)]^dag,
  *        C_mu(n) = sum psi(n) [(1+gamma_mu) chi(n+mu)]^dag;
  *   D_S: B_mu(n) = -eta_mu(n) sum psi(n+mu) chi(n)^dag,
- *        C_mu(n) =  eta_mu(n) sum psi(n) chi(n+mu)^dag. */
+ *        C_mu(n) =  eta_mu(n) sum psi(n) chi(n+mu)^dag;
+ *   D_B: B_mu(n) = K_mu(n), C = 0, with dS = Re sum tr[dU K] from
+ *        M_s(n) = sum (S_s psi(n+s)) chi(n)^dag, S_s = rho_k sum s_mu gamma_mu
+ *        - lambda_k/2, carried back through the level recursion of W_s.
+ *        The Brillouin force keeps a scratch of 216 N_c x N_c matrices per
+ *        site in the handle (allocated on the first call, freed with it). */
 enum { DIRAC_FORCE_TA = 0, DIRAC_FORCE_GRAD = 1 };
 int dirac_force(const dirac_op *op, const void *psi, const void *chi, void *force_out, int mode, void *stream);
 /* dirac_force restricted to D_W (DIRAC_ERR_INVALID_ARG for other kinds). */
@@ -376,6 +390,15 @@ long dirac_flops_per_site(dirac_kind kind, int nc);
 /* Flops per site per RHS of the clover term as App. E counts it for the
  * two-multiplication form: 64Nc^2 (576 for SU(3)). */
 long dirac_clover_flops_per_site(int nc);
+/* Measured FP32 FMA peak of the current device, the denominator of the ALU
+ * roofline the Brillouin stencil (App. E: 30168 flop per site and RHS for
+ * SU(3), about 45 flop per algorithmic byte at N_v = 12) is reported against.
+ * Runs an FMA-only kernel (8 independent chains per thread, 8 x 256 threads per
+ * SM, `iters` x 128 FMAs per chain) once untimed and once timed with CUDA
+ * events on `stream`; *tflops receives 2 x FMAs / time in TFLOP/s and
+ * *sm_count (may be NULL) the device's multiprocessor count.  Synchronises
+ * `stream`.  iters < 1 or tflops == NULL: DIRAC_ERR_INVALID_ARG. */
+int dirac_measure_fp32_peak(int iters, double *tflops, int *sm_count, void *stream);
 /* Compile-time library version (major*10000 + minor*100 + patch). */
 int dirac_version(void);
 

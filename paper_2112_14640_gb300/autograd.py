@@ -1,9 +1,10 @@
 """torch.autograd wrapper of the pseudofermion action
 
-    S(U, phi) = sum_v Re phi_v^dag (D^dag D)^-1 phi_v,   D = D_W or D_S
+    S(U, phi) = sum_v Re phi_v^dag (D^dag D)^-1 phi_v,   D = D_W, D_S or D_B
 
-(the paper has no differentiation; this grows its Wilson and staggered
-operators and CG solver into a differentiable layer).  Forward: one CG solve of
+(the paper has no differentiation; this grows its Wilson, staggered and
+Brillouin operators and CG solver into a differentiable layer; for D_B the
+link gradient runs back through the path-averaged W links of Tab. off-axis).  Forward: one CG solve of
 D^dag D psi = phi (``dirac_solve`` with DIRAC_CG_HPD) and S = Re <phi, psi>
 from the library's dot product.  Backward: the adjoint solve, recomputed
 instead of stored (D^dag D is Hermitian, so the adjoint system is the forward
@@ -51,15 +52,15 @@ class _Action(torch.autograd.Function):
 
 
 class PseudofermionAction:
-    """Differentiable S(U, phi) for the Wilson (default) or staggered operator
-    on one lattice shape.
+    """Differentiable S(U, phi) for the Wilson (default), staggered or
+    Brillouin operator on one lattice shape.
 
     The operator handle is created on first use and its links refreshed from
     U on every call (``dirac_op_update_links``)."""
 
     def __init__(self, m0, bc=(1, 1, 1, 1), prec=D.F32, tol=1e-8, maxit=20000, save_solution=False, kind=D.WILSON):
-        if kind not in (D.WILSON, D.STAGGERED):
-            raise ValueError("the force is derived for D_W and D_S")
+        if kind not in (D.WILSON, D.STAGGERED, D.BRILLOUIN):
+            raise ValueError("the force is derived for D_W, D_S and D_B")
         self.kind = kind
         self.m0, self.bc, self.prec = float(m0), tuple(bc), prec
         self.tol, self.maxit, self.save_solution = tol, maxit, save_solution

@@ -5,11 +5,16 @@
 // the device, so an iteration is a host-free chain of kernels.  A segment of
 // K iterations followed by the recompute of the true residual (the paper's
 // recompute rule, Sec. 9, every K = 20 iterations in low precision) is
-// captured for all solves into ONE graph, each solve on its own forked
-// branch so small lattices run concurrently; the graph is replayed until
-// every solve has converged.  A solve's completion is stamped on the device
-// with %globaltimer.  No kernel waits on another: ordering comes only from
-// graph edges.
+// recorded per solve into the body of a conditional (if) node; the if nodes
+// of all solves sit side by side (small lattices run concurrently) in the
+// body of one while node, closed by a kernel that keeps the loop going while
+// any solve is unconverged.  The host launches that graph once and waits
+// once; the loop, the per-solve skipping of converged solves and the
+// convergence test all run on the device.  A solve's completion is stamped
+// on the device with %globaltimer.  No kernel waits on another: ordering
+// comes only from graph edges and the conditional nodes.  Where the driver
+// cannot build conditional nodes, a host loop replays a one-segment graph
+// instead (stats report the number of host launches).
 #include <math.h>
 #include <string.h>
 
@@ -61,7 +66,7 @@ struct BatchState {
 };
 
 __global__ void batch_check_kernel(int nv, const double *rr_true, const double *nb, double tol2, double *act,
-                                   BatchState *st, int K) {
+                                   BatchState *st, int K, cudaGraphConditionalHandle cond, int set_cond) {
     __shared__ int any;
     const int v = threadIdx.x;
     if (v == 0) any = 0;
@@ -80,6 +85,20 @@ __global__ void batch_check_kernel(int nv, const double *rr_true, const double *
             st->stamp = globaltimer();
         }
     }
+    // inside the device-side loop: this solve's segment runs again only while
+    // it has not converged
+    if (v == 0 && set_cond) cudaGraphSetConditional(cond, st->done ? 0u : 1u);
+}
+
+// End of one pass of the device-side loop: another pass while any solve is
+// unconverged and the iteration limit allows (a single thread; one launch).
+__global__ void batch_while_kernel(const BatchState *st, int nsolves, int *passes, int max_passes,
+                                   cudaGraphConditionalHandle cond) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int any = 0;
+    for (int i = 0; i < nsolves; ++i) any |= st[i].done == 0;
+    const int p = ++*passes;
+    cudaGraphSetConditional(cond, (any && p < max_passes) ? 1u : 0u);
 }
 
 }  // namespace dgb
@@ -166,24 +185,15 @@ extern "C" int dirac_solve_batched(int nsolves, dirac_op *const *ops, const void
         TRYB(op_apply_cg(op, x[i], q, m0[i], main));
         TRYB(blas_axpby(op, p, r, rhs, nullptr, 1.0, q, nullptr, -1.0, rr, main));
         TRYB(blas_axpby(op, p, pv, r, nullptr, 1.0, nullptr, nullptr, 0.0, nullptr, main));
-        batch_check_kernel<<<1, 64, 0, main>>>(nv, rr, nb, tol2, act, dstate + i, 0);
+        batch_check_kernel<<<1, 64, 0, main>>>(nv, rr, nb, tol2, act, dstate + i, 0, 0, 0);
         TRYB(launch_check("batch setup"));
     }
-    // The graph holds one segment (K iterations + recompute) of every solve
-    // still running; it is rebuilt without the finished ones whenever a solve
-    // completes, so converged solves stop costing GPU time.
     TRYB(cuda_check(cudaMemcpyAsync(hstate.data(), dstate, nsolves * sizeof(BatchState), cudaMemcpyDeviceToHost,
                                     main), "D2H state"));
     TRYB(cuda_check(cudaStreamSynchronize(main), "batch sync"));
-    while (replays < max_replays) {
-        std::vector<int> live;
-        for (int i = 0; i < nsolves; ++i)
-            if (!hstate[i].done) live.push_back(i);
-        if (live.empty()) break;
-        TRYB(cuda_check(cudaStreamBeginCapture(main, cudaStreamCaptureModeThreadLocal), "begin capture"));
-        TRYB(cuda_check(cudaEventRecord(fork, main), "fork"));
-        for (int i : live) {
-            cudaStream_t s = br[i];
+    {
+        // one segment (K iterations + recompute + convergence check) of solve i on stream s
+        auto record_segment = [&](int i, cudaStream_t s, cudaGraphConditionalHandle cond, int set_cond) -> int {
             const dirac_op *op = ops[i];
             const dirac_prec p = op->prec;
             const int nv = op->nv;
@@ -191,49 +201,145 @@ extern "C" int dirac_solve_batched(int nsolves, dirac_op *const *ops, const void
             double *sc = scal[i];
             double *rr = sc, *rr_new = sc + 128, *pq = sc + 2 * 128, *alpha = sc + 3 * 128, *beta = sc + 4 * 128;
             double *act = sc + 5 * 128, *nb = sc + 6 * 128;
-            TRYB(cuda_check(cudaStreamWaitEvent(s, fork, 0), "wait fork"));
+            int e;
             for (int k = 0; k < K; ++k) {
-                TRYB(batch_apply_A_pq(op, pv, q, pq, m0[i], s));
+                if ((e = batch_apply_A_pq(op, pv, q, pq, m0[i], s))) return e;
                 batch_alpha_kernel<<<1, 64, 0, s>>>(nv, rr, pq, act, alpha);
-                TRYB(blas_axpby(op, p, r, r, nullptr, 1.0, q, alpha, -1.0, rr_new, s));
+                if ((e = blas_axpby(op, p, r, r, nullptr, 1.0, q, alpha, -1.0, rr_new, s))) return e;
                 if (k + 1 < K) {
                     batch_beta_kernel<<<1, 64, 0, s>>>(nv, rr_new, rr, act, beta);
-                    TRYB(blas_update_xp(op, p, x[i], pv, r, alpha, beta, s));   // x += alpha p; p = r + beta p
+                    if ((e = blas_update_xp(op, p, x[i], pv, r, alpha, beta, s))) return e;   // x += alpha p; p = r + beta p
                 } else {
                     // last iteration of the segment: x += alpha p, then replace r by
                     // the true residual and build the next direction from it
-                    TRYB(blas_axpby(op, p, x[i], x[i], nullptr, 1.0, pv, alpha, 1.0, nullptr, s));
-                    TRYB(op_apply_cg(op, x[i], q, m0[i], s));
-                    TRYB(blas_axpby(op, p, r, rhs, nullptr, 1.0, q, nullptr, -1.0, rr_new, s));
+                    if ((e = blas_axpby(op, p, x[i], x[i], nullptr, 1.0, pv, alpha, 1.0, nullptr, s))) return e;
+                    if ((e = op_apply_cg(op, x[i], q, m0[i], s))) return e;
+                    if ((e = blas_axpby(op, p, r, rhs, nullptr, 1.0, q, nullptr, -1.0, rr_new, s))) return e;
                     batch_beta_kernel<<<1, 64, 0, s>>>(nv, rr_new, rr, act, beta);
-                    TRYB(blas_axpby(op, p, pv, r, nullptr, 1.0, pv, beta, 1.0, nullptr, s));
+                    if ((e = blas_axpby(op, p, pv, r, nullptr, 1.0, pv, beta, 1.0, nullptr, s))) return e;
                 }
             }
             // freeze converged RHS (rr now holds the true residual), stamp completion
-            batch_check_kernel<<<1, 64, 0, s>>>(nv, rr, nb, tol2, act, dstate + i, K);
-            TRYB(launch_check("batch segment"));
-            TRYB(cuda_check(cudaEventRecord(joins[i], s), "join"));
-            TRYB(cuda_check(cudaStreamWaitEvent(main, joins[i], 0), "wait join"));
-        }
-        rc = cuda_check(cudaStreamEndCapture(main, &graph), "end capture");
-        if (rc) goto fail;
-        TRYB(cuda_check(cudaGraphInstantiate(&exec, graph, 0), "graph instantiate"));
-        for (; replays < max_replays; ++replays) {
-            TRYB(cuda_check(cudaGraphLaunch(exec, main), "graph launch"));
-            TRYB(cuda_check(cudaMemcpyAsync(hstate.data(), dstate, nsolves * sizeof(BatchState),
-                                            cudaMemcpyDeviceToHost, main), "D2H state"));
-            TRYB(cuda_check(cudaStreamSynchronize(main), "batch sync"));
-            bool finished_one = false;
-            for (int i : live) finished_one |= hstate[i].done != 0;
-            if (finished_one) {
-                ++replays;
-                break;
+            batch_check_kernel<<<1, 64, 0, s>>>(nv, rr, nb, tol2, act, dstate + i, K, cond, set_cond);
+            return launch_check("batch segment");
+        };
+
+        // Device-side loop: one graph whose while node repeats, until every
+        // solve has converged or the iteration limit is reached, a body that
+        // holds one conditional (if) node per solve, each running that
+        // solve's segment only while it is unconverged.  The host launches it
+        // once and waits once.  If the driver cannot build it, the host
+        // replay below runs the same segments instead.
+        bool device_loop = false;
+        {
+            cudaGraph_t g = nullptr;
+            cudaGraphExec_t gx = nullptr;
+            int *dpasses = nullptr;
+            int e = cuda_check(cudaMalloc(&dpasses, sizeof(int)), "pass counter");
+            if (!e) e = cuda_check(cudaMemsetAsync(dpasses, 0, sizeof(int), main), "memset");
+            if (!e) e = cuda_check(cudaGraphCreate(&g, 0), "graph create");
+            cudaGraphConditionalHandle hw = 0;
+            cudaGraph_t body = nullptr;
+            if (!e) e = cuda_check(cudaGraphConditionalHandleCreate(&hw, g, 1, cudaGraphCondAssignDefault),
+                                   "while handle");
+            if (!e) {
+                cudaGraphNodeParams wp = {};
+                wp.type = cudaGraphNodeTypeConditional;
+                wp.conditional.handle = hw;
+                wp.conditional.type = cudaGraphCondTypeWhile;
+                wp.conditional.size = 1;
+                cudaGraphNode_t wnode;
+                e = cuda_check(cudaGraphAddNode(&wnode, g, nullptr, nullptr, 0, &wp), "while node");
+                if (!e) body = wp.conditional.phGraph_out[0];
             }
+            std::vector<cudaGraphNode_t> ifs(nsolves);
+            for (int i = 0; i < nsolves && !e; ++i) {
+                cudaGraphConditionalHandle hi = 0;
+                e = cuda_check(cudaGraphConditionalHandleCreate(&hi, body, hstate[i].done ? 0 : 1,
+                                                                cudaGraphCondAssignDefault), "if handle");
+                if (e) break;
+                cudaGraphNodeParams ip = {};
+                ip.type = cudaGraphNodeTypeConditional;
+                ip.conditional.handle = hi;
+                ip.conditional.type = cudaGraphCondTypeIf;
+                ip.conditional.size = 1;
+                e = cuda_check(cudaGraphAddNode(&ifs[i], body, nullptr, nullptr, 0, &ip), "if node");
+                if (e) break;
+                e = cuda_check(cudaStreamBeginCaptureToGraph(br[i], ip.conditional.phGraph_out[0], nullptr, nullptr, 0,
+                                                             cudaStreamCaptureModeThreadLocal), "capture to graph");
+                if (e) break;
+                const int seg = record_segment(i, br[i], hi, 1);
+                cudaGraph_t captured = nullptr;
+                const int end_rc = cuda_check(cudaStreamEndCapture(br[i], &captured), "end capture");
+                e = seg ? seg : end_rc;
+            }
+            if (!e) {
+                cudaKernelNodeParams kp = {};
+                int ns = nsolves, maxp = max_replays;
+                void *args[] = {(void *)&dstate, (void *)&ns, (void *)&dpasses, (void *)&maxp, (void *)&hw};
+                kp.func = (void *)batch_while_kernel;
+                kp.gridDim = dim3(1);
+                kp.blockDim = dim3(32);
+                kp.kernelParams = args;
+                cudaGraphNode_t kn;
+                e = cuda_check(cudaGraphAddKernelNode(&kn, body, ifs.data(), nsolves, &kp), "while kernel node");
+            }
+            if (!e) e = cuda_check(cudaGraphInstantiate(&gx, g, 0), "graph instantiate");
+            if (!e) {
+                device_loop = true;
+                rc = cuda_check(cudaGraphLaunch(gx, main), "graph launch");
+                ++replays;
+                if (!rc) rc = cuda_check(cudaMemcpyAsync(hstate.data(), dstate, nsolves * sizeof(BatchState),
+                                                         cudaMemcpyDeviceToHost, main), "D2H state");
+                if (!rc) rc = cuda_check(cudaStreamSynchronize(main), "batch sync");
+            }
+            if (gx) cudaGraphExecDestroy(gx);
+            if (g) cudaGraphDestroy(g);
+            if (dpasses) {
+                cudaStreamSynchronize(main);
+                cudaFree(dpasses);
+            }
+            cudaGetLastError();
+            if (device_loop && rc) goto fail;
+            rc = DIRAC_OK;
         }
-        cudaGraphExecDestroy(exec);
-        exec = nullptr;
-        cudaGraphDestroy(graph);
-        graph = nullptr;
+
+        // Host replay: the graph holds one segment of every solve still
+        // running; it is rebuilt without the finished ones whenever a solve
+        // completes, so converged solves stop costing GPU time.
+        while (!device_loop && replays < max_replays) {
+            std::vector<int> live;
+            for (int i = 0; i < nsolves; ++i)
+                if (!hstate[i].done) live.push_back(i);
+            if (live.empty()) break;
+            TRYB(cuda_check(cudaStreamBeginCapture(main, cudaStreamCaptureModeThreadLocal), "begin capture"));
+            TRYB(cuda_check(cudaEventRecord(fork, main), "fork"));
+            for (int i : live) {
+                TRYB(cuda_check(cudaStreamWaitEvent(br[i], fork, 0), "wait fork"));
+                TRYB(record_segment(i, br[i], 0, 0));
+                TRYB(cuda_check(cudaEventRecord(joins[i], br[i]), "join"));
+                TRYB(cuda_check(cudaStreamWaitEvent(main, joins[i], 0), "wait join"));
+            }
+            rc = cuda_check(cudaStreamEndCapture(main, &graph), "end capture");
+            if (rc) goto fail;
+            TRYB(cuda_check(cudaGraphInstantiate(&exec, graph, 0), "graph instantiate"));
+            for (; replays < max_replays; ++replays) {
+                TRYB(cuda_check(cudaGraphLaunch(exec, main), "graph launch"));
+                TRYB(cuda_check(cudaMemcpyAsync(hstate.data(), dstate, nsolves * sizeof(BatchState),
+                                                cudaMemcpyDeviceToHost, main), "D2H state"));
+                TRYB(cuda_check(cudaStreamSynchronize(main), "batch sync"));
+                bool finished_one = false;
+                for (int i : live) finished_one |= hstate[i].done != 0;
+                if (finished_one) {
+                    ++replays;
+                    break;
+                }
+            }
+            cudaGraphExecDestroy(exec);
+            exec = nullptr;
+            cudaGraphDestroy(graph);
+            graph = nullptr;
+        }
     }
     TRYB(cuda_check(cudaMemcpy(&hstart, dstart, sizeof(hstart), cudaMemcpyDeviceToHost), "D2H stamp"));
     if (stats) {
@@ -253,6 +359,7 @@ extern "C" int dirac_solve_batched(int nsolves, dirac_op *const *ops, const void
                 st.status_per_rhs[v] = (nb[v] == 0.0 || rr[v] < tol2 * nb[v]) ? DIRAC_OK : DIRAC_NOT_CONVERGED;
             }
             st.seconds = hstate[i].done ? (double)(hstate[i].stamp - hstart) * 1e-9 : wall;
+            st.host_launches = replays;
         }
     }
     rc = DIRAC_OK;

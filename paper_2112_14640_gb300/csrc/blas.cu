@@ -18,6 +18,8 @@
 //
 // Every thread handles four rows per loop trip so that four independent
 // 16-byte loads per operand are in flight.
+#include <atomic>
+
 #include "internal.h"
 
 namespace dgb {
@@ -515,7 +517,9 @@ int blas_convert(const dirac_op *op, const void *src, dirac_prec sp, void *dst, 
 static __device__ __align__(256) double g_noalloc_partial[DIRAC_NOALLOC_MAX_BLOCKS * 64];
 
 static double *noalloc_partial_ptr(int *rc) {
-    static double *addr[128] = {nullptr};
+    // one cached device address per device; host threads may race on the
+    // first lookup, so the slots are atomics (every racer stores the same value)
+    static std::atomic<double *> addr[128];
     int dev = 0;
     *rc = cuda_check(cudaGetDevice(&dev), "cudaGetDevice");
     if (*rc) return nullptr;
@@ -523,13 +527,13 @@ static double *noalloc_partial_ptr(int *rc) {
         *rc = DIRAC_ERR_CAPACITY;
         return nullptr;
     }
-    if (!addr[dev]) {
-        double *p = nullptr;
+    double *p = addr[dev].load(std::memory_order_acquire);
+    if (!p) {
         *rc = cuda_check(cudaGetSymbolAddress((void **)&p, g_noalloc_partial), "cudaGetSymbolAddress");
         if (*rc) return nullptr;
-        addr[dev] = p;
+        addr[dev].store(p, std::memory_order_release);
     }
-    return addr[dev];
+    return p;
 }
 
 }  // namespace dgb
@@ -540,7 +544,8 @@ extern "C" int dirac_vec_norm2_noalloc(const void *v, dirac_prec prec, long long
     if (!v || !out_dev || rows < 1) return DIRAC_ERR_INVALID_ARG;
     if ((uintptr_t)v & 15) return DIRAC_ERR_ALIGNMENT;
     if (prec < DIRAC_F64 || prec > DIRAC_F16) return DIRAC_ERR_UNSUPPORTED_PREC;
-    if (nv < 1 || nv > 64) {
+    if (nv < 1) return DIRAC_ERR_INVALID_ARG;
+    if (nv > 64) {
         fprintf(stderr, "libdirac: dirac_vec_norm2_noalloc: nv = %d exceeds the static capacity of 64\n", nv);
         return DIRAC_ERR_CAPACITY;
     }

@@ -72,6 +72,20 @@ __device__ __forceinline__ cx<A> spin_mix(const cx<A> (&p)[4], const A (&e)[4], 
     return f;
 }
 
+// spin component S of  sum_mu e_mu gamma_mu p + d p  for all four axes
+// (e_mu = 0 off the support; the run-time-mask path of large N_c)
+template <int S, typename A>
+__device__ __forceinline__ cx<A> spin_mix_rt(const cx<A> (&p)[4], const A (&e)[4], A d) {
+    cx<A> f = {d * p[S].re, d * p[S].im};
+    const cx<A> t[4] = {gamma_term<0, S>(p), gamma_term<1, S>(p), gamma_term<2, S>(p), gamma_term<3, S>(p)};
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+        f.re = fma(e[mu], t[mu].re, f.re);
+        f.im = fma(e[mu], t[mu].im, f.im);
+    }
+    return f;
+}
+
 template <int NC, int VR, typename E, typename EL, int LAYOUT>
 struct Ctx {
     using A = typename Acc<E>::T;
@@ -141,6 +155,81 @@ __device__ __forceinline__ void offset(const Ctx<NC, VR, E, EL, LAYOUT> &C, int 
     }
 }
 
+// Large N_c: one offset (support M, sign pattern b, both run-time values) with
+// the W~ read one row at a time instead of a register double buffer of N_c^2
+// elements; the spin-mixed neighbour spinor of every colour is formed first.
+// With e_mu = s_mu s_lead on the axes of M and 0 elsewhere, the spin factor
+// is sum_mu e_mu gamma_mu + d (as in `offset`, without compile-time masks).
+template <int NC, int VR, typename E, typename EL, int LAYOUT, typename A>
+__device__ __forceinline__ void offset_rows(const Ctx<NC, VR, E, EL, LAYOUT> &C, int q, int M, int b,
+                                            cx<A> (&acc)[NC][4][VR]) {
+    using L = Layout<LAYOUT>;
+    const int K = popc4(M);
+    const A ck = (A)c_lambda(K);
+    const long long cs = L::cs_stride(C.g);
+    A sig[4] = {0, 0, 0, 0};
+    int m = C.n;
+    {
+        int jbit = 0;
+#pragma unroll
+        for (int mu = 0; mu < 4; ++mu) {
+            if ((M >> mu) & 1) {
+                const bool neg = (b >> jbit) & 1;
+                sig[mu] = neg ? (A)-1 : (A)1;
+                m += neg ? C.dm[mu] : C.dp[mu];
+                ++jbit;
+            }
+        }
+    }
+    const A sl = sig[lead_axis(M)];
+    A e[4];
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) e[mu] = sig[mu] * sl;
+    const A d = -C.sgn * ck * sl;
+    const E *pm = C.in + 2 * (L::vec(C.g, (long long)m, NC * 4, 0) + C.vbase);
+    cx<A> f[NC][4][VR];
+#pragma unroll
+    for (int kc = 0; kc < NC; ++kc) {
+        cx<A> p[4][VR];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) load_cx<E, VR, A>(pm + 2 * (kc * 4 + s) * cs, p[s]);
+#pragma unroll
+        for (int v = 0; v < VR; ++v) {
+            const cx<A> pv[4] = {p[0][v], p[1][v], p[2][v], p[3][v]};
+            f[kc][0][v] = spin_mix_rt<0>(pv, e, d);
+            f[kc][1][v] = spin_mix_rt<1>(pv, e, d);
+            f[kc][2][v] = spin_mix_rt<2>(pv, e, d);
+            f[kc][3][v] = spin_mix_rt<3>(pv, e, d);
+        }
+    }
+    const EL *wq = C.wp + q * (2 * NC * NC);
+#pragma unroll 1
+    for (int a = 0; a < NC; ++a) {
+        cx<A> wr[NC];
+#pragma unroll
+        for (int kc = 0; kc < NC; ++kc) wr[kc] = ld1<EL, A>(wq + 2 * (a * NC + kc));
+        cx<A> o[4][VR];
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+#pragma unroll
+            for (int v = 0; v < VR; ++v) o[s][v] = cx<A>{0, 0};
+#pragma unroll
+        for (int kc = 0; kc < NC; ++kc)
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+#pragma unroll
+                for (int v = 0; v < VR; ++v) cmac(o[s][v], wr[kc], f[kc][s][v]);
+        // run-time row index: add through a compile-time switch over rows
+#pragma unroll
+        for (int r = 0; r < NC; ++r)
+            if (r == a)
+#pragma unroll
+                for (int s = 0; s < 4; ++s)
+#pragma unroll
+                    for (int v = 0; v < VR; ++v) acc[r][s][v] = acc[r][s][v] + o[s][v];
+    }
+}
+
 // The 2^k offsets of support M: their signs run in a loop, everything that
 // depends on M alone is fixed at compile time.  Two offsets per trip, so the
 // two W~ buffers swap roles without copies (every group has an even count);
@@ -149,19 +238,33 @@ template <int M, int NC, int VR, typename E, typename EL, int LAYOUT, typename A
 __device__ __forceinline__ void group(const Ctx<NC, VR, E, EL, LAYOUT> &C, int &q, cx<A> (&Wc)[NC][NC],
                                       cx<A> (&acc)[NC][4][VR]) {
     constexpr int K = popc4(M);
-    cx<A> Wn[NC][NC];
+    if constexpr (NC > kMaxNcSmall) {
+        static_assert(M == 1, "large N_c visits all groups in one run-time loop");
+        // every group M = 1..15 and its 2^k sign patterns in run-time loops
 #pragma unroll 1
-    for (int b = 0; b < (1 << K); b += 2) {
-        offset<M>(C, q, b, Wc, Wn, acc);
-        offset<M>(C, q + 1, b + 1, Wn, Wc, acc);
-        q += 2;
+        for (int Mr = 1; Mr <= 15; ++Mr)
+#pragma unroll 1
+            for (int b = 0; b < (1 << popc4(Mr)); ++b) {
+                offset_rows(C, q, Mr, b, acc);
+                ++q;
+            }
+    } else {
+        cx<A> Wn[NC][NC];
+#pragma unroll 1
+        for (int b = 0; b < (1 << K); b += 2) {
+            offset<M>(C, q, b, Wc, Wn, acc);
+            offset<M>(C, q + 1, b + 1, Wn, Wc, acc);
+            q += 2;
+        }
     }
 }
 
 template <int M, int NC, int VR, typename E, typename EL, int LAYOUT, typename A>
 __device__ __forceinline__ void groups_from(const Ctx<NC, VR, E, EL, LAYOUT> &C, int &q, cx<A> (&Wc)[NC][NC],
                                             cx<A> (&acc)[NC][4][VR]) {
-    if constexpr (M <= 15) {
+    if constexpr (NC > kMaxNcSmall) {
+        group<1>(C, q, Wc, acc);   // one run-time loop over all groups
+    } else if constexpr (M <= 15) {
         group<M>(C, q, Wc, acc);
         groups_from<M + 1>(C, q, Wc, acc);
     }
@@ -212,7 +315,7 @@ __global__ void __launch_bounds__(stencil_max_threads(MINB), (MINB > 1 ? 1 : 0))
             for (int v = 0; v < VR; ++v) acc[a][s][v] = cx<A>{0, 0};
 
     cx<A> Wc[NC][NC];
-    load_mat<NC, EL, A>(C.wp, Wc);
+    if constexpr (NC <= kMaxNcSmall) load_mat<NC, EL, A>(C.wp, Wc);
     int q = 0;
     bril::groups_from<1>(C, q, Wc, acc);
 
@@ -225,11 +328,12 @@ int launch_brillouin_v(const dirac_op *op, const void *in, void *out, double m0,
     int vr, minb, block;
     launch_variant(op, vr, minb, block);
     using A = typename Acc<E>::T;
-    return dispatch_nc(op->nc, [&](auto ncc) {
+    return dispatch_nc<big_nc_ok<E>()>(op->nc, [&](auto ncc) {
         constexpr int NC = decltype(ncc)::value;
         return dispatch_vr(vr, [&](auto vrc) {
             constexpr int VR = decltype(vrc)::value;
-            return dispatch_minb<NC>(minb, [&](auto mbc) {
+            if constexpr (!vr_compiled<NC>(VR)) return (int)DIRAC_ERR_INVALID_ARG;
+            else return dispatch_minb<NC>(minb, [&](auto mbc) {
             constexpr int MINB = decltype(mbc)::value;
             {
                 const long long threads = op->lat.nsites * (op->nv / VR);

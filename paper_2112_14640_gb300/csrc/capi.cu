@@ -101,6 +101,7 @@ static void op_free(dirac_op *op) {
     cudaFree(op->stage_out);
     cudaFree(op->red_partial);
     cudaFree(op->solver_ws);
+    cudaFree(op->force_ws);
     free(op);
 }
 
@@ -113,9 +114,10 @@ static int validate_geom(dirac_kind kind, const dirac_geom *g) {
         if (kind == DIRAC_STAGGERED && (g->dims[m] & 1)) return DIRAC_ERR_INVALID_ARG;
     }
     if ((long long)g->dims[0] * g->dims[1] * g->dims[2] * g->dims[3] > (1LL << 31)) return DIRAC_ERR_INVALID_ARG;
-    if (g->nc < 1 || g->nc > 4) return DIRAC_ERR_UNSUPPORTED_NC;
-    if (g->nv < 1 || g->nv > 64) return DIRAC_ERR_INVALID_ARG;
     if (g->prec < DIRAC_F64 || g->prec > DIRAC_F16) return DIRAC_ERR_UNSUPPORTED_PREC;
+    // N_c 1..8 for FP64/FP32 vectors, 1..4 with 16-bit storage (internal.h)
+    if (!nc_supported(g->nc, g->prec)) return DIRAC_ERR_UNSUPPORTED_NC;
+    if (g->nv < 1 || g->nv > 64) return DIRAC_ERR_INVALID_ARG;
     if (g->layout != DIRAC_LAYOUT_SITE_OUTER && g->layout != DIRAC_LAYOUT_SITE_INNER) return DIRAC_ERR_INVALID_ARG;
     if (g->link_storage != DIRAC_LINKS_NATIVE && g->link_storage != DIRAC_LINKS_F32) return DIRAC_ERR_INVALID_ARG;
     if (g->link_storage == DIRAC_LINKS_F32 && g->prec != DIRAC_BF16 && g->prec != DIRAC_F16)
@@ -321,8 +323,8 @@ int dirac_stout_smear(const void *U_in, void *V_out, const int dims[4], int nc, 
     if (!U_in || !V_out || !dims || nsteps < 0 || nsteps > 1000 || !std::isfinite(rho)) return DIRAC_ERR_INVALID_ARG;
     for (int m = 0; m < 4; ++m)
         if (dims[m] < 2) return DIRAC_ERR_INVALID_ARG;
-    if (nc < 1 || nc > 4) return DIRAC_ERR_UNSUPPORTED_NC;
     if (prec != DIRAC_F64 && prec != DIRAC_F32) return DIRAC_ERR_UNSUPPORTED_PREC;
+    if (!nc_supported(nc, prec)) return DIRAC_ERR_UNSUPPORTED_NC;
     const long long V = (long long)dims[0] * dims[1] * dims[2] * dims[3];
     if (V > (1LL << 31)) return DIRAC_ERR_INVALID_ARG;
     const size_t bytes = (size_t)V * 4 * nc * nc * 2 * elem_bytes(prec);

@@ -194,8 +194,11 @@ __device__ __forceinline__ long long neighbour(const Lat &g, long long n, const 
 // Index arithmetic of the two vector layouts (in complex numbers).  ncs is the
 // number of internal components per site (N_c*4 or N_c), cs one of them.
 //   OUTER: ((site * ncs + cs) * nv + v)      INNER: ((cs * V + site) * nv + v)
-// Links / W matrices, element e of matrix k (k = mu or dir):
-//   OUTER: ((site * nk + k) * NC*NC + e)     INNER: ((k * NC*NC + e) * V + site)
+// Links and clover blocks, element e of matrix k (k = mu or block), for either
+// vector layout: ((site * nk + k) * NC*NC + e), one site's matrices contiguous.
+// (With site-inner vectors the links were once stored [k][e][site]: a warp's
+// link loads then touched nine arrays a whole field apart, and D_W at
+// 16^3x32, N_v = 12 took 0.105 ms against 0.097 ms site-contiguous.)
 template <int LAYOUT>
 struct Layout {
     static __host__ __device__ __forceinline__ long long vec(const Lat &g, long long site, int ncs, int cs) {
@@ -208,15 +211,11 @@ struct Layout {
         else return g.V * g.nv;
     }
     template <int NC>
-    static __host__ __device__ __forceinline__ long long mat(const Lat &g, long long site, int nk, int k) {
-        if constexpr (LAYOUT == 0) return (site * nk + k) * (long long)(NC * NC);
-        else return (long long)k * NC * NC * g.V + site;
+    static __host__ __device__ __forceinline__ long long mat(const Lat &, long long site, int nk, int k) {
+        return (site * nk + k) * (long long)(NC * NC);
     }
     // distance between consecutive matrix elements
-    static __host__ __device__ __forceinline__ long long mat_stride(const Lat &g) {
-        if constexpr (LAYOUT == 0) return 1;
-        else return g.V;
-    }
+    static __host__ __device__ __forceinline__ long long mat_stride(const Lat &) { return 1; }
 };
 
 // NC x NC matrix whose elements are `stride` complex numbers apart.

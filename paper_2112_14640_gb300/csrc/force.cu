@@ -187,12 +187,15 @@ using namespace dgb;
 extern "C" int dirac_force(const dirac_op *op, const void *psi, const void *chi, void *force_out, int mode,
                            void *stream) {
     if (!op || !psi || !chi || !force_out) return DIRAC_ERR_INVALID_ARG;
-    if ((op->kind != DIRAC_WILSON && op->kind != DIRAC_STAGGERED) || (mode != 0 && mode != 1))
+    if ((op->kind != DIRAC_WILSON && op->kind != DIRAC_STAGGERED && op->kind != DIRAC_BRILLOUIN) ||
+        (mode != 0 && mode != 1))
         return DIRAC_ERR_INVALID_ARG;
     if (op->clover) return DIRAC_ERR_INVALID_ARG;   // derived without the clover term
     if (((uintptr_t)psi & 15) || ((uintptr_t)chi & 15)) return DIRAC_ERR_ALIGNMENT;
     if (op->prec != DIRAC_F64 && op->prec != DIRAC_F32) return DIRAC_ERR_UNSUPPORTED_PREC;
     cudaStream_t s = (cudaStream_t)stream;
+    // the handle owns the Brillouin force's scratch (allocated on first use)
+    if (op->kind == DIRAC_BRILLOUIN) return launch_bril_force(const_cast<dirac_op *>(op), psi, chi, force_out, mode, s);
     const bool stag = op->kind == DIRAC_STAGGERED;
     return dispatch_prec(op->prec, [&](auto tag) {
         using E = std::remove_pointer_t<decltype(tag)>;

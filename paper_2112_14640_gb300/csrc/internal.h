@@ -34,6 +34,8 @@ struct dirac_op {
     int red_blocks;
     void *solver_ws;       // solver workspace (lazy), solver_ws_bytes long
     size_t solver_ws_bytes;
+    void *force_ws;        // Brillouin force: 216 link terms per site (lazy), force_ws_bytes long
+    size_t force_ws_bytes;
     dirac_op *inner[4][2]; // lower-precision twins for mixed solves (lazy), by [prec][link storage]
     int vr, minb, block;   // stencil launch variant (RHS per thread, register class, threads per block);
                            // 0 = default
@@ -87,7 +89,13 @@ int dispatch_prec(dirac_prec p, F &&f) {
     return DIRAC_ERR_UNSUPPORTED_PREC;
 }
 
-template <typename F>
+// Colour counts compiled: 1..8 (the paper's N_c sweep reaches 8 within this
+// range).  N_c 5..8 are compiled for FP64 and FP32 storage only (BIG = false
+// restricts a dispatch to 1..4, as the 16-bit stencils use it), with one RHS
+// per thread and the compiler's own register choice (kMaxNcSmall below).
+constexpr int kMaxNc = 8;
+constexpr int kMaxNcSmall = 4;
+template <bool BIG = true, typename F>
 int dispatch_nc(int nc, F &&f) {
     switch (nc) {
     case 1: return f(std::integral_constant<int, 1>{});
@@ -95,8 +103,26 @@ int dispatch_nc(int nc, F &&f) {
     case 3: return f(std::integral_constant<int, 3>{});
     case 4: return f(std::integral_constant<int, 4>{});
     }
+    if constexpr (BIG) {
+        switch (nc) {
+        case 5: return f(std::integral_constant<int, 5>{});
+        case 6: return f(std::integral_constant<int, 6>{});
+        case 7: return f(std::integral_constant<int, 7>{});
+        case 8: return f(std::integral_constant<int, 8>{});
+        }
+    }
     return DIRAC_ERR_UNSUPPORTED_NC;
 }
+// N_c compiled for a vector element type (16-bit storage: 1..4)
+template <typename E>
+constexpr bool big_nc_ok() { return sizeof(E) >= 4; }
+inline bool nc_supported(int nc, dirac_prec p) {
+    return nc >= 1 && nc <= (p == DIRAC_F64 || p == DIRAC_F32 ? kMaxNc : kMaxNcSmall);
+}
+
+// VR values compiled for NC colours: 1, 2, 4 for N_c <= 4; 1 above
+template <int NC>
+constexpr bool vr_compiled(int vr) { return NC <= kMaxNcSmall || vr == 1; }
 
 template <typename F>
 int dispatch_vr(int vr, F &&f) {
@@ -121,6 +147,7 @@ constexpr int kStencilBlock = 128;
 __host__ __device__ constexpr int stencil_max_threads(int minb) { return minb > 1 ? 128 * minb : 128; }
 inline bool variant_compiled(int nc, int vr, int minb) {
     if (vr != 1 && vr != 2 && vr != 4) return false;
+    if (nc > kMaxNcSmall) return vr == 1 && minb == 1;
     if (minb == 1) return true;
     return nc == 3 && (minb == 3 || minb == 4 || minb == 6);
 }
@@ -166,7 +193,7 @@ inline void launch_variant(const dirac_op *op, int &vr, int &minb, int &block) {
     }
     // untuned: the widest 16-byte RHS group and, for N_c = 3, the register
     // class and block size the autotuner picks for FP32 on 16^3x32 lattices
-    vr = pick_vr(op->prec, op->nv);
+    vr = op->nc > kMaxNcSmall ? 1 : pick_vr(op->prec, op->nv);
     minb = 1;
     block = kStencilBlock;
     if (op->nc == 3) {
@@ -202,6 +229,8 @@ int launch_build_clover(dirac_op *op, const void *V, dirac_prec v_prec, cudaStre
 // the stored W~ (order and scale of bril_dirs.h) back to W_s in the public order
 int launch_unpack_w(const dirac_op *op, void *out, cudaStream_t s);
 int launch_convert_links(const dirac_op *src, dirac_op *dst, cudaStream_t s);
+// Brillouin fermion force (force_bril.cu): F = P_TA(U K) (mode 0) or G = bc K^dag (mode 1)
+int launch_bril_force(dirac_op *op, const void *psi, const void *chi, void *out, int mode, cudaStream_t s);
 
 // BLAS-1 (vectors in precision p with op's shape)
 int blas_norm2(const dirac_op *op, dirac_prec p, const void *v, double *out, cudaStream_t s);

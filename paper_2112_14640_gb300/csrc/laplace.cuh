@@ -188,11 +188,12 @@ int launch_laplace_v(const dirac_op *op, const void *in, void *out, double m, cu
     using A = typename Acc<E>::T;
     const bool bril = uses_w(op->kind);
     const double centre = bril ? 0.5 * m * m + 240.0 / 128.0 : 4.0 + 0.5 * m * m;
-    return dispatch_nc(op->nc, [&](auto ncc) {
+    return dispatch_nc<big_nc_ok<E>()>(op->nc, [&](auto ncc) {
         constexpr int NC = decltype(ncc)::value;
         return dispatch_vr(vr, [&](auto vrc) {
             constexpr int VR = decltype(vrc)::value;
-            return dispatch_minb<NC>(minb, [&](auto mbc) {
+            if constexpr (!vr_compiled<NC>(VR)) return (int)DIRAC_ERR_INVALID_ARG;
+            else return dispatch_minb<NC>(minb, [&](auto mbc) {
                 constexpr int MINB = decltype(mbc)::value;
                 const long long threads = op->lat.nsites * (op->nv / VR);
                 auto go = [&](auto nsc) {

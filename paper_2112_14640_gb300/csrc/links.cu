@@ -44,8 +44,8 @@ __global__ void phase_links_kernel(const UE *__restrict__ U, E *__restrict__ out
     const int per = nc * nc;
     for (int e = 0; e < per; ++e) {
         cx<double> u = ld_u(U, tid * per + e);
-        // [site][mu][a][b] (site-outer) or [mu][a][b][site] (site-inner)
-        const long long o = layout == 0 ? tid * per + e : ((long long)mu * per + e) * g.V + n;
+        // [site][mu][a][b] for either vector layout (common.cuh, Layout::mat)
+        const long long o = tid * per + e;
         out[2 * o] = from_acc<E, double>(f * u.re);
         out[2 * o + 1] = from_acc<E, double>(f * u.im);
     }
@@ -72,10 +72,18 @@ __device__ __forceinline__ void signed_link(const UE *__restrict__ U, const Lat 
 
 // W in FP64 for FP64 links, in FP32 otherwise (FP32 links carry 24 bits; the
 // four levels add a few FP32 roundings, and FP64 arithmetic is slow here).
+template <int NC, typename E>
+using WArith = std::conditional_t<sizeof(E) == 8, double, float>;
+// shared memory of build_w_kernel: the 81 W_s of one site
+template <int NC, typename E>
+constexpr size_t build_w_smem() { return sizeof(cx<WArith<NC, E>>) * 81 * NC * NC; }
+
 template <int NC, typename UE, typename E>
 __global__ void __launch_bounds__(96) build_w_kernel(const UE *__restrict__ U, E *__restrict__ W, Lat g, Phases ph) {
-    using AB = std::conditional_t<sizeof(E) == 8, double, float>;
-    __shared__ cx<AB> Ws[81][NC * NC];
+    using AB = WArith<NC, E>;
+    // dynamic: 81 N_c^2 complex numbers exceed the static 48 KB for N_c >= 7 in FP64
+    extern __shared__ __align__(16) unsigned char w_smem[];
+    auto Ws = reinterpret_cast<cx<AB>(*)[NC * NC]>(w_smem);
     const long long n = blockIdx.x;
     const int dir = threadIdx.x;
     const Coord c = site_coords(g, n);
@@ -197,10 +205,18 @@ int launch_build_w(dirac_op *op, const void *U, dirac_prec u_prec, cudaStream_t 
         using UE = std::remove_pointer_t<decltype(utag)>;
         return dispatch_prec(link_prec(op), [&](auto tag) {
             using E = std::remove_pointer_t<decltype(tag)>;
-            return dispatch_nc(op->nc, [&](auto ncc) {
+            return dispatch_nc<big_nc_ok<E>()>(op->nc, [&](auto ncc) {
                 constexpr int NC = decltype(ncc)::value;
-                build_w_kernel<NC, UE, E><<<(unsigned)op->V, 96, 0, s>>>((const UE *)U, (E *)op->w, op->lat,
-                                                                       phases_of(op));
+                constexpr size_t smem = build_w_smem<NC, E>();
+                if constexpr (smem > 48 * 1024) {
+                    const int rc = cuda_check(cudaFuncSetAttribute(build_w_kernel<NC, UE, E>,
+                                                                   cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                                   (int)smem),
+                                              "build_w_kernel shared memory");
+                    if (rc) return rc;
+                }
+                build_w_kernel<NC, UE, E><<<(unsigned)op->V, 96, smem, s>>>((const UE *)U, (E *)op->w, op->lat,
+                                                                          phases_of(op));
                 return launch_check("build_w_kernel");
             });
         });
@@ -318,8 +334,8 @@ __global__ void __launch_bounds__(128) build_clover_kernel(const UE *__restrict_
 #pragma unroll
         for (int b = 0; b < NC; ++b) {
             const int el = a * NC + b;
-            // the links' layout: [site][k][a][b] or [k][a][b][site]
-            const long long o = layout == 0 ? tid * per + el : ((long long)k * per + el) * g.V + n;
+            // the links' layout: [site][k][a][b] for either vector layout
+            const long long o = tid * per + el;
             out[2 * o] = from_acc<E, double>(f * (double)acc[a][b].re);
             out[2 * o + 1] = from_acc<E, double>(f * (double)acc[a][b].im);
         }
@@ -330,7 +346,7 @@ int launch_build_clover(dirac_op *op, const void *V, dirac_prec v_prec, cudaStre
         using UE = std::remove_pointer_t<decltype(utag)>;
         return dispatch_prec(link_prec(op), [&](auto tag) {
             using E = std::remove_pointer_t<decltype(tag)>;
-            return dispatch_nc(op->nc, [&](auto ncc) {
+            return dispatch_nc<big_nc_ok<E>()>(op->nc, [&](auto ncc) {
                 constexpr int NC = decltype(ncc)::value;
                 const long long threads = op->V * 4;
                 // closed loops do not see the boundary phases: leave them out

@@ -16,6 +16,29 @@ namespace dgb {
 template <int NC, int VR, bool DAG, typename E, typename A, typename EL>
 __device__ __forceinline__ void stag_hop(cx<A> (&acc)[NC][VR], const EL *__restrict__ link, long long lstride,
                                          const E *__restrict__ phi, long long cs_stride, A f) {
+    if constexpr (NC > kMaxNcSmall) {
+        // large N_c: the link is read one row (column for the dagger) at a time
+        cx<A> p[NC][VR];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) load_cx<E, VR, A>(phi + 2 * c * cs_stride, p[c]);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            cx<A> Lr[NC];
+#pragma unroll
+            for (int k = 0; k < NC; ++k) Lr[k] = ld1<EL, A>(link + 2 * lstride * (DAG ? k * NC + c : c * NC + k));
+#pragma unroll
+            for (int v = 0; v < VR; ++v) {
+                cx<A> t = {0, 0};
+#pragma unroll
+                for (int k = 0; k < NC; ++k) {
+                    if constexpr (DAG) cmac_conj(t, Lr[k], p[k][v]);
+                    else cmac(t, Lr[k], p[k][v]);
+                }
+                rmac(acc[c][v], f, t);
+            }
+        }
+        return;
+    }
     cx<A> L[NC][NC];
     load_mat_s<NC, EL, A>(link, lstride, L);
     cx<A> p[NC][VR];
@@ -89,11 +112,12 @@ int launch_staggered_v(const dirac_op *op, const void *in, void *out, double m0,
     int vr, minb, block;
     launch_variant(op, vr, minb, block);
     using A = typename Acc<E>::T;
-    return dispatch_nc(op->nc, [&](auto ncc) {
+    return dispatch_nc<big_nc_ok<E>()>(op->nc, [&](auto ncc) {
         constexpr int NC = decltype(ncc)::value;
         return dispatch_vr(vr, [&](auto vrc) {
             constexpr int VR = decltype(vrc)::value;
-            return dispatch_minb<NC>(minb, [&](auto mbc) {
+            if constexpr (!vr_compiled<NC>(VR)) return (int)DIRAC_ERR_INVALID_ARG;
+            else return dispatch_minb<NC>(minb, [&](auto mbc) {
             constexpr int MINB = decltype(mbc)::value;
             {
                 const long long threads = op->lat.nsites * (op->nv / VR);

@@ -65,6 +65,41 @@ __device__ __forceinline__ void reconstruct(cx<A> &o0, cx<A> &o1, cx<A> &o2, cx<
 template <int MU, bool DAG, int NC, int VR, typename E, typename A, typename EL>
 __device__ __forceinline__ void wilson_hop(cx<A> (&acc)[NC][4][VR], const EL *__restrict__ link, long long lstride,
                                            const E *__restrict__ psi, long long cs_stride, A a) {
+    if constexpr (NC > kMaxNcSmall) {
+        // large N_c: project first, then read the link one row (column for
+        // the dagger) at a time instead of holding all N_c^2 elements
+        cx<A> h[NC][2][VR];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            cx<A> p[4][VR];
+#pragma unroll
+            for (int s = 0; s < 4; ++s) load_cx<E, VR, A>(psi + 2 * (c * 4 + s) * cs_stride, p[s]);
+#pragma unroll
+            for (int v = 0; v < VR; ++v) project<MU, A>(p[0][v], p[1][v], p[2][v], p[3][v], a, h[c][0][v], h[c][1][v]);
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            cx<A> Lr[NC];
+#pragma unroll
+            for (int k = 0; k < NC; ++k) Lr[k] = ld1<EL, A>(link + 2 * lstride * (DAG ? k * NC + c : c * NC + k));
+#pragma unroll
+            for (int v = 0; v < VR; ++v) {
+                cx<A> c0 = {0, 0}, c1 = {0, 0};
+#pragma unroll
+                for (int k = 0; k < NC; ++k) {
+                    if constexpr (DAG) {
+                        cmac_conj(c0, Lr[k], h[k][0][v]);
+                        cmac_conj(c1, Lr[k], h[k][1][v]);
+                    } else {
+                        cmac(c0, Lr[k], h[k][0][v]);
+                        cmac(c1, Lr[k], h[k][1][v]);
+                    }
+                }
+                reconstruct<MU, A>(acc[c][0][v], acc[c][1][v], acc[c][2][v], acc[c][3][v], c0, c1, a);
+            }
+        }
+        return;
+    }
     cx<A> L[NC][NC];
     load_mat_s<NC, EL, A>(link, lstride, L);
     cx<A> h[NC][2][VR];
@@ -147,11 +182,12 @@ int launch_wilson_v(const dirac_op *op, const void *in, void *out, double m0, in
     int vr, minb, block;
     launch_variant(op, vr, minb, block);
     using A = typename Acc<E>::T;
-    return dispatch_nc(op->nc, [&](auto ncc) {
+    return dispatch_nc<big_nc_ok<E>()>(op->nc, [&](auto ncc) {
         constexpr int NC = decltype(ncc)::value;
         return dispatch_vr(vr, [&](auto vrc) {
             constexpr int VR = decltype(vrc)::value;
-            return dispatch_minb<NC>(minb, [&](auto mbc) {
+            if constexpr (!vr_compiled<NC>(VR)) return (int)DIRAC_ERR_INVALID_ARG;
+            else return dispatch_minb<NC>(minb, [&](auto mbc) {
                 constexpr int MINB = decltype(mbc)::value;
                 const long long threads = op->lat.nsites * (op->nv / VR);
                 // the clover term is a compile-time switch here (no cost to D_W without it)

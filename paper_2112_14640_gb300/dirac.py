@@ -56,7 +56,8 @@ class SolveStats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("outer_iters", ctypes.c_int), ("recomputes", ctypes.c_int),
                 ("status", ctypes.c_int), ("status_per_rhs", ctypes.c_int * 64), ("relres", ctypes.c_double * 64),
                 ("true_relres", ctypes.c_double * 64), ("seconds", ctypes.c_double),
-                ("lambda_min", ctypes.c_double * 64), ("lambda_max", ctypes.c_double * 64)]
+                ("lambda_min", ctypes.c_double * 64), ("lambda_max", ctypes.c_double * 64),
+                ("host_launches", ctypes.c_int)]
 
 
 class DiracError(RuntimeError):
@@ -99,6 +100,7 @@ SIGNATURES = {
     "dirac_flops_per_site": (ctypes.c_long, [_I, _I]),
     "dirac_clover_flops_per_site": (ctypes.c_long, [_I]),
     "dirac_version": (_I, []),
+    "dirac_measure_fp32_peak": (_I, [_I, ctypes.POINTER(_D), ctypes.POINTER(_I), _P]),
 }
 
 
@@ -128,6 +130,16 @@ def error_string(code):
 
 def flops_per_site(kind, nc):
     return int(lib().dirac_flops_per_site(int(kind), int(nc)))
+
+
+def measure_fp32_peak(iters=20000, stream=None):
+    """(TFLOP/s, SM count) of the FMA-only probe kernel on the current device."""
+    t, n = ctypes.c_double(), ctypes.c_int()
+    st = torch.cuda.current_stream() if stream is None else stream
+    rc = lib().dirac_measure_fp32_peak(int(iters), ctypes.byref(t), ctypes.byref(n), _P(st.cuda_stream))
+    if rc:
+        raise DiracError(rc, "dirac_measure_fp32_peak")
+    return t.value, n.value
 
 
 def stout_smear(U, rho=0.12, nsteps=3, out=None, stream=None):
@@ -427,5 +439,6 @@ def solve_batched(ops, bs, xs=None, m0s=None, solver=CG_NORMAL, tol=1e-6, maxit=
     for op, s in zip(ops, st):
         nv = op.nv
         out.append(dict(status=s.status, iters=s.iters, relres=list(s.relres[:nv]),
-                        status_per_rhs=list(s.status_per_rhs[:nv]), seconds=s.seconds))
+                        status_per_rhs=list(s.status_per_rhs[:nv]), seconds=s.seconds,
+                        host_launches=s.host_launches))
     return xs, out, rc

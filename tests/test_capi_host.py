@@ -69,7 +69,10 @@ def test_create_validates_before_touching_the_device(lib):
 
     assert create(D.WILSON, (4, 4, 4, 1), 3, 4) == -1          # extent < 2
     assert create(D.STAGGERED, (4, 4, 3, 4), 3, 4) == -1       # odd extent for staggered
-    assert create(D.WILSON, (4, 4, 4, 4), 5, 4) == -2          # N_c not compiled
+    assert create(D.WILSON, (4, 4, 4, 4), 9, 4) == -2          # N_c above 8 not compiled
+    assert create(D.WILSON, (4, 4, 4, 4), 0, 4) == -2          # no colours
+    assert create(D.WILSON, (4, 4, 4, 4), 5, 4, prec=D.BF16) == -2   # N_c 5..8 only in FP64/FP32
+    assert create(D.WILSON, (4, 4, 4, 4), 8, 4, prec=D.F16) == -2
     assert create(D.WILSON, (4, 4, 4, 4), 3, 0) == -1          # N_v = 0
     assert create(D.WILSON, (4, 4, 4, 4), 3, 65) == -1         # N_v > 64
     assert create(D.WILSON, (4, 4, 4, 4), 3, 4, bc=(1, 1, 1, 2)) == -1
@@ -141,5 +144,5 @@ def test_stout_smear_validates_without_device(lib):
     assert lib.dirac_stout_smear(None, p, dims, 3, D.F64, 0.12, 3, None) == -1
     assert lib.dirac_stout_smear(p, p, bad, 3, D.F64, 0.12, 3, None) == -1
     assert lib.dirac_stout_smear(p, p, dims, 3, D.F64, 0.12, -1, None) == -1
-    assert lib.dirac_stout_smear(p, p, dims, 5, D.F64, 0.12, 3, None) == -2
+    assert lib.dirac_stout_smear(p, p, dims, 9, D.F64, 0.12, 3, None) == -2
     assert lib.dirac_stout_smear(p, p, dims, 3, D.BF16, 0.12, 3, None) == -3

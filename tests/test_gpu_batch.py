@@ -38,6 +38,8 @@ def test_batched_solves_match_oracle(prec, tol):
     assert rc == 0
     for i, (op, ref, b, st) in enumerate(zip(ops, refs, bn, stats)):
         assert st["status"] == 0 and st["iters"] > 0 and st["seconds"] > 0, (i, st)
+        # the whole convergence loop ran as one graph launch (device-side while node)
+        assert st["host_launches"] == 1, st
         xsn = to_numpy(op, xs[i])
         bN = ref.apply_dagger(b, m0s[i])
         res = np.sqrt(O.norm2(bN - ref.apply_normal(xsn, m0s[i])) / O.norm2(bN))
@@ -56,5 +58,6 @@ def test_batched_solve_already_converged_and_hpd():
                                     solver=D.CG_HPD, tol=1e-10, maxit=5000)
     assert rc == 0
     assert stats[0]["iters"] == 0          # converged at set-up
+    assert stats[0]["host_launches"] == 1
     assert stats[1]["iters"] > 0
     assert torch.allclose(xs[1], x0, rtol=0, atol=1e-8 * x0.abs().max().item())

@@ -44,6 +44,11 @@ CASES = [
     ((4, 6, 4, 2), 2, 4, (1, 1, 1, 1)),
     ((2, 4, 4, 6), 4, 5, (-1, 1, 1, -1)),
     ((4, 4, 2, 4), 1, 8, (1, 1, 1, -1)),
+    # N_c beyond 4 (FP64/FP32 storage; the paper's N_c sweep reaches 8 and beyond)
+    ((4, 2, 4, 2), 5, 4, (-1, 1, 1, 1)),
+    ((4, 4, 2, 4), 6, 3, (1, 1, 1, -1)),
+    ((2, 4, 2, 4), 7, 2, (1, 1, -1, 1)),
+    ((2, 4, 4, 2), 8, 2, (1, -1, 1, -1)),
 ]
 
 
@@ -311,4 +316,41 @@ def test_extreme_shapes(kind, prec):
         n2 = op.norm2(x).cpu().numpy()
         assert np.allclose(n2, O.norm2(src if prec == D.F64 else src.astype(np.complex64).astype(np.complex128)),
                            rtol=1e-12)
+        op.close()
+
+
+@pytest.mark.parametrize("nc", [5, 6, 8])
+def test_large_nc_rejected_for_16bit_storage_and_variants(nc):
+    """N_c above 4 is compiled for FP64/FP32 storage with one RHS per thread:
+    16-bit storage and wider launch variants are refused by the C ABI."""
+    U = torch.from_numpy(I.gauge_field((2, 2, 2, 2), nc, 0.4, 3)).cuda()
+    for prec in (D.BF16, D.F16):
+        with pytest.raises(D.DiracError) as e:
+            D.DiracOp(D.WILSON, U, 2, (1, 1, 1, 1), prec)
+        assert e.value.code == -2
+    op = D.DiracOp(D.WILSON, U, 4, (1, 1, 1, 1), D.F32)
+    with pytest.raises(D.DiracError):
+        op.set_launch(2, 1, 128)
+    op.set_launch(1, 1, 64)
+    assert op.get_launch() == (1, 1, 64)
+    op.close()
+    with pytest.raises(D.DiracError) as e:
+        D.DiracOp(D.WILSON, torch.from_numpy(I.gauge_field((2, 2, 2, 2), 9, 0.4, 3)).cuda(), 2)
+    assert e.value.code == -2
+
+
+@pytest.mark.parametrize("kind", KINDS)
+def test_large_nc_full_lattice_sampled(kind):
+    """N_c = 6 and 8 at N_v = 12 on 8^3x4 (many thread blocks), FP32,
+    site-inner, autotuned: sampled sites against the oracle."""
+    for nc in (6, 8):
+        dims, nv, bc = (8, 8, 8, 4), 12, (1, 1, 1, -1)
+        m0 = 0.05 if kind == D.STAGGERED else 0.1
+        op, ref, src = make(kind, dims, nc, nv, bc, D.F32, seed=77, layout=D.SITE_INNER)
+        op.autotune(m0)
+        x = to_device(op, src)
+        V = int(np.prod(dims))
+        sites = np.concatenate([[0, V - 1], np.random.default_rng(nc).choice(V, 40, replace=False)])
+        got = to_numpy(op, op.apply(x, m0=m0)).reshape((V,) + src.shape[4:])[sites]
+        check(got, ref.apply_sites(src, sites, m0), D.F32, kind, nc, site_axes=1)
         op.close()

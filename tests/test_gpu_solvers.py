@@ -209,3 +209,24 @@ def test_adaptive_mode_finishes_a_stalling_fp16_solve():
                        mixed_mode=D.MIXED_ADAPTIVE)
     x3, st3 = op.solve(to_device(op, b), m0=m0, tol=1e-10, maxit=20000, inner_prec=D.F32)
     assert st2["iters"] == st3["iters"] and torch.equal(x2, x3)
+
+
+@pytest.mark.parametrize("nc", [6, 8])
+@pytest.mark.parametrize("kind", [D.WILSON, D.BRILLOUIN, D.STAGGERED])
+def test_large_nc_solvers(kind, nc):
+    """N_c = 6 and 8: CG on the normal equations in FP64 to 1e-11, BiCGstab
+    (Wilson-type) and the FP64/FP32 mixed-precision CG to 1e-10, each solution
+    checked by the oracle applying D in FP64."""
+    m0 = 0.3
+    op, ref, b = setup(kind, (4, 2, 2, 4), nc, 2, (1, 1, 1, -1), D.F64)
+    x, st = op.solve(to_device(op, b), m0=m0, tol=1e-11, maxit=5000)
+    assert st["status"] == 0, st
+    assert np.all(normal_relres(ref, to_numpy(op, x), b, m0) < 1.01e-11)
+    if kind != D.STAGGERED:
+        x, st = op.solve(to_device(op, b), m0=m0, solver=D.BICGSTAB, tol=1e-10, maxit=5000)
+        assert st["status"] == 0, st
+        assert np.all(true_relres(ref, to_numpy(op, x), b, m0) < 1.01e-10)
+    x, st = op.solve(to_device(op, b), m0=m0, tol=1e-10, maxit=20000, inner_prec=D.F32)
+    assert st["status"] == 0, st
+    assert np.all(normal_relres(ref, to_numpy(op, x), b, m0) < 1.01e-10)
+    op.close()
