@@ -165,6 +165,24 @@ int dirac_op_set_clover(dirac_op *op, double csw, const void *V, dirac_prec v_pr
  * Synchronises `stream` before returning. */
 int dirac_stout_smear(const void *U_in, void *V_out, const int dims[4], int nc, dirac_prec prec, double rho,
                       int nsteps, void *stream);
+/* Chain rule of a link derivative through stout smearing (the paper has no
+ * force; derived here): with V = dirac_stout_smear(U, rho, nsteps) and G_V in
+ * the convention of DIRAC_FORCE_GRAD (dS = Re sum conj(G_V) dV for any
+ * complex dV, e.g. dirac_force of an operator built from V), G_U receives the
+ * same for U: dS = Re sum conj(G_U) dU.  Per step V' = exp(iQ) U, in the form
+ * dS = Re sum tr[dV' Sigma'] (Sigma' = G^dag):
+ *   Sigma_U = Sigma' e^{iQ} - C^dag Xi + the staple terms of Y = U^dag Xi,
+ *   Xi = anti-hermitian part of Lambda - tr(Lambda)/N_c,
+ *   Lambda = L(iQ, U Sigma') the Frechet derivative of exp at iQ (computed
+ *            as the upper-right block of exp([[iQ, U Sigma'], [0, iQ]])),
+ * and each link of the staples in C_mu(x) receives rho times the derivative of
+ * tr[(staple) Y_mu(x)] with respect to it.  U_in, G_V, G_U: device fields
+ * [site][mu][a][b] complex in prec (F64 or F32), no boundary phases; G_U must
+ * not alias U_in or G_V; N_c 1..4.  Arithmetic in FP64; the intermediate fields of the
+ * forward steps are recomputed (nsteps - 1 fields plus three FP64 fields are
+ * allocated and freed here).  Synchronises `stream`. */
+int dirac_stout_backward(const void *U_in, const void *G_V, void *G_U, const int dims[4], int nc, dirac_prec prec,
+                         double rho, int nsteps, void *stream);
 
 /* Copy the operator's W links W_s(n) (Brillouin only) into the device
  * buffer w_out (w_bytes long, not overlapping the operator), layout
@@ -204,6 +222,17 @@ int dirac_apply_normal(const dirac_op *op, const void *psi_in, void *psi_out, do
  * Calls on one operator must not run concurrently. */
 int dirac_apply_host(const dirac_op *op, const void *host_in, void *host_out, double m0,
                      int dagger, void *stream);
+/* dirac_apply_host without the final synchronisation, so that the host
+ * applies of several operators overlap (one operator's stencil runs while
+ * another's slabs are copied).  Returns once everything is enqueued; host_out
+ * is complete when `stream` reaches the point after the call.  host_in must
+ * be ready when the call is made: the copies in wait only for this
+ * operator's previous host apply (its staging buffers), not for earlier work
+ * on `stream`.  Both host buffers must stay valid (and host_in unchanged)
+ * until then; calls on one operator are ordered, calls on different
+ * operators may share `stream`. */
+int dirac_apply_host_async(const dirac_op *op, const void *host_in, void *host_out, double m0,
+                           int dagger, void *stream);
 
 /* ----------------------------------------------------- launch tuning
  * A stencil launch variant is (vr, minb, block): vr = right-hand sides per

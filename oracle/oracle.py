@@ -276,6 +276,90 @@ def stout_smear(U, rho=0.12, nsteps=3):
     return V
 
 
+def _expi_frechet(Q, G):
+    """L(iQ, G), the Frechet derivative of the matrix exponential at iQ (Q
+    hermitian) in the direction G, by the Daleckii-Krein formula in the
+    eigenbasis Q = V diag(w) V^dag: L = V [F o (V^dag G V)] V^dag with the
+    divided differences F_jk = (e^{i w_j} - e^{i w_k}) / (i w_j - i w_k)
+    = e^{i (w_j + w_k)/2} sinc((w_j - w_k)/2) (e^{i w_j} on the diagonal).
+    It also gives the adjoint: tr[L(iQ, E) G] = tr[E L(iQ, G)]."""
+    w, v = np.linalg.eigh(Q)
+    h = 0.5 * (w[..., :, None] - w[..., None, :])
+    F = np.exp(0.5j * (w[..., :, None] + w[..., None, :])) * np.sinc(h / np.pi)
+    Gt = _dag(v) @ G @ v
+    return v @ (F * Gt) @ _dag(v)
+
+
+def _stout_parts(U, mu, rho):
+    """Staple sum C (times rho), Q and exp(iQ) of one stout step for links mu."""
+    nc = U.shape[-1]
+    Umu = U[..., mu, :, :]
+    C = np.zeros_like(Umu)
+    for nu in range(4):
+        if nu == mu:
+            continue
+        Unu = U[..., nu, :, :]
+        C += Unu @ _shift_links(Umu, nu, 1) @ _dag(_shift_links(Unu, mu, 1))
+        C += _dag(_shift_links(Unu, nu, -1)) @ _shift_links(Umu, nu, -1) @ _shift_links(_shift_links(Unu, nu, -1), mu, 1)
+    C = rho * C
+    Om = C @ _dag(Umu)
+    D = _dag(Om) - Om
+    Q = 0.5j * D - (0.5j / nc) * np.trace(D, axis1=-2, axis2=-1)[..., None, None] * np.eye(nc)
+    return C, Q, _expi_herm(Q)
+
+
+def stout_backward(U, G_V, rho=0.12, nsteps=3):
+    """Chain rule of the link derivative through nsteps stout steps (derived
+    here; the paper only cites the smearing): given G_V with
+    dS = Re sum conj(G_V) dV for V = stout_smear(U), returns G_U with
+    dS = Re sum conj(G_U) dU.  In the form dS = Re sum tr[dV Sigma'] (Sigma'
+    = G_V^dag) one step V = exp(iQ) U, Q from Omega = C U^dag, gives
+      Sigma = Sigma' e^{iQ} - C^dag Xi  plus the staple terms of Y = U^dag Xi,
+      Xi = the anti-hermitian part of Lambda - tr(Lambda)/N,
+      Lambda = L(iQ, U Sigma')            (tr[d e^{iQ} U Sigma'] = tr[i dQ Lambda]),
+    and every link in the staples of C_mu(x) receives the derivative of
+    rho tr[d(staple) Y_mu(x)], one term per factor (the dagger of the
+    transported product for a factor that enters daggered).  The
+    intermediate fields are recomputed from U."""
+    fields = [np.array(U, np.complex128)]
+    for _ in range(nsteps):
+        fields.append(stout_smear(fields[-1], rho, 1))
+    Sig = _dag(np.asarray(G_V, np.complex128))
+    sh = lambda A, mu, k: _shift_links(A, mu, k)
+    for i in reversed(range(nsteps)):
+        Uin = fields[i]
+        new = np.zeros_like(Sig)
+        Y = np.zeros_like(Sig)
+        for mu in range(4):
+            C, Q, E = _stout_parts(Uin, mu, rho)
+            Umu = Uin[..., mu, :, :]
+            Lam = _expi_frechet(Q, Umu @ Sig[..., mu, :, :])
+            nc = Lam.shape[-1]
+            Lp = Lam - (np.trace(Lam, axis1=-2, axis2=-1) / nc)[..., None, None] * np.eye(nc)
+            Xi = 0.5 * (Lp - _dag(Lp))
+            new[..., mu, :, :] += Sig[..., mu, :, :] @ E - _dag(C) @ Xi
+            Y[..., mu, :, :] = _dag(Umu) @ Xi
+        for mu in range(4):
+            Ym = Y[..., mu, :, :]
+            Umu = Uin[..., mu, :, :]
+            for nu in range(4):
+                if nu == mu:
+                    continue
+                Unu = Uin[..., nu, :, :]
+                # up staple U_nu(x) U_mu(x+nu) U_nu(x+mu)^dag of link (x, mu)
+                new[..., nu, :, :] += rho * sh(Umu, nu, 1) @ _dag(sh(Unu, mu, 1)) @ Ym
+                new[..., mu, :, :] += rho * sh(_dag(sh(Unu, mu, 1)) @ Ym @ Unu, nu, -1)
+                new[..., nu, :, :] += rho * sh(_dag(Ym @ Unu @ sh(Umu, nu, 1)), mu, -1)
+                # down staple U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu) of link (x, mu)
+                Unb, Umb = sh(Unu, nu, -1), sh(Umu, nu, -1)
+                Unbm = sh(Unb, mu, 1)
+                new[..., nu, :, :] += rho * sh(_dag(Umb @ Unbm @ Ym), nu, 1)
+                new[..., mu, :, :] += rho * sh(Unbm @ Ym @ _dag(Unb), nu, 1)
+                new[..., nu, :, :] += rho * sh(sh(Ym @ _dag(Unb) @ Umb, nu, 1), mu, -1)
+        Sig = new
+    return _dag(Sig)
+
+
 def gamma5(psi):
     nt, nz, ny, nx, nc, _, nv = psi.shape
     psi = np.ascontiguousarray(psi, np.complex128)

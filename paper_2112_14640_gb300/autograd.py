@@ -51,6 +51,27 @@ class _Action(torch.autograd.Function):
         return gU, gphi, None, None, None, None, None, None, None
 
 
+class _Stout(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, U, rho, nsteps):
+        ctx.rho, ctx.nsteps = rho, nsteps
+        ctx.save_for_backward(U)
+        return D.stout_smear(U.detach().contiguous(), rho, nsteps)
+
+    @staticmethod
+    def backward(ctx, gV):
+        U, = ctx.saved_tensors
+        gU = D.stout_backward(U.detach().contiguous(), gV.contiguous().to(U.dtype), ctx.rho, ctx.nsteps)
+        return gU, None, None
+
+
+def stout_smear(U, rho=0.12, nsteps=3):
+    """Differentiable stout smearing V(U) (dirac_stout_smear forward,
+    dirac_stout_backward for the gradient): composes with PseudofermionAction
+    to give the force of an operator built from smeared links."""
+    return _Stout.apply(U, float(rho), int(nsteps))
+
+
 class PseudofermionAction:
     """Differentiable S(U, phi) for the Wilson (default), staggered or
     Brillouin operator on one lattice shape.

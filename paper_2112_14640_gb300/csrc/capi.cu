@@ -18,6 +18,7 @@ constexpr int kMaxSlabs = 8;
 struct dirac_host_pipe {
     cudaStream_t h2d = nullptr, d2h = nullptr;
     cudaEvent_t in_done[kMaxSlabs] = {}, out_ready[kMaxSlabs] = {}, start = nullptr, end = nullptr;
+    bool used = false;   // `end` has been recorded by an earlier call
 };
 
 using namespace dgb;
@@ -355,6 +356,22 @@ int dirac_stout_smear(const void *U_in, void *V_out, const int dims[4], int nc, 
     return rc;
 }
 
+int dirac_stout_backward(const void *U_in, const void *G_V, void *G_U, const int dims[4], int nc, dirac_prec prec,
+                         double rho, int nsteps, void *stream) {
+    if (!U_in || !G_V || !G_U || !dims || nsteps < 0 || nsteps > 1000 || !std::isfinite(rho))
+        return DIRAC_ERR_INVALID_ARG;
+    for (int m = 0; m < 4; ++m)
+        if (dims[m] < 2) return DIRAC_ERR_INVALID_ARG;
+    if (prec != DIRAC_F64 && prec != DIRAC_F32) return DIRAC_ERR_UNSUPPORTED_PREC;
+    if (!nc_supported(nc, prec)) return DIRAC_ERR_UNSUPPORTED_NC;
+    const long long V = (long long)dims[0] * dims[1] * dims[2] * dims[3];
+    if (V > (1LL << 31)) return DIRAC_ERR_INVALID_ARG;
+    if (G_V == G_U || U_in == G_U) return DIRAC_ERR_INVALID_ARG;
+    if (nc > kMaxNcSmall) return DIRAC_ERR_UNSUPPORTED_NC;
+    const Lat g{dims[0], dims[1], dims[2], dims[3], 1, V, 0, V};
+    return launch_stout_backward(U_in, G_V, G_U, g, nc, prec, rho, nsteps, (cudaStream_t)stream);
+}
+
 int dirac_op_copy_w(const dirac_op *op, void *w_out, void *stream) {
     if (!op || !w_out || !uses_w(op->kind)) return DIRAC_ERR_INVALID_ARG;
     return launch_unpack_w(op, w_out, (cudaStream_t)stream);
@@ -500,7 +517,8 @@ static int copy_slab(const dirac_op *op, void *dst, const void *src, int t0, int
     return DIRAC_OK;
 }
 
-int dirac_apply_host(const dirac_op *op, const void *host_in, void *host_out, double m0, int dagger, void *stream) {
+static int host_apply(const dirac_op *op, const void *host_in, void *host_out, double m0, int dagger, void *stream,
+                      bool sync) {
     if (!op || !host_in || !host_out) return DIRAC_ERR_INVALID_ARG;
     dirac_op *self = (dirac_op *)op;
     int rc = DIRAC_OK;
@@ -516,7 +534,7 @@ int dirac_apply_host(const dirac_op *op, const void *host_in, void *host_out, do
         if (!rc) rc = op_apply(op, self->stage_in, self->stage_out, m0, sgn, s);
         if (!rc) rc = cuda_check(cudaMemcpyAsync(host_out, self->stage_out, op->vec_bytes, cudaMemcpyDeviceToHost, s),
                                  "D2H");
-        if (!rc) rc = cuda_check(cudaStreamSynchronize(s), "apply_host sync");
+        if (!rc && sync) rc = cuda_check(cudaStreamSynchronize(s), "apply_host sync");
         return rc;
     }
     // Pipelined: slab k = time slices [k nt / K, (k+1) nt / K) goes in on the
@@ -528,9 +546,17 @@ int dirac_apply_host(const dirac_op *op, const void *host_in, void *host_out, do
     dirac_host_pipe *p = nullptr;
     CTRY(pipe_get(self, &p));
     auto t_of = [&](int k) { return (int)((long long)k * nt / K); };
-    CTRY(cuda_check(cudaEventRecord(p->start, s), "pipe event"));          // staging buffers free
-    CTRY(cuda_check(cudaStreamWaitEvent(p->h2d, p->start, 0), "pipe wait"));
-    CTRY(cuda_check(cudaStreamWaitEvent(p->d2h, p->start, 0), "pipe wait"));
+    if (sync) {
+        CTRY(cuda_check(cudaEventRecord(p->start, s), "pipe event"));      // staging buffers free
+        CTRY(cuda_check(cudaStreamWaitEvent(p->h2d, p->start, 0), "pipe wait"));
+        CTRY(cuda_check(cudaStreamWaitEvent(p->d2h, p->start, 0), "pipe wait"));
+    } else if (p->used) {
+        // asynchronous form: the staging buffers are free once this
+        // operator's previous host apply has copied its output out; earlier
+        // work of other operators on `stream` is not waited for, so their
+        // computation overlaps these copies
+        CTRY(cuda_check(cudaStreamWaitEvent(p->h2d, p->end, 0), "pipe wait"));
+    }
     for (int k = 0; k < K; ++k) {
         CTRY(copy_slab(op, self->stage_in, host_in, t_of(k), t_of(k + 1), cudaMemcpyHostToDevice, p->h2d));
         CTRY(cuda_check(cudaEventRecord(p->in_done[k], p->h2d), "pipe event"));
@@ -549,8 +575,18 @@ int dirac_apply_host(const dirac_op *op, const void *host_in, void *host_out, do
         CTRY(copy_slab(op, host_out, self->stage_out, t_of(k), t_of(k + 1), cudaMemcpyDeviceToHost, p->d2h));
     }
     CTRY(cuda_check(cudaEventRecord(p->end, p->d2h), "pipe event"));
+    p->used = true;
     CTRY(cuda_check(cudaStreamWaitEvent(s, p->end, 0), "pipe wait"));
-    return cuda_check(cudaStreamSynchronize(s), "apply_host sync");
+    return sync ? cuda_check(cudaStreamSynchronize(s), "apply_host sync") : DIRAC_OK;
+}
+
+int dirac_apply_host(const dirac_op *op, const void *host_in, void *host_out, double m0, int dagger, void *stream) {
+    return host_apply(op, host_in, host_out, m0, dagger, stream, true);
+}
+
+int dirac_apply_host_async(const dirac_op *op, const void *host_in, void *host_out, double m0, int dagger,
+                           void *stream) {
+    return host_apply(op, host_in, host_out, m0, dagger, stream, false);
 }
 
 int dirac_vec_norm2(const dirac_op *op, const void *v, double *out_dev, void *stream) {

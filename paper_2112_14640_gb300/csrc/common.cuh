@@ -165,15 +165,33 @@ struct Coord {
     int x, y, z, t;
 };
 
+// Site coordinates with 32-bit unsigned division: volumes are at most 2^31
+// sites (checked when an operator is created), and a 64-bit division is a
+// long instruction sequence that every stencil thread would pay six times.
 __device__ __forceinline__ Coord site_coords(const Lat &g, long long n) {
     Coord c;
-    c.x = (int)(n % g.nx);
-    long long r = n / g.nx;
-    c.y = (int)(r % g.ny);
-    r /= g.ny;
-    c.z = (int)(r % g.nz);
-    c.t = (int)(r / g.nz);
+    const unsigned u = (unsigned)n;
+    unsigned r = u / (unsigned)g.nx;
+    c.x = (int)(u - r * (unsigned)g.nx);
+    unsigned r2 = r / (unsigned)g.ny;
+    c.y = (int)(r - r2 * (unsigned)g.ny);
+    r = r2 / (unsigned)g.nz;
+    c.z = (int)(r2 - r * (unsigned)g.nz);
+    c.t = (int)r;
     return c;
+}
+
+// Thread index -> (output site offset i, RHS chunk j) of a stencil launch,
+// with 32-bit division whenever the index fits.
+__device__ __forceinline__ void split_tid(long long tid, int nchunk, long long &i, int &j) {
+    if (tid < 0xFFFFFFFFLL) {
+        const unsigned t = (unsigned)tid, q = t / (unsigned)nchunk;
+        i = q;
+        j = (int)(t - q * (unsigned)nchunk);
+    } else {
+        i = tid / nchunk;
+        j = (int)(tid - i * nchunk);
+    }
 }
 
 // Site index of the neighbour n + sign * mu-hat (periodic wrap).

@@ -224,6 +224,9 @@ int launch_phase_links(dirac_op *op, const void *U, dirac_prec u_prec, cudaStrea
 int launch_build_w(dirac_op *op, const void *U, dirac_prec u_prec, cudaStream_t s);
 // one stout-smearing step of a periodic field [site][mu][a][b] (F64 or F32)
 int launch_stout_step(const void *U, void *out, const Lat &g, int nc, dirac_prec prec, double rho, cudaStream_t s);
+// chain rule through nsteps stout steps (links.cu): G_V -> G_U, GRAD convention; synchronises s
+int launch_stout_backward(const void *U, const void *G_V, void *G_U, const Lat &g, int nc, dirac_prec prec, double rho,
+                          int nsteps, cudaStream_t s);
 // clover term of c_SW = op->csw from gauge field V into op->clover (allocated)
 int launch_build_clover(dirac_op *op, const void *V, dirac_prec v_prec, cudaStream_t s);
 // the stored W~ (order and scale of bril_dirs.h) back to W_s in the public order

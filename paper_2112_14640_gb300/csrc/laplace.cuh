@@ -102,9 +102,10 @@ __global__ void __launch_bounds__(stencil_max_threads(MINB), (MINB > 1 ? 1 : 0))
     const int nchunk = g.nv / VR;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= g.nsites * nchunk) return;
-    const long long i = tid / nchunk;
+    long long i;
+    int j;
+    split_tid(tid, nchunk, i, j);
     const long long n = g.n0 + i;
-    const int j = (int)(tid - i * nchunk);
     const Coord c = site_coords(g, n);
     const long long cs = L::cs_stride(g), ls = L::mat_stride(g);
 
@@ -139,9 +140,10 @@ __global__ void __launch_bounds__(stencil_max_threads(MINB), (MINB > 1 ? 1 : 0))
     const int nchunk = g.nv / VR;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= g.nsites * nchunk) return;
-    const long long i = tid / nchunk;
+    long long i;
+    int j;
+    split_tid(tid, nchunk, i, j);
     const long long n = g.n0 + i;
-    const int j = (int)(tid - i * nchunk);
     const Coord c = site_coords(g, n);
     const long long cs = L::cs_stride(g);
     // site-index steps of +1 / -1 along each axis, with the periodic wrap

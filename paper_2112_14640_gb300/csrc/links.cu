@@ -18,6 +18,7 @@
 //    from (Sec. 2, App. F), steps of Morningstar-Peardon stout smearing.
 #include "bril_dirs.h"
 #include "internal.h"
+#include "linkalg.cuh"
 
 namespace dgb {
 
@@ -25,10 +26,6 @@ struct Phases {
     int bc[4];
 };
 
-template <typename UE>
-__device__ __forceinline__ cx<double> ld_u(const UE *U, long long idx) {
-    return cx<double>{(double)U[2 * idx], (double)U[2 * idx + 1]};
-}
 
 template <typename UE, typename E>
 __global__ void phase_links_kernel(const UE *__restrict__ U, E *__restrict__ out, Lat g, Phases ph, int nc,
@@ -173,12 +170,6 @@ int launch_unpack_w(const dirac_op *op, void *out, cudaStream_t s) {
     });
 }
 
-template <typename F>
-static int dispatch_uprec(dirac_prec p, F &&f) {
-    if (p == DIRAC_F64) return f((double *)nullptr);
-    if (p == DIRAC_F32) return f((float *)nullptr);
-    return DIRAC_ERR_UNSUPPORTED_PREC;
-}
 
 static Phases phases_of(const dirac_op *op) {
     Phases ph;
@@ -225,22 +216,6 @@ int launch_build_w(dirac_op *op, const void *U, dirac_prec u_prec, cudaStream_t 
 
 // ------------------------------------------------------------ clover term
 
-template <int NC, typename AB>
-__device__ __forceinline__ void mat_mul(const cx<AB> (&X)[NC][NC], const cx<AB> (&Y)[NC][NC], cx<AB> (&Z)[NC][NC]) {
-#pragma unroll
-    for (int a = 0; a < NC; ++a)
-#pragma unroll
-        for (int b = 0; b < NC; ++b) {
-            cx<AB> t = {0, 0};
-#pragma unroll
-            for (int q = 0; q < NC; ++q) cmac(t, X[a][q], Y[q][b]);
-            Z[a][b] = t;
-        }
-}
-
-__device__ __forceinline__ void step(int (&x)[4], const int ext[4], int mu, int sign) {
-    x[mu] = sign > 0 ? (x[mu] + 1 == ext[mu] ? 0 : x[mu] + 1) : (x[mu] == 0 ? ext[mu] - 1 : x[mu] - 1);
-}
 
 // F_mu,nu at site x0 from the four leaves (+mu,+nu), (+nu,-mu), (-mu,-nu),
 // (-nu,+mu); the leaf (a, b) is V_a(n) V_b(n+a) V_-a(n+a+b) V_-b(n+b).
@@ -356,178 +331,6 @@ int launch_build_clover(dirac_op *op, const void *V, dirac_prec v_prec, cudaStre
                     (const UE *)V, (E *)op->clover, op->lat, none, op->csw, op->geom.layout);
                 return launch_check("build_clover_kernel");
             });
-        });
-    });
-}
-
-// ------------------------------------------------------------ stout smearing
-// One step, one thread per link (n, mu), FP64 arithmetic for either storage:
-//   C = rho sum_{nu != mu} [U_nu(n) U_mu(n+nu) U_nu(n+mu)^dag + U_nu(n-nu)^dag U_mu(n-nu) U_nu(n-nu+mu)],
-//   Omega = C U_mu(n)^dag,  Q = (i/2)(Omega^dag - Omega) - (i/2N) Tr(Omega^dag - Omega),
-//   U'_mu(n) = exp(iQ) U_mu(n).
-// exp(iQ) by scaling and squaring of the Taylor series (Moler and Van Loan):
-// X = iQ / 2^s with ||X||_inf <= 1/4, the series summed until a term falls
-// below 1e-17 of the partial sum (at most 30 terms), then squared s times;
-// valid for every N_c.
-
-template <int NC, typename UE>
-__device__ __forceinline__ void load_link(const UE *__restrict__ U, const Lat &g, const int x[4], int mu,
-                                          cx<double> (&L)[NC][NC]) {
-    const long long site = (((long long)x[3] * g.nz + x[2]) * g.ny + x[1]) * g.nx + x[0];
-    const long long base = (site * 4 + mu) * NC * NC;
-#pragma unroll
-    for (int a = 0; a < NC; ++a)
-#pragma unroll
-        for (int b = 0; b < NC; ++b) L[a][b] = ld_u(U, base + a * NC + b);
-}
-
-template <int NC>
-__device__ __forceinline__ void mul_nn(const cx<double> (&X)[NC][NC], const cx<double> (&Y)[NC][NC],
-                                       cx<double> (&Z)[NC][NC]) {
-    mat_mul<NC, double>(X, Y, Z);
-}
-
-// Z = X Y^dag
-template <int NC>
-__device__ __forceinline__ void mul_nd(const cx<double> (&X)[NC][NC], const cx<double> (&Y)[NC][NC],
-                                       cx<double> (&Z)[NC][NC]) {
-#pragma unroll
-    for (int a = 0; a < NC; ++a)
-#pragma unroll
-        for (int b = 0; b < NC; ++b) {
-            cx<double> t = {0, 0};
-#pragma unroll
-            for (int q = 0; q < NC; ++q) cmac_conj(t, Y[b][q], X[a][q]);
-            Z[a][b] = t;
-        }
-}
-
-// Z = X^dag Y
-template <int NC>
-__device__ __forceinline__ void mul_dn(const cx<double> (&X)[NC][NC], const cx<double> (&Y)[NC][NC],
-                                       cx<double> (&Z)[NC][NC]) {
-#pragma unroll
-    for (int a = 0; a < NC; ++a)
-#pragma unroll
-        for (int b = 0; b < NC; ++b) {
-            cx<double> t = {0, 0};
-#pragma unroll
-            for (int q = 0; q < NC; ++q) cmac_conj(t, X[q][a], Y[q][b]);
-            Z[a][b] = t;
-        }
-}
-
-template <int NC>
-__device__ void expm_taylor(cx<double> (&X)[NC][NC], cx<double> (&E)[NC][NC]) {
-    double nrm = 0;
-    for (int a = 0; a < NC; ++a) {
-        double r = 0;
-        for (int b = 0; b < NC; ++b) r += sqrt(X[a][b].re * X[a][b].re + X[a][b].im * X[a][b].im);
-        nrm = fmax(nrm, r);
-    }
-    int sq = 0;
-    while (nrm > 0.25 && sq < 40) {
-        nrm *= 0.5;
-        ++sq;
-    }
-    const double f = ldexp(1.0, -sq);
-    cx<double> T[NC][NC], P[NC][NC];
-    for (int a = 0; a < NC; ++a)
-        for (int b = 0; b < NC; ++b) {
-            X[a][b] = cx<double>{f * X[a][b].re, f * X[a][b].im};
-            T[a][b] = cx<double>{a == b ? 1.0 : 0.0, 0.0};
-            E[a][b] = T[a][b];
-        }
-    for (int k = 1; k <= 30; ++k) {
-        mat_mul<NC, double>(T, X, P);   // T_k = T_{k-1} X / k
-        double tn = 0, en = 0;
-        for (int a = 0; a < NC; ++a)
-            for (int b = 0; b < NC; ++b) {
-                T[a][b] = cx<double>{P[a][b].re / k, P[a][b].im / k};
-                E[a][b] = E[a][b] + T[a][b];
-                tn = fmax(tn, fabs(T[a][b].re) + fabs(T[a][b].im));
-                en = fmax(en, fabs(E[a][b].re) + fabs(E[a][b].im));
-            }
-        if (tn <= 1e-17 * en) break;
-    }
-    for (int i = 0; i < sq; ++i) {
-        mat_mul<NC, double>(E, E, P);
-        for (int a = 0; a < NC; ++a)
-            for (int b = 0; b < NC; ++b) E[a][b] = P[a][b];
-    }
-}
-
-template <int NC, typename UE>
-__global__ void __launch_bounds__(128) stout_step_kernel(const UE *__restrict__ U, UE *__restrict__ out, Lat g,
-                                                         double rho) {
-    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (tid >= g.V * 4) return;
-    const long long n = tid / 4;
-    const int mu = (int)(tid % 4);
-    const Coord c = site_coords(g, n);
-    const int x0[4] = {c.x, c.y, c.z, c.t};
-    const int ext[4] = {g.nx, g.ny, g.nz, g.nt};
-    cx<double> Cs[NC][NC], A[NC][NC], B[NC][NC], T[NC][NC];
-    for (int a = 0; a < NC; ++a)
-        for (int b = 0; b < NC; ++b) Cs[a][b] = cx<double>{0, 0};
-    for (int nu = 0; nu < 4; ++nu) {
-        if (nu == mu) continue;
-        int xm[4] = {x0[0], x0[1], x0[2], x0[3]}, xn[4] = {x0[0], x0[1], x0[2], x0[3]};
-        step(xm, ext, mu, +1);   // n + mu
-        step(xn, ext, nu, +1);   // n + nu
-        // forward staple U_nu(n) U_mu(n+nu) U_nu(n+mu)^dag
-        load_link<NC, UE>(U, g, x0, nu, A);
-        load_link<NC, UE>(U, g, xn, mu, B);
-        mul_nn<NC>(A, B, T);
-        load_link<NC, UE>(U, g, xm, nu, A);
-        mul_nd<NC>(T, A, B);
-        for (int a = 0; a < NC; ++a)
-            for (int b = 0; b < NC; ++b) Cs[a][b] = Cs[a][b] + B[a][b];
-        // backward staple U_nu(n-nu)^dag U_mu(n-nu) U_nu(n-nu+mu)
-        int xb[4] = {x0[0], x0[1], x0[2], x0[3]};
-        step(xb, ext, nu, -1);   // n - nu
-        int xbm[4] = {xb[0], xb[1], xb[2], xb[3]};
-        step(xbm, ext, mu, +1);  // n - nu + mu
-        load_link<NC, UE>(U, g, xb, nu, A);
-        load_link<NC, UE>(U, g, xb, mu, B);
-        mul_dn<NC>(A, B, T);
-        load_link<NC, UE>(U, g, xbm, nu, A);
-        mul_nn<NC>(T, A, B);
-        for (int a = 0; a < NC; ++a)
-            for (int b = 0; b < NC; ++b) Cs[a][b] = Cs[a][b] + B[a][b];
-    }
-    // Omega = rho C U_mu(n)^dag
-    load_link<NC, UE>(U, g, x0, mu, A);
-    mul_nd<NC>(Cs, A, T);
-    // X = iQ = -(1/2) D + (1/2N) Tr(D), D = Omega^dag - Omega: traceless anti-hermitian
-    for (int a = 0; a < NC; ++a)
-        for (int b = 0; b < NC; ++b) {
-            // D = Omega^dag - Omega, element (a, b) = conj(Om[b][a]) - Om[a][b]
-            const cx<double> d = {rho * (T[b][a].re - T[a][b].re), rho * (-T[b][a].im - T[a][b].im)};
-            B[a][b] = cx<double>{-0.5 * d.re, -0.5 * d.im};
-        }
-    // subtract Tr(-D/2)/N from the diagonal
-    cx<double> trx = {0, 0};
-    for (int a = 0; a < NC; ++a) trx = trx + B[a][a];
-    for (int a = 0; a < NC; ++a) B[a][a] = B[a][a] - cx<double>{trx.re / NC, trx.im / NC};
-    expm_taylor<NC>(B, T);
-    mul_nn<NC>(T, A, B);
-    const long long base = tid * NC * NC;
-    for (int a = 0; a < NC; ++a)
-        for (int b = 0; b < NC; ++b) {
-            out[2 * (base + a * NC + b)] = (UE)B[a][b].re;
-            out[2 * (base + a * NC + b) + 1] = (UE)B[a][b].im;
-        }
-}
-
-int launch_stout_step(const void *U, void *out, const Lat &g, int nc, dirac_prec prec, double rho, cudaStream_t s) {
-    return dispatch_uprec(prec, [&](auto utag) {
-        using UE = std::remove_pointer_t<decltype(utag)>;
-        return dispatch_nc(nc, [&](auto ncc) {
-            constexpr int NC = decltype(ncc)::value;
-            const long long threads = g.V * 4;
-            stout_step_kernel<NC, UE><<<grid_for(threads, 128), 128, 0, s>>>((const UE *)U, (UE *)out, g, rho);
-            return launch_check("stout_step_kernel");
         });
     });
 }

@@ -13,6 +13,10 @@
 
 namespace dgb {
 
+template <int NC, int VR, bool DAG, typename E, typename A>
+__device__ __forceinline__ void stag_hop_m(cx<A> (&acc)[NC][VR], const cx<A> (&L)[NC][NC],
+                                           const E *__restrict__ phi, long long cs_stride, A f);
+
 template <int NC, int VR, bool DAG, typename E, typename A, typename EL>
 __device__ __forceinline__ void stag_hop(cx<A> (&acc)[NC][VR], const EL *__restrict__ link, long long lstride,
                                          const E *__restrict__ phi, long long cs_stride, A f) {
@@ -41,6 +45,13 @@ __device__ __forceinline__ void stag_hop(cx<A> (&acc)[NC][VR], const EL *__restr
     }
     cx<A> L[NC][NC];
     load_mat_s<NC, EL, A>(link, lstride, L);
+    stag_hop_m<NC, VR, DAG, E, A>(acc, L, phi, cs_stride, f);
+}
+
+// One hop with the link matrix already in registers (N_c <= 4).
+template <int NC, int VR, bool DAG, typename E, typename A>
+__device__ __forceinline__ void stag_hop_m(cx<A> (&acc)[NC][VR], const cx<A> (&L)[NC][NC],
+                                           const E *__restrict__ phi, long long cs_stride, A f) {
     cx<A> p[NC][VR];
 #pragma unroll
     for (int c = 0; c < NC; ++c) load_cx<E, VR, A>(phi + 2 * c * cs_stride, p[c]);
@@ -66,9 +77,10 @@ __global__ void __launch_bounds__(stencil_max_threads(MINB), (MINB > 1 ? 1 : 0))
     const int nchunk = g.nv / VR;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= g.nsites * nchunk) return;
-    const long long i = tid / nchunk;
+    long long i;
+    int j;
+    split_tid(tid, nchunk, i, j);
     const long long n = g.n0 + i;
-    const int j = (int)(tid - i * nchunk);
     const Coord c = site_coords(g, n);
     using L = Layout<LAYOUT>;
     const long long cs = L::cs_stride(g), ls = L::mat_stride(g);
@@ -86,10 +98,19 @@ __global__ void __launch_bounds__(stencil_max_threads(MINB), (MINB > 1 ? 1 : 0))
         const A eta = (e[mu] & 1) ? (A)-1 : (A)1;
         const long long fw = neighbour(g, n, c, mu, +1);
         const long long bw = neighbour(g, n, c, mu, -1);
-        stag_hop<NC, VR, false>(acc, U + 2 * L::template mat<NC>(g, n, 4, mu), ls,
-                                in + 2 * (L::vec(g, fw, NC, 0) + (long long)j * VR), cs, eta);
-        stag_hop<NC, VR, true>(acc, U + 2 * L::template mat<NC>(g, bw, 4, mu), ls,
-                               in + 2 * (L::vec(g, bw, NC, 0) + (long long)j * VR), cs, -eta);
+        if constexpr (NC <= kMaxNcSmall) {
+            // both links of the direction requested before either hop
+            cx<A> Lf[NC][NC], Lb[NC][NC];
+            load_mat_s<NC, EL, A>(U + 2 * L::template mat<NC>(g, n, 4, mu), ls, Lf);
+            load_mat_s<NC, EL, A>(U + 2 * L::template mat<NC>(g, bw, 4, mu), ls, Lb);
+            stag_hop_m<NC, VR, false, E, A>(acc, Lf, in + 2 * (L::vec(g, fw, NC, 0) + (long long)j * VR), cs, eta);
+            stag_hop_m<NC, VR, true, E, A>(acc, Lb, in + 2 * (L::vec(g, bw, NC, 0) + (long long)j * VR), cs, -eta);
+        } else {
+            stag_hop<NC, VR, false>(acc, U + 2 * L::template mat<NC>(g, n, 4, mu), ls,
+                                    in + 2 * (L::vec(g, fw, NC, 0) + (long long)j * VR), cs, eta);
+            stag_hop<NC, VR, true>(acc, U + 2 * L::template mat<NC>(g, bw, 4, mu), ls,
+                                   in + 2 * (L::vec(g, bw, NC, 0) + (long long)j * VR), cs, -eta);
+        }
     }
 
     const long long base = 2 * (L::vec(g, n, NC, 0) + (long long)j * VR);

@@ -59,6 +59,10 @@ __device__ __forceinline__ void reconstruct(cx<A> &o0, cx<A> &o1, cx<A> &o2, cx<
     }
 }
 
+template <int MU, bool DAG, int NC, int VR, typename E, typename A>
+__device__ __forceinline__ void wilson_hop_m(cx<A> (&acc)[NC][4][VR], const cx<A> (&L)[NC][NC],
+                                             const E *__restrict__ psi, long long cs_stride, A a);
+
 // One hop: acc += (1 + a gamma_MU) (x) L psi(m), L = link or link^dag.  The
 // link elements are lstride complex numbers apart, the spinor components
 // cs_stride apart (both depend on the layout).
@@ -102,6 +106,13 @@ __device__ __forceinline__ void wilson_hop(cx<A> (&acc)[NC][4][VR], const EL *__
     }
     cx<A> L[NC][NC];
     load_mat_s<NC, EL, A>(link, lstride, L);
+    wilson_hop_m<MU, DAG, NC, VR, E, A>(acc, L, psi, cs_stride, a);
+}
+
+// One hop with the link matrix already in registers (N_c <= 4).
+template <int MU, bool DAG, int NC, int VR, typename E, typename A>
+__device__ __forceinline__ void wilson_hop_m(cx<A> (&acc)[NC][4][VR], const cx<A> (&L)[NC][NC],
+                                             const E *__restrict__ psi, long long cs_stride, A a) {
     cx<A> h[NC][2][VR];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
@@ -139,12 +150,23 @@ __device__ __forceinline__ void wilson_dir(cx<A> (&acc)[NC][4][VR], const EL *__
     const long long fw = neighbour(g, n, c, MU, +1);
     const long long bw = neighbour(g, n, c, MU, -1);
     const long long cs = L::cs_stride(g), ls = L::mat_stride(g);
-    // forward: (1 - sgn gamma) U_mu(n) psi(n+mu)
-    wilson_hop<MU, false, NC, VR>(acc, U + 2 * L::template mat<NC>(g, n, 4, MU), ls,
-                                  in + 2 * (L::vec(g, fw, NC * 4, 0) + (long long)j * VR), cs, -sgn);
-    // backward: (1 + sgn gamma) U_mu(n-mu)^dag psi(n-mu)
-    wilson_hop<MU, true, NC, VR>(acc, U + 2 * L::template mat<NC>(g, bw, 4, MU), ls,
-                                 in + 2 * (L::vec(g, bw, NC * 4, 0) + (long long)j * VR), cs, sgn);
+    if constexpr (NC <= kMaxNcSmall) {
+        // both links of the direction are requested before either hop, so
+        // their loads are in flight together
+        cx<A> Lf[NC][NC], Lb[NC][NC];
+        load_mat_s<NC, EL, A>(U + 2 * L::template mat<NC>(g, n, 4, MU), ls, Lf);
+        load_mat_s<NC, EL, A>(U + 2 * L::template mat<NC>(g, bw, 4, MU), ls, Lb);
+        // forward: (1 - sgn gamma) U_mu(n) psi(n+mu); backward: (1 + sgn gamma) U_mu(n-mu)^dag psi(n-mu)
+        wilson_hop_m<MU, false, NC, VR, E, A>(acc, Lf, in + 2 * (L::vec(g, fw, NC * 4, 0) + (long long)j * VR), cs,
+                                              -sgn);
+        wilson_hop_m<MU, true, NC, VR, E, A>(acc, Lb, in + 2 * (L::vec(g, bw, NC * 4, 0) + (long long)j * VR), cs,
+                                             sgn);
+    } else {
+        wilson_hop<MU, false, NC, VR>(acc, U + 2 * L::template mat<NC>(g, n, 4, MU), ls,
+                                      in + 2 * (L::vec(g, fw, NC * 4, 0) + (long long)j * VR), cs, -sgn);
+        wilson_hop<MU, true, NC, VR>(acc, U + 2 * L::template mat<NC>(g, bw, 4, MU), ls,
+                                     in + 2 * (L::vec(g, bw, NC * 4, 0) + (long long)j * VR), cs, sgn);
+    }
 }
 
 template <int NC, int VR, typename E, int MINB, int LAYOUT, typename EL, int CLOV>
@@ -155,9 +177,10 @@ __global__ void __launch_bounds__(stencil_max_threads(MINB), (MINB > 1 ? 1 : 0))
     const int nchunk = g.nv / VR;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= g.nsites * nchunk) return;
-    const long long i = tid / nchunk;
+    long long i;
+    int j;
+    split_tid(tid, nchunk, i, j);
     const long long n = g.n0 + i;
-    const int j = (int)(tid - i * nchunk);
     const Coord c = site_coords(g, n);
 
     cx<A> acc[NC][4][VR];

@@ -76,11 +76,13 @@ SIGNATURES = {
     "dirac_op_copy_w": (_I, [_P, _P, _P]),
     "dirac_op_set_clover": (_I, [_P, _D, _P, _I, _P]),
     "dirac_stout_smear": (_I, [_P, _P, ctypes.POINTER(_I), _I, _I, _D, _I, _P]),
+    "dirac_stout_backward": (_I, [_P, _P, _P, ctypes.POINTER(_I), _I, _I, _D, _I, _P]),
     "dirac_op_destroy": (None, [_P]),
     "dirac_apply": (_I, [_P, _P, _P, _D, _P]),
     "dirac_apply_dagger": (_I, [_P, _P, _P, _D, _P]),
     "dirac_apply_normal": (_I, [_P, _P, _P, _D, _P]),
     "dirac_apply_host": (_I, [_P, _P, _P, _D, _I, _P]),
+    "dirac_apply_host_async": (_I, [_P, _P, _P, _D, _I, _P]),
     "dirac_op_set_launch": (_I, [_P, _I, _I, _I]),
     "dirac_op_get_launch": (_I, [_P, ctypes.POINTER(_I), ctypes.POINTER(_I), ctypes.POINTER(_I)]),
     "dirac_op_autotune": (_I, [_P, _D, _P, ctypes.POINTER(_D)]),
@@ -156,6 +158,23 @@ def stout_smear(U, rho=0.12, nsteps=3, out=None, stream=None):
     prec = F64 if U.dtype == torch.complex128 else F32
     _check(lib().dirac_stout_smear(_ptr(U), _ptr(out), dims, int(U.shape[-1]), prec, float(rho), int(nsteps),
                                    _stream(stream)), "dirac_stout_smear")
+    return out
+
+
+def stout_backward(U, G_V, rho=0.12, nsteps=3, stream=None):
+    """Chain rule through stout smearing (dirac_stout_backward): for
+    V = stout_smear(U, rho, nsteps) and G_V with dS = Re sum conj(G_V) dV,
+    returns G_U with dS = Re sum conj(G_U) dU (same shape and dtype as U)."""
+    if not U.is_cuda or U.dtype not in (torch.complex128, torch.complex64) or not U.is_contiguous():
+        raise ValueError("U must be a contiguous complex128 or complex64 CUDA tensor")
+    if G_V.shape != U.shape or G_V.dtype != U.dtype or not G_V.is_contiguous():
+        raise ValueError("G_V must match U")
+    nt, nz, ny, nx = U.shape[:4]
+    out = torch.empty_like(U)
+    dims = (ctypes.c_int * 4)(nx, ny, nz, nt)
+    prec = F64 if U.dtype == torch.complex128 else F32
+    _check(lib().dirac_stout_backward(_ptr(U), _ptr(G_V), _ptr(out), dims, int(U.shape[-1]), prec, float(rho),
+                                      int(nsteps), _stream(stream)), "dirac_stout_backward")
     return out
 
 
@@ -346,6 +365,19 @@ class DiracOp:
             raise ValueError("host buffers must hold exactly one vector")
         _check(lib().dirac_apply_host(self._h, _ptr(host_in), _ptr(host_out), float(m0), int(bool(dagger)),
                                       _stream(stream)), "dirac_apply_host")
+        return host_out
+
+    def apply_host_async(self, host_in, host_out, m0=0.0, dagger=False, stream=None):
+        """apply_host without the final synchronisation (dirac_apply_host_async):
+        host_out is ready once ``stream`` (torch's current stream by default)
+        has reached this point; host applies of different operators overlap."""
+        if host_in.is_cuda or host_out.is_cuda:
+            raise ValueError("apply_host_async takes host tensors")
+        nb = self.vec_bytes()
+        if host_in.numel() * host_in.element_size() != nb or host_out.numel() * host_out.element_size() != nb:
+            raise ValueError("host buffers must hold exactly one vector")
+        _check(lib().dirac_apply_host_async(self._h, _ptr(host_in), _ptr(host_out), float(m0), int(bool(dagger)),
+                                            _stream(stream)), "dirac_apply_host_async")
         return host_out
 
     def copy_w(self, stream=None):

@@ -2,7 +2,10 @@
 smeared field element by element (FP64 1e-12, FP32 storage 1e-6 relative
 L2), in place and out of place, several N_c and step counts; and the
 paper's solver setting, where D and the clover term are both built from
-the smeared field, checked through the operators against the oracle."""
+the smeared field, checked through the operators against the oracle; and
+the chain rule of the force through the smearing (dirac_stout_backward),
+against the oracle's and, composed with the pseudofermion action by
+autograd, against finite differences."""
 import numpy as np
 import pytest
 import torch
@@ -74,3 +77,54 @@ def test_stout_extent_two():
     want = O.stout_smear(U, 0.12, 3)
     got = D.stout_smear(torch.from_numpy(U).cuda(), 0.12, 3).cpu().numpy()
     assert rel_l2(got, want) < 1e-12
+
+
+@pytest.mark.parametrize("prec,tol", [(torch.complex128, 1e-11), (torch.complex64, 1e-5)])
+@pytest.mark.parametrize("dims,nc,nsteps", [((4, 4, 2, 4), 3, 3), ((2, 4, 3, 2), 2, 1), ((4, 2, 2, 2), 4, 2)])
+def test_stout_backward_matches_oracle(prec, tol, dims, nc, nsteps):
+    """The chain rule through stout smearing on the GPU against the oracle's
+    (which is pinned by finite differences on the CPU), for a random complex
+    G_V; the block-exponential Frechet derivative against the oracle's
+    eigenbasis formula."""
+    U_np = I.gauge_field(dims, nc, 0.5, 91)
+    rng = np.random.default_rng(92)
+    G_np = rng.standard_normal(U_np.shape) + 1j * rng.standard_normal(U_np.shape)
+    U = torch.from_numpy(U_np).cuda().to(prec)
+    G = torch.from_numpy(G_np).cuda().to(prec)
+    got = D.stout_backward(U, G, 0.12, nsteps).to(torch.complex128).cpu().numpy()
+    Uw = U_np if prec == torch.complex128 else U_np.astype(np.complex64).astype(np.complex128)
+    Gw = G_np if prec == torch.complex128 else G_np.astype(np.complex64).astype(np.complex128)
+    want = O.stout_backward(Uw, Gw, 0.12, nsteps)
+    assert rel_l2(got, want) <= tol
+
+
+def test_smeared_action_autograd_and_finite_differences():
+    """S(U) = sum Re phi^dag (D_W[V]^dag D_W[V])^-1 phi with V = stout^3(U),
+    differentiated by autograd through PseudofermionAction and stout_smear:
+    against the oracle's chain rule and against central differences of the
+    GPU action along random complex directions (FP64, 4^4, N_v = 2)."""
+    from paper_2112_14640_gb300.autograd import PseudofermionAction, stout_smear
+    dims, nc, nv, m0, bc, rho, ns = (4, 4, 4, 4), 3, 2, 0.3, (1, 1, 1, -1), 0.12, 3
+    U_np = I.gauge_field(dims, nc, 0.4, 93)
+    phi_np = I.source(dims, nc, nv, 94)
+    U = torch.from_numpy(U_np).cuda().requires_grad_(True)
+    phi = torch.from_numpy(phi_np).cuda()
+    act = PseudofermionAction(m0, bc, prec=D.F64, tol=1e-13)
+    S = act(stout_smear(U, rho, ns), phi)
+    gU, = torch.autograd.grad(S, (U,))
+    V_np = O.stout_smear(U_np, rho, ns)
+    ref = O.Operator(O.WILSON, V_np, bc)
+    S_ref, psi = O.pseudofermion_action(ref, phi_np, m0)
+    assert abs(S.item() - S_ref) < 1e-10 * abs(S_ref)
+    want = O.stout_backward(U_np, O.wilson_action_gradient(ref, psi, ref.apply(psi, m0)), rho, ns)
+    assert rel_l2(gU.cpu().numpy(), want) < 1e-9
+    rng = np.random.default_rng(95)
+    for _ in range(3):
+        dU = torch.from_numpy(rng.standard_normal(U_np.shape) + 1j * rng.standard_normal(U_np.shape)).cuda()
+        eps = 1e-5
+        with torch.no_grad():
+            Sp = act(stout_smear(U + eps * dU, rho, ns), phi).item()
+            Sm = act(stout_smear(U - eps * dU, rho, ns), phi).item()
+        fd = (Sp - Sm) / (2 * eps)
+        an = torch.sum(torch.real(torch.conj(gU) * dU)).item()
+        assert abs(fd - an) < 1e-6 * abs(an), (fd, an)

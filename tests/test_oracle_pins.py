@@ -1111,3 +1111,63 @@ def test_dense_elementwise_matches_oracle_apply(kind, dims, nc):
     want = _dense_elementwise(kind, U, bc, m0, dims, rho, lam)
     got = dense(op.apply, shape)
     assert np.abs(got - want).max() < 1e-13 * np.abs(want).max()
+
+
+# ------------------------------------------ chain rule through stout smearing
+
+def _smeared_action_and_gradient(U, phi, bc, m0, rho, nsteps, kind=O.WILSON):
+    V = O.stout_smear(U, rho, nsteps)
+    op = O.Operator(kind, V, bc)
+    S, psi = O.pseudofermion_action(op, phi, m0, tol=1e-14)
+    chi = op.apply(psi, m0)
+    GV = {O.WILSON: O.wilson_action_gradient, O.STAGGERED: O.staggered_action_gradient,
+          O.BRILLOUIN: O.brillouin_action_gradient}[kind](op, psi, chi)
+    return S, GV
+
+
+def _fd_check(U, phi, bc, m0, rho, nsteps, GU, kind, rng, count=2):
+    worst = 0.0
+    for _ in range(count):
+        dU = rng.standard_normal(U.shape) + 1j * rng.standard_normal(U.shape)
+        eps = 1e-5
+        Sp = O.pseudofermion_action(O.Operator(kind, O.stout_smear(U + eps * dU, rho, nsteps), bc), phi, m0,
+                                    tol=1e-14)[0]
+        Sm = O.pseudofermion_action(O.Operator(kind, O.stout_smear(U - eps * dU, rho, nsteps), bc), phi, m0,
+                                    tol=1e-14)[0]
+        fd = (Sp - Sm) / (2 * eps)
+        an = float(np.sum(np.real(np.conj(GU) * dU)))
+        worst = max(worst, abs(fd - an) / abs(an))
+    return worst
+
+
+@pytest.mark.parametrize("kind", [O.WILSON, O.STAGGERED])
+def test_stout_chain_rule_matches_finite_differences(kind):
+    """S(U) = sum Re phi^dag (D[V]^dag D[V])^-1 phi with V = stout^2(U): the
+    gradient carried back through the two stout steps (oracle.stout_backward)
+    against central differences along random complex directions dU."""
+    dims, nc, nv, m0, bc = (4, 4, 2, 4), 3, 2, 0.3, (1, 1, 1, -1)
+    U = I.gauge_field(dims, nc, 0.4, 81)
+    phi = I.source(dims, nc, nv, 82, staggered=(kind == O.STAGGERED))
+    rho, nsteps = 0.12, 2
+    _, GV = _smeared_action_and_gradient(U, phi, bc, m0, rho, nsteps, kind)
+    GU = O.stout_backward(U, GV, rho, nsteps)
+    assert _fd_check(U, phi, bc, m0, rho, nsteps, GU, kind, np.random.default_rng(3)) < 1e-7
+
+
+def test_stout_chain_rule_identity_cases_and_planted_mistake(monkeypatch):
+    """No step (or rho = 0) passes the gradient through unchanged; and a
+    Frechet derivative that treats exp(iQ) as commuting with its direction
+    (a plausible shortcut), planted in the oracle, fails the difference check."""
+    dims, nc, nv, m0, bc = (4, 2, 2, 4), 3, 2, 0.3, (1, 1, 1, -1)
+    U = I.gauge_field(dims, nc, 0.5, 83)
+    phi = I.source(dims, nc, nv, 84)
+    G = np.random.default_rng(5).standard_normal(U.shape) + 0j
+    assert np.array_equal(O.stout_backward(U, G, 0.12, 0), G)
+    assert np.abs(O.stout_backward(U, G, 0.0, 3) - G).max() < 1e-14
+    rho, nsteps = 0.12, 1
+    _, GV = _smeared_action_and_gradient(U, phi, bc, m0, rho, nsteps)
+    good = O.stout_backward(U, GV, rho, nsteps)
+    assert _fd_check(U, phi, bc, m0, rho, nsteps, good, O.WILSON, np.random.default_rng(6), 1) < 1e-7
+    monkeypatch.setattr(O.oracle, "_expi_frechet", lambda Q, G: O.oracle._expi_herm(Q) @ G)
+    bad = O.stout_backward(U, GV, rho, nsteps)
+    assert _fd_check(U, phi, bc, m0, rho, nsteps, bad, O.WILSON, np.random.default_rng(6), 1) > 1e-4
