@@ -61,7 +61,8 @@ def parse():
     p.add_argument("--solve-budget", type=float, default=240.0,
                    help="wall-clock seconds the default solver comparison may use")
     p.add_argument("--no-large", action="store_true", help="skip the 32^3x64 operator timing")
-    p.add_argument("--batch", action="store_true", help="add the config-4 batched-solve measurement")
+    p.add_argument("--no-nc-sweep", action="store_true", help="skip the N_c sweep (24^3x48, N_v = 24)")
+    p.add_argument("--no-batch", action="store_true", help="skip the config-4 batched-solve measurement")
     p.add_argument("--ncu", action="store_true", help="short run for profiler launch lists (no extras)")
     p.add_argument("--csw", type=float, default=0.0,
                    help="time D_W and D_B with the clover term of this c_SW (0: the plain operators)")
@@ -478,11 +479,13 @@ def main():
         line["large_lattice"] = large_lattice_timing(D, I, torch, pk, fp32_peak)
     if not args.ncu:
         line["force"] = force_timing(D, I, torch)
+    if not args.ncu and not args.no_nc_sweep:
+        line["nc_sweep"] = nc_sweep(D, I, torch)
     if args.solve:
         line["solve"] = solver_comparison(D, I, torch)
     elif not args.ncu and not args.no_solve:
         line["solve"] = solve_default(D, I, torch, args.solve_budget)
-    if args.batch:
+    if not args.ncu and not args.no_batch:
         line["batch"] = batch_measurement(D, I, torch)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.ncu:
@@ -514,7 +517,21 @@ def pinned_copy_rate(torch, nbytes, reps=5):
         e1.record(st)
         torch.cuda.synchronize()
         out[name] = nbytes * reps / (e0.elapsed_time(e1) * 1e-3) / 1e9
-    del h, d
+    # both directions at once, on two streams: the rate the overlapped
+    # end-to-end step can reach at best (bytes moved in both directions)
+    h2 = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d2 = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        with torch.cuda.stream(s1):
+            d.copy_(h, non_blocking=True)
+        with torch.cuda.stream(s2):
+            h2.copy_(d2, non_blocking=True)
+    torch.cuda.synchronize()
+    out["bidirectional_GBps"] = 2 * nbytes * reps / (time.perf_counter() - t0) / 1e9
+    del h, d, h2, d2
     return out
 
 
@@ -560,9 +577,46 @@ def large_lattice_timing(D, I, torch, pk, fp32_peak, dims=(32, 32, 32, 64)):
     return out
 
 
+def nc_sweep(D, I, torch, dims=(24, 24, 24, 48), nv=24, ncs=(2, 3, 4, 6, 8)):
+    """Gflop/s (App. E counts) of D_W, D_B and D_S as a function of N_c at
+    24^3x48, N_v = 24, FP32, site-inner, autotuned: the workload of the
+    paper's N_c table (Sec. "Dependence on compile-time parameters")."""
+    import numpy as np
+    V = int(np.prod(dims))
+    st = torch.cuda.current_stream()
+    out = {"lattice": "x".join(map(str, dims)), "nv": nv}
+    for nc in ncs:
+        U = torch.from_numpy(I.gauge_field(dims, nc, EPS, 900 + nc)).cuda().to(torch.complex64)
+        row = {}
+        for k in (D.WILSON, D.BRILLOUIN, D.STAGGERED):
+            op = D.DiracOp(k, U, nv, BC, D.F32, layout=D.SITE_INNER)
+            op.autotune(MASS[k])
+            x = op.new_vector()
+            x.real.normal_()
+            y = op.new_vector(zero=False)
+            op.apply(x, y, m0=MASS[k])
+            reps = 2 if k == D.BRILLOUIN else 10
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            for _ in range(reps):
+                op.apply(x, y, m0=MASS[k])
+            e1.record(st)
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1) / reps * 1e-3
+            row[D.KIND_NAMES[k]] = {"ms": t * 1e3, "gflops": D.flops_per_site(k, nc) * V * nv / t / 1e9,
+                                    "alg_GBps": alg_bytes_per_site(k, nc, nv) * V / t / 1e9}
+            op.close()
+            del x, y
+            torch.cuda.empty_cache()
+        out["nc=%d" % nc] = row
+        del U
+        torch.cuda.empty_cache()
+    return out
+
+
 def force_timing(D, I, torch, dims=(16, 16, 16, 32), nv=4):
-    """The fermion-force kernel of the differentiation workload (16^3x32,
-    N_v = 4, FP32, Wilson and staggered): time per call and the algorithmic
+    """The fermion-force kernels of the differentiation workload (16^3x32,
+    N_v = 4, FP32; Wilson, staggered and Brillouin): time per call and the algorithmic
     bytes it moves (psi and chi read once, links read once, the force
     written once)."""
     import numpy as np
@@ -570,14 +624,14 @@ def force_timing(D, I, torch, dims=(16, 16, 16, 32), nv=4):
     U = torch.from_numpy(I.gauge_field(dims, NC, EPS, 7)).cuda()
     st = torch.cuda.current_stream()
     out = {"lattice": "x".join(map(str, dims)), "nv": nv}
-    for k in (D.WILSON, D.STAGGERED):
+    for k in (D.WILSON, D.STAGGERED, D.BRILLOUIN):
         op = D.DiracOp(k, U, nv, BC, D.F32)
         psi, chi = op.new_vector(), op.new_vector()
         psi.real.normal_()
         chi.real.normal_()
         op.force(psi, chi)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = 20
+        reps = 3 if k == D.BRILLOUIN else 20
         e0.record(st)
         for _ in range(reps):
             op.force(psi, chi)
@@ -587,6 +641,8 @@ def force_timing(D, I, torch, dims=(16, 16, 16, 32), nv=4):
         spin = 1 if k == D.STAGGERED else 4
         gbytes = V * (2 * NC * spin * nv * 8 + 2 * 4 * NC * NC * 8) / 1e9
         out[D.KIND_NAMES[k]] = {"ms": t * 1e3, "alg_GBps": gbytes / t, "hbm_frac": gbytes / t / peaks()["hbm"]}
+        if k == D.BRILLOUIN:   # plus the 216 link terms per site written and read back
+            out[D.KIND_NAMES[k]]["scratch_GB"] = V * 216 * NC * NC * 8 / 1e9
         op.close()
     return out
 
@@ -748,7 +804,9 @@ def batch_measurement(D, I, torch, nsolves=64, seed=2026):
            "latency_p50_s": float(np.percentile(lat, 50)), "latency_p99_s": float(np.percentile(lat, 99)),
            "iters_total": int(sum(s["iters"] for s in stats)),
            "all_converged": all(s["status"] == 0 for s in stats),
-           "rhs_total": int(sum(d[2] for d in desc))}
+           "rhs_total": int(sum(d[2] for d in desc)), "tol": TOL_BATCH,
+           "host_graph_launches": int(stats[0]["host_launches"]),
+           "lattices": sorted({d[1] for d in desc})}
     for op in ops:
         op.close()
     return res

@@ -234,6 +234,36 @@ int dirac_apply_host(const dirac_op *op, const void *host_in, void *host_out, do
 int dirac_apply_host_async(const dirac_op *op, const void *host_in, void *host_out, double m0,
                            int dagger, void *stream);
 
+/* ------------------------------------------------- domain decomposition
+ * A lattice split into slabs of time slices, one per GPU (the paper leaves
+ * distributed memory to future work, Sec. 1; App. A notes that the spin
+ * projection halves a Wilson halo).  A slab operator is an ordinary operator
+ * whose t extent is N_t,local + 2: slices 0 and N_t,local + 1 are ghost copies
+ * of the neighbouring slabs' edge slices, links included (the caller folds the
+ * global boundary phase into its links and passes bc[3] = +1).  Each stencil
+ * reaches one slice in t, so these two ghost slices are the whole halo.
+ *
+ * dirac_apply_range: D (dagger = 0) or D^dag psi for the output sites
+ * [site0, site0 + nsites) only (site order of the layout; the owned slices of
+ * a slab operator are site0 = N_x N_y N_z, nsites = N_t,local N_x N_y N_z);
+ * other output sites are left untouched.  Asynchronous on `stream`.
+ *
+ * dirac_halo_pack / dirac_halo_unpack: copy time slice t of a vector into a
+ * contiguous buffer and back.  proj = 0: the full slice, order
+ * [site in slice][colour][spin][v]; proj = a = +-1 (Wilson-type vectors only):
+ * the half spinor h = upper two spin components of (1 + a gamma_4) psi
+ * (gamma_4 of App. A), unpacked as (1 + a gamma_4) psi / 2, whose
+ * (1 + a gamma_4) projection is exactly (1 + a gamma_4) psi: the D_W hop into
+ * a ghost slice then gives the full-spinor result with half the bytes.  D_W
+ * applies (1 - gamma_4) to the slice above and (1 + gamma_4) to the slice
+ * below (signs swapped for the dagger).  dirac_halo_bytes gives the buffer
+ * size (0 for invalid arguments).  Asynchronous on `stream`. */
+int dirac_apply_range(const dirac_op *op, const void *psi_in, void *psi_out, double m0, int dagger,
+                      long long site0, long long nsites, void *stream);
+size_t dirac_halo_bytes(const dirac_op *op, int proj);
+int dirac_halo_pack(const dirac_op *op, const void *v, int t, int proj, void *buf, void *stream);
+int dirac_halo_unpack(const dirac_op *op, const void *buf, int t, int proj, void *v, void *stream);
+
 /* ----------------------------------------------------- launch tuning
  * A stencil launch variant is (vr, minb, block): vr = right-hand sides per
  * thread (1, 2 or 4, dividing N_v); minb = register class, the cap of minb

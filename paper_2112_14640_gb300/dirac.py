@@ -103,6 +103,10 @@ SIGNATURES = {
     "dirac_clover_flops_per_site": (ctypes.c_long, [_I]),
     "dirac_version": (_I, []),
     "dirac_measure_fp32_peak": (_I, [_I, ctypes.POINTER(_D), ctypes.POINTER(_I), _P]),
+    "dirac_apply_range": (_I, [_P, _P, _P, _D, _I, ctypes.c_longlong, ctypes.c_longlong, _P]),
+    "dirac_halo_bytes": (_SZ, [_P, _I]),
+    "dirac_halo_pack": (_I, [_P, _P, _I, _I, _P, _P]),
+    "dirac_halo_unpack": (_I, [_P, _P, _I, _I, _P, _P]),
 }
 
 
@@ -366,6 +370,31 @@ class DiracOp:
         _check(lib().dirac_apply_host(self._h, _ptr(host_in), _ptr(host_out), float(m0), int(bool(dagger)),
                                       _stream(stream)), "dirac_apply_host")
         return host_out
+
+    def apply_range(self, x, out, site0, nsites, m0=0.0, dagger=False, stream=None):
+        """D (or D^dag) x for the output sites [site0, site0 + nsites) only
+        (dirac_apply_range); the rest of ``out`` is left untouched."""
+        _check(lib().dirac_apply_range(self._h, self._vec(x, "x"), self._vec(out, "out"), float(m0),
+                                       int(bool(dagger)), int(site0), int(nsites), _stream(stream)),
+               "dirac_apply_range")
+        return out
+
+    def halo_buffer(self, proj=0):
+        """A device buffer for one packed time slice (dirac_halo_bytes)."""
+        nb = int(lib().dirac_halo_bytes(self._h, int(proj)))
+        if nb == 0:
+            raise DiracError(-1, "dirac_halo_bytes")
+        return torch.empty(nb, dtype=torch.uint8, device=self.device)
+
+    def halo_pack(self, x, t, buf, proj=0, stream=None):
+        _check(lib().dirac_halo_pack(self._h, self._vec(x, "x"), int(t), int(proj), _ptr(buf), _stream(stream)),
+               "dirac_halo_pack")
+        return buf
+
+    def halo_unpack(self, buf, t, x, proj=0, stream=None):
+        _check(lib().dirac_halo_unpack(self._h, _ptr(buf), int(t), int(proj), self._vec(x, "x"), _stream(stream)),
+               "dirac_halo_unpack")
+        return x
 
     def apply_host_async(self, host_in, host_out, m0=0.0, dagger=False, stream=None):
         """apply_host without the final synchronisation (dirac_apply_host_async):
