@@ -180,7 +180,7 @@ int op_alloc(dirac_kind kind, const dirac_geom *g, dirac_op **out) {
     op->rows = op->V * op->nc * spins_of(kind);
     const size_t eb = elem_bytes(op->prec), lb = elem_bytes(link_prec(op));
     op->vec_bytes = (size_t)op->rows * op->nv * 2 * eb;
-    op->link_bytes = (size_t)op->V * 4 * op->nc * op->nc * 2 * lb;
+    op->link_bytes = (size_t)link_sites(op->V) * 4 * op->nc * op->nc * 2 * lb;   // whole 32-site blocks
     op->w_bytes = uses_w(kind) ? (size_t)op->V * 80 * op->nc * op->nc * 2 * lb : 0;
     // one reduction block per 2 SMs' worth of work, at most 1216 blocks
     long long want = (op->rows + 255) / 256;

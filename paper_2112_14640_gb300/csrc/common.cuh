@@ -212,11 +212,24 @@ __device__ __forceinline__ long long neighbour(const Lat &g, long long n, const 
 // Index arithmetic of the two vector layouts (in complex numbers).  ncs is the
 // number of internal components per site (N_c*4 or N_c), cs one of them.
 //   OUTER: ((site * ncs + cs) * nv + v)      INNER: ((cs * V + site) * nv + v)
-// Links and clover blocks, element e of matrix k (k = mu or block), for either
-// vector layout: ((site * nk + k) * NC*NC + e), one site's matrices contiguous.
-// (With site-inner vectors the links were once stored [k][e][site]: a warp's
-// link loads then touched nine arrays a whole field apart, and D_W at
-// 16^3x32, N_v = 12 took 0.105 ms against 0.097 ms site-contiguous.)
+// Links and clover blocks, element e of matrix k (k = mu or block) of site n,
+// for either vector layout: blocks of kLinkBlock consecutive sites, within a
+// block [k][e][n % kLinkBlock] (link_index).  Consecutive sites' elements are
+// adjacent, so the link loads of a warp coalesce whether its threads cover 32
+// sites (one RHS) or a few sites with many RHS each, and one block's matrices
+// stay within a few KB.  (Measured at 16^3x32, FP32: [k][e][site] over the
+// whole field, D_W 0.105 ms at N_v = 12; [site][k][e], 0.097 ms at N_v = 12
+// but 35-45% slower D_W and D_S at N_v = 1.)  Buffers are padded to a whole
+// number of blocks (link_sites).
+constexpr int kLinkBlockLog2 = 5, kLinkBlock = 1 << kLinkBlockLog2;
+__host__ __device__ __forceinline__ long long link_sites(long long V) {
+    return (V + kLinkBlock - 1) >> kLinkBlockLog2 << kLinkBlockLog2;
+}
+// site >= 0: shifts instead of signed division
+__host__ __device__ __forceinline__ long long link_index(long long site, int nk, int per, int k, int e) {
+    return (((site >> kLinkBlockLog2) * nk * per + (long long)k * per + e) << kLinkBlockLog2) +
+           (site & (kLinkBlock - 1));
+}
 template <int LAYOUT>
 struct Layout {
     static __host__ __device__ __forceinline__ long long vec(const Lat &g, long long site, int ncs, int cs) {
@@ -228,12 +241,13 @@ struct Layout {
         if constexpr (LAYOUT == 0) return g.nv;
         else return g.V * g.nv;
     }
+    // element 0 of matrix k of site `site` (nk matrices per site)
     template <int NC>
     static __host__ __device__ __forceinline__ long long mat(const Lat &, long long site, int nk, int k) {
-        return (site * nk + k) * (long long)(NC * NC);
+        return link_index(site, nk, NC * NC, k, 0);
     }
     // distance between consecutive matrix elements
-    static __host__ __device__ __forceinline__ long long mat_stride(const Lat &) { return 1; }
+    static __host__ __device__ __forceinline__ long long mat_stride(const Lat &) { return kLinkBlock; }
 };
 
 // NC x NC matrix whose elements are `stride` complex numbers apart.

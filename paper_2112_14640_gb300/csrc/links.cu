@@ -41,8 +41,8 @@ __global__ void phase_links_kernel(const UE *__restrict__ U, E *__restrict__ out
     const int per = nc * nc;
     for (int e = 0; e < per; ++e) {
         cx<double> u = ld_u(U, tid * per + e);
-        // [site][mu][a][b] for either vector layout (common.cuh, Layout::mat)
-        const long long o = tid * per + e;
+        // blocks of 32 sites, [mu][a][b][site % 32] within (common.cuh, link_index)
+        const long long o = link_index(n, 4, per, mu, e);
         out[2 * o] = from_acc<E, double>(f * u.re);
         out[2 * o + 1] = from_acc<E, double>(f * u.im);
     }
@@ -309,8 +309,8 @@ __global__ void __launch_bounds__(128) build_clover_kernel(const UE *__restrict_
 #pragma unroll
         for (int b = 0; b < NC; ++b) {
             const int el = a * NC + b;
-            // the links' layout: [site][k][a][b] for either vector layout
-            const long long o = tid * per + el;
+            // the links' layout (common.cuh, link_index)
+            const long long o = link_index(n, 4, per, k, el);
             out[2 * o] = from_acc<E, double>(f * (double)acc[a][b].re);
             out[2 * o + 1] = from_acc<E, double>(f * (double)acc[a][b].im);
         }
@@ -353,7 +353,7 @@ static int convert_array(const void *src, dirac_prec sp, void *dst, dirac_prec d
 }
 
 int launch_convert_links(const dirac_op *src, dirac_op *dst, cudaStream_t s) {
-    long long n = src->V * 4 * src->nc * src->nc * 2;
+    long long n = link_sites(src->V) * 4 * src->nc * src->nc * 2;
     int rc = convert_array(src->links, link_prec(src), dst->links, link_prec(dst), n, s);
     if (rc) return rc;
     if (src->w) {
@@ -362,7 +362,7 @@ int launch_convert_links(const dirac_op *src, dirac_op *dst, cudaStream_t s) {
         rc = convert_array(src->w, link_prec(src), dst->w, link_prec(dst), n, s);
     }
     if (!rc && src->clover) {
-        n = src->V * 4 * src->nc * src->nc * 2;
+        n = link_sites(src->V) * 4 * src->nc * src->nc * 2;
         rc = convert_array(src->clover, link_prec(src), dst->clover, link_prec(dst), n, s);
     }
     return rc;
