@@ -431,10 +431,12 @@ def main():
         for k in kinds:
             ops[k].apply_host(hin[k], hout[k], m0=MASS[k])
         # one step = the three host applies enqueued back to back (each
-        # operator's copies overlap the others' stencils), one wait per step
+        # operator's copies overlap the others' stencils), one wait per step;
+        # the longest stencil first, so that its copies go out last
+        order = sorted(kinds, key=lambda k: -per_op[D.KIND_NAMES[k]]["ms"])
         t0 = time.perf_counter()
         for _ in range(Ke):
-            for k in kinds:
+            for k in order:
                 ops[k].apply_host_async(hin[k], hout[k], m0=MASS[k])
             torch.cuda.current_stream().synchronize()
         dt = (time.perf_counter() - t0) / Ke
@@ -690,6 +692,11 @@ def solve_default(D, I, torch, budget_s):
                 r["max_true_relres"].append(max(st["true_relres"]))
                 r["max_normal_relres"] = max(st["relres"])
                 r["cond_lanczos"] = max(st["lambda_max"]) / max(min(st["lambda_min"]), 1e-300)
+                r["ms_per_iter"] = 1e3 * st["seconds"] / max(st["iters"], 1)
+                if inner != D.F32:
+                    # the 16-bit phase: how far it carried the solve and what its iterations cost
+                    r["iters_16bit"] = st["iters_16bit"]
+                    r["ms_per_iter_16bit"] = 1e3 * st["seconds_16bit"] / max(st["iters_16bit"], 1)
                 del x
         for mname, *_ in modes:
             if mname in row:

@@ -107,7 +107,8 @@ enum { DIRAC_LINKS_NATIVE = 0, DIRAC_LINKS_F32 = 1 };
  *               threads of a warp, which cover consecutive sites, read one
  *               contiguous run per (colour, spin) component.
  * The gauge field handed to dirac_op_create is always [site][mu][a][b]; the
- * operator stores its own copy in the order that matches the layout. */
+ * operator stores its own phased copy in blocks of 32 sites, the same for
+ * both layouts (internal, never exposed). */
 enum { DIRAC_LAYOUT_SITE_OUTER = 0, DIRAC_LAYOUT_SITE_INNER = 1 };
 
 typedef struct dirac_op dirac_op;   /* opaque */
@@ -225,12 +226,12 @@ int dirac_apply_host(const dirac_op *op, const void *host_in, void *host_out, do
 /* dirac_apply_host without the final synchronisation, so that the host
  * applies of several operators overlap (one operator's stencil runs while
  * another's slabs are copied).  Returns once everything is enqueued; host_out
- * is complete when `stream` reaches the point after the call.  host_in must
- * be ready when the call is made: the copies in wait only for this
+ * is complete when `stream` reaches the point after the call.  The copies
+ * and the stencils run on operator-owned streams and wait only for this
  * operator's previous host apply (its staging buffers), not for earlier work
- * on `stream`.  Both host buffers must stay valid (and host_in unchanged)
- * until then; calls on one operator are ordered, calls on different
- * operators may share `stream`. */
+ * on `stream`, so host_in must be ready when the call is made.  Both host
+ * buffers must stay valid (and host_in unchanged) until then; calls on one
+ * operator are ordered, calls on different operators may share `stream`. */
 int dirac_apply_host_async(const dirac_op *op, const void *host_in, void *host_out, double m0,
                            int dagger, void *stream);
 
@@ -383,6 +384,9 @@ typedef struct {
     double lambda_max[64];     /* of D^dag D from the CG coefficients (App. F "cond"); 0 otherwise */
     int host_launches;         /* dirac_solve_batched: graph launches issued by the host (1 when the
                                   whole convergence loop ran as one graph with a device-side loop) */
+    int iters_16bit;           /* RELIABLE / ADAPTIVE CG with a 16-bit inner_prec: iterations run
+                                  with 16-bit sloppy vectors (ADAPTIVE: before the FP32 hand-over) */
+    double seconds_16bit;      /* wall time of those iterations, refreshes included */
 } dirac_solve_stats;
 
 /* Solve for N_v right-hand sides b (operator precision); x holds the initial

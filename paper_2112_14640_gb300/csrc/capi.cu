@@ -13,10 +13,14 @@
 #include "internal.h"
 
 // Streams and events of the pipelined host apply (dirac_apply_host), which
-// works in at most kMaxSlabs slabs of time slices.
+// works in at most kMaxSlabs slabs of time slices.  Each operator has its own
+// copy streams: the host applies of several operators enqueued back to back
+// then copy concurrently, which measured faster than one copy-in stream shared
+// by all of them in call order (16^3x32, N_v = 12, D_B + D_W + D_S: 2.74 vs
+// 2.99 ms per step).
 constexpr int kMaxSlabs = 8;
 struct dirac_host_pipe {
-    cudaStream_t h2d = nullptr, d2h = nullptr;
+    cudaStream_t h2d = nullptr, d2h = nullptr, comp = nullptr;   // comp: stencils of the asynchronous form
     cudaEvent_t in_done[kMaxSlabs] = {}, out_ready[kMaxSlabs] = {}, start = nullptr, end = nullptr;
     bool used = false;   // `end` has been recorded by an earlier call
 };
@@ -65,6 +69,7 @@ static void pipe_free(dirac_host_pipe *p) {
     if (p->end) cudaEventDestroy(p->end);
     if (p->h2d) cudaStreamDestroy(p->h2d);
     if (p->d2h) cudaStreamDestroy(p->d2h);
+    if (p->comp) cudaStreamDestroy(p->comp);
     delete p;
 }
 
@@ -73,6 +78,7 @@ static int pipe_get(dirac_op *op, dirac_host_pipe **out) {
         dirac_host_pipe *p = new dirac_host_pipe();
         int rc = cuda_check(cudaStreamCreateWithFlags(&p->h2d, cudaStreamNonBlocking), "pipe stream");
         if (!rc) rc = cuda_check(cudaStreamCreateWithFlags(&p->d2h, cudaStreamNonBlocking), "pipe stream");
+        if (!rc) rc = cuda_check(cudaStreamCreateWithFlags(&p->comp, cudaStreamNonBlocking), "pipe stream");
         for (int k = 0; k < kMaxSlabs && !rc; ++k) {
             rc = cuda_check(cudaEventCreateWithFlags(&p->in_done[k], cudaEventDisableTiming), "pipe event");
             if (!rc) rc = cuda_check(cudaEventCreateWithFlags(&p->out_ready[k], cudaEventDisableTiming), "pipe event");
@@ -542,9 +548,13 @@ static int host_apply(const dirac_op *op, const void *host_in, void *host_out, d
     // k+1 (every stencil reaches one slice in t), so the stencil runs on slabs
     // 1, 2, .., K-1 as their upper neighbours arrive and on slab 0 last; each
     // finished output slab goes out on the copy-out stream while later slabs
-    // are still being copied in or computed.
+    // are still being copied in or computed.  The synchronous form runs the
+    // stencils on `stream`; the asynchronous one on the operator's own compute
+    // stream, so that its stencils do not queue behind the copies out of
+    // another operator's host apply that `stream` waits for.
     dirac_host_pipe *p = nullptr;
     CTRY(pipe_get(self, &p));
+    cudaStream_t cs = sync ? s : p->comp;
     auto t_of = [&](int k) { return (int)((long long)k * nt / K); };
     if (sync) {
         CTRY(cuda_check(cudaEventRecord(p->start, s), "pipe event"));      // staging buffers free
@@ -565,12 +575,12 @@ static int host_apply(const dirac_op *op, const void *host_in, void *host_out, d
     for (int i = 0; i < K; ++i) {
         const int k = (i + 1) % K;
         const int need = (k >= 1 && k <= K - 2) ? k + 1 : K - 1;   // last input slab it reads
-        CTRY(cuda_check(cudaStreamWaitEvent(s, p->in_done[need], 0), "pipe wait"));
+        CTRY(cuda_check(cudaStreamWaitEvent(cs, p->in_done[need], 0), "pipe wait"));
         dirac_op part = *op;   // same buffers, output sites of slab k only
         part.lat.n0 = t_of(k) * slab_sites;
         part.lat.nsites = (t_of(k + 1) - t_of(k)) * slab_sites;
-        CTRY(op_apply(&part, self->stage_in, self->stage_out, m0, sgn, s));
-        CTRY(cuda_check(cudaEventRecord(p->out_ready[k], s), "pipe event"));
+        CTRY(op_apply(&part, self->stage_in, self->stage_out, m0, sgn, cs));
+        CTRY(cuda_check(cudaEventRecord(p->out_ready[k], cs), "pipe event"));
         CTRY(cuda_check(cudaStreamWaitEvent(p->d2h, p->out_ready[k], 0), "pipe wait"));
         CTRY(copy_slab(op, host_out, self->stage_out, t_of(k), t_of(k + 1), cudaMemcpyDeviceToHost, p->d2h));
     }

@@ -770,8 +770,13 @@ static int reliable_solve(const dirac_op *op, const void *b, void *x, double m0,
     // adaptive: the 16-bit iteration runs while reliable updates keep halving
     // the true residual (2 misses in a row end it), then an FP32 iteration
     // continues from the current solution
+    const auto t16 = std::chrono::steady_clock::now();
     TRY(cg_reliable(op, lo, rhs, x, m0, prm->tol, prm->maxit, delta, co, &lan, s, adaptive ? 2 : 30));
     int iters = co.iters, updates = co.recomputes;
+    if (half) {   // cg_reliable reads the residual norms on the host every iteration: the wall time is the GPU's
+        st->iters_16bit = co.iters;
+        st->seconds_16bit = std::chrono::duration<double>(std::chrono::steady_clock::now() - t16).count();
+    }
     if (adaptive && co.status == DIRAC_STAGNATED && co.iters < prm->maxit) {
         dirac_op *lo32 = nullptr;
         TRY(op_inner(op, DIRAC_F32, DIRAC_LINKS_NATIVE, &lo32, s));

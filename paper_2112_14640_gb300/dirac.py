@@ -57,7 +57,7 @@ class SolveStats(ctypes.Structure):
                 ("status", ctypes.c_int), ("status_per_rhs", ctypes.c_int * 64), ("relres", ctypes.c_double * 64),
                 ("true_relres", ctypes.c_double * 64), ("seconds", ctypes.c_double),
                 ("lambda_min", ctypes.c_double * 64), ("lambda_max", ctypes.c_double * 64),
-                ("host_launches", ctypes.c_int)]
+                ("host_launches", ctypes.c_int), ("iters_16bit", ctypes.c_int), ("seconds_16bit", ctypes.c_double)]
 
 
 class DiracError(RuntimeError):
@@ -476,7 +476,8 @@ class DiracOp:
         stats = dict(code=rc, status=st.status, iters=st.iters, outer_iters=st.outer_iters,
                      recomputes=st.recomputes, status_per_rhs=list(st.status_per_rhs[:nv]),
                      relres=list(st.relres[:nv]), true_relres=list(st.true_relres[:nv]), seconds=st.seconds,
-                     lambda_min=list(st.lambda_min[:nv]), lambda_max=list(st.lambda_max[:nv]))
+                     lambda_min=list(st.lambda_min[:nv]), lambda_max=list(st.lambda_max[:nv]),
+                     iters_16bit=st.iters_16bit, seconds_16bit=st.seconds_16bit)
         return x, stats
 
 

@@ -195,6 +195,18 @@ def test_async_host_applies_overlap_and_match(dims):
     torch.cuda.current_stream().synchronize()
     for op, ho, dv in zip(ops, houts, devs):
         assert torch.equal(ho, dv)
+    # the synchronous and the asynchronous form in turn on one operator (their
+    # stencils run on different streams): each sees the other's staging buffers free
+    op, hi = ops[0], hins[0]
+    h2 = (2 * hi).pin_memory()
+    want2 = op.apply(h2.cuda(), m0=0.1).cpu()
+    o1, o2, o3 = (torch.zeros_like(hi).pin_memory() for _ in range(3))
+    op.apply_host_async(h2, o1, m0=0.1)
+    op.apply_host(hi, o2, m0=0.1)
+    op.apply_host_async(h2, o3, m0=0.1)
+    torch.cuda.current_stream().synchronize()
+    assert torch.equal(o1, want2) and torch.equal(o2, devs[0]) and torch.equal(o3, want2)
+    for op in ops:
         op.close()
 
 

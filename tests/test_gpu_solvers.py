@@ -76,6 +76,7 @@ def test_mixed_precision_cg_reaches_1e10(kind, inner):
     x, st = op.solve(to_device(op, b), m0=m0, tol=1e-10, maxit=20000, inner_prec=inner)
     assert st["status"] == 0, st
     assert st["outer_iters"] >= 2
+    assert st["iters_16bit"] == (0 if inner == D.F32 else st["iters"]), st
     assert np.all(normal_relres(ref, to_numpy(op, x), b, m0) < 1.01e-10)
 
 
@@ -204,11 +205,14 @@ def test_adaptive_mode_finishes_a_stalling_fp16_solve():
     assert st["status"] == 0, st
     assert st["iters"] < 10000, st
     assert np.all(normal_relres(ref, to_numpy(op, x), b, m0) < 1.01e-10)
+    # the FP16 phase is counted separately: it ran, and the FP32 one finished
+    assert 0 < st["iters_16bit"] < st["iters"] and 0 < st["seconds_16bit"] < st["seconds"], st
     # FP32 inner: adaptive is the plain reliable mode
     x2, st2 = op.solve(to_device(op, b), m0=m0, tol=1e-10, maxit=20000, inner_prec=D.F32,
                        mixed_mode=D.MIXED_ADAPTIVE)
     x3, st3 = op.solve(to_device(op, b), m0=m0, tol=1e-10, maxit=20000, inner_prec=D.F32)
     assert st2["iters"] == st3["iters"] and torch.equal(x2, x3)
+    assert st2["iters_16bit"] == 0 and st3["seconds_16bit"] == 0.0
 
 
 @pytest.mark.parametrize("nc", [6, 8])
