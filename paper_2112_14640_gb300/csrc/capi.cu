@@ -422,7 +422,7 @@ int dirac_op_autotune(dirac_op *op, double m0, void *stream, double *best_ms) {
         float ms;
     };
     std::vector<Cand> cands;
-    const int vrs[3] = {1, 2, 4}, minbs[4] = {1, 3, 4, 6}, blocks[5] = {128, 256, 384, 512, 768};
+    const int vrs[3] = {1, 2, 4}, minbs[5] = {1, 3, 4, 5, 6}, blocks[5] = {128, 256, 384, 512, 768};
     for (int vr : vrs)
         for (int mb : minbs)
             for (int bl : blocks)

@@ -149,7 +149,7 @@ inline bool variant_compiled(int nc, int vr, int minb) {
     if (vr != 1 && vr != 2 && vr != 4) return false;
     if (nc > kMaxNcSmall) return vr == 1 && minb == 1;
     if (minb == 1) return true;
-    return nc == 3 && (minb == 3 || minb == 4 || minb == 6);
+    return nc == 3 && (minb >= 3 && minb <= 6);
 }
 
 template <typename F>
@@ -170,6 +170,7 @@ int dispatch_minb(int minb, F &&f) {
         case 1: return f(std::integral_constant<int, 1>{});
         case 3: return f(std::integral_constant<int, 3>{});
         case 4: return f(std::integral_constant<int, 4>{});
+        case 5: return f(std::integral_constant<int, 5>{});
         case 6: return f(std::integral_constant<int, 6>{});
         }
         return DIRAC_ERR_INVALID_ARG;

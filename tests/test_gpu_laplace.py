@@ -73,7 +73,7 @@ def test_laplace_every_launch_variant(kind):
         want = ref.apply(src, 0.2)
         tried = 0
         for vr in (1, 2, 4):
-            for minb in (1, 3, 4, 6):
+            for minb in (1, 3, 4, 5, 6):
                 try:
                     op.set_launch(vr, minb, 128)
                 except D.DiracError:

@@ -275,7 +275,7 @@ def test_every_launch_variant_matches_the_oracle(kind):
         want = ref.apply(src, m0)
         tried = 0
         for vr in (1, 2, 4):
-            for minb in (1, 3, 4, 6):
+            for minb in (1, 3, 4, 5, 6):
                 for block in (64, 128, 384):
                     try:
                         op.set_launch(vr, minb, block)
