@@ -49,10 +49,25 @@ __host__ __device__ constexpr OffsetTable make_offset_table() {
 
 static __constant__ bril::OffsetTable kLapOffsets = bril::make_offset_table();
 
-// acc[c][s] += L psi(m) (or L^dag psi(m)) for every spin component s
+// Whether a hop multiplies its weight into the N_c x N_c matrix once (N_c^2
+// complex scalings) instead of into each of the NS VR N_c products (one real
+// multiply-add per complex component): worth it when NS VR > N_c.
+template <int NC, int NS, int VR>
+constexpr bool fold_weight() { return NS * VR > NC; }
+
+// acc[c][s] += f L psi(m) (or f L^dag psi(m)) for every spin component s
 template <int NC, int NS, int VR, bool DAG, typename E, typename A>
-__device__ __forceinline__ void lap_hop(cx<A> (&acc)[NC][NS][VR], const cx<A> (&L)[NC][NC],
+__device__ __forceinline__ void lap_hop(cx<A> (&acc)[NC][NS][VR], const cx<A> (&Lin)[NC][NC],
                                         const E *__restrict__ psi, long long cs_stride, A f) {
+    constexpr bool FOLD = fold_weight<NC, NS, VR>();
+    cx<A> Lf[NC][NC];
+    if constexpr (FOLD) {
+#pragma unroll
+        for (int a = 0; a < NC; ++a)
+#pragma unroll
+            for (int b = 0; b < NC; ++b) Lf[a][b] = cx<A>{f * Lin[a][b].re, f * Lin[a][b].im};
+    }
+    const cx<A>(*L)[NC] = FOLD ? (const cx<A>(*)[NC])Lf : Lin;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
         cx<A> p[NC][VR];
@@ -62,13 +77,21 @@ __device__ __forceinline__ void lap_hop(cx<A> (&acc)[NC][NS][VR], const cx<A> (&
         for (int c = 0; c < NC; ++c)
 #pragma unroll
             for (int v = 0; v < VR; ++v) {
-                cx<A> t = {0, 0};
+                if constexpr (FOLD) {
 #pragma unroll
-                for (int k = 0; k < NC; ++k) {
-                    if constexpr (DAG) cmac_conj(t, L[k][c], p[k][v]);
-                    else cmac(t, L[c][k], p[k][v]);
+                    for (int k = 0; k < NC; ++k) {
+                        if constexpr (DAG) cmac_conj(acc[c][s][v], L[k][c], p[k][v]);
+                        else cmac(acc[c][s][v], L[c][k], p[k][v]);
+                    }
+                } else {
+                    cx<A> t = {0, 0};
+#pragma unroll
+                    for (int k = 0; k < NC; ++k) {
+                        if constexpr (DAG) cmac_conj(t, L[k][c], p[k][v]);
+                        else cmac(t, L[c][k], p[k][v]);
+                    }
+                    rmac(acc[c][s][v], f, t);
                 }
-                rmac(acc[c][s][v], f, t);
             }
     }
 }
@@ -147,15 +170,16 @@ __global__ void __launch_bounds__(stencil_max_threads(MINB), (MINB > 1 ? 1 : 0))
     const Coord c = site_coords(g, n);
     const long long cs = L::cs_stride(g);
     // site-index steps of +1 / -1 along each axis, with the periodic wrap
-    long long dp[4], dm[4];
+    // (32-bit: volumes are below 2^31 sites)
+    int dp[4], dm[4];
     {
         const int co[4] = {c.x, c.y, c.z, c.t};
         const int ext[4] = {g.nx, g.ny, g.nz, g.nt};
-        long long stride = 1;
+        int stride = 1;
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu) {
-            dp[mu] = (co[mu] == ext[mu] - 1 ? -(long long)(ext[mu] - 1) : 1LL) * stride;
-            dm[mu] = (co[mu] == 0 ? (long long)(ext[mu] - 1) : -1LL) * stride;
+            dp[mu] = (co[mu] == ext[mu] - 1 ? -(ext[mu] - 1) : 1) * stride;
+            dm[mu] = (co[mu] == 0 ? ext[mu] - 1 : -1) * stride;
             stride *= ext[mu];
         }
     }
@@ -168,17 +192,37 @@ __global__ void __launch_bounds__(stencil_max_threads(MINB), (MINB > 1 ? 1 : 0))
             for (int v = 0; v < VR; ++v) acc[a][s][v] = cx<A>{0, 0};
     // W~ of one site contiguous in visiting order (either vector layout)
     const E *wp = W + 2LL * n * 80 * NC * NC;
-    for (int q = 0; q < 80; ++q) {
-        long long m = n;
+    const E *inj = in + 2LL * j * VR;
+    auto hop = [&](int q, const cx<A>(&Wm)[NC][NC]) {
+        int m = (int)n;
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu) {
             const int sm = kLapOffsets.s[q][mu];
             m += sm > 0 ? dp[mu] : (sm < 0 ? dm[mu] : 0);
         }
-        cx<A> Wm[NC][NC];
-        load_mat<NC, E, A>(wp + 2 * q * NC * NC, Wm);
-        lap_hop<NC, NS, VR, false>(acc, Wm, in + 2 * (L::vec(g, m, NC * NS, 0) + (long long)j * VR), cs,
+        lap_hop<NC, NS, VR, false>(acc, Wm, inj + 2 * L::vec(g, (long long)m, NC * NS, 0), cs,
                                    (A)kLapOffsets.lap[q]);
+    };
+    if constexpr (NC <= kMaxNcSmall) {
+        // two offsets per trip: the W~ of the next offset is loaded while the
+        // current one is applied, the two buffers swapping roles (80 is even)
+        cx<A> Wa[NC][NC], Wb[NC][NC];
+        load_mat<NC, E, A>(wp, Wa);
+#pragma unroll 1
+        for (int q = 0; q < 80; q += 2) {
+            load_mat<NC, E, A>(wp + 2 * (q + 1) * NC * NC, Wb);
+            hop(q, Wa);
+            if (q + 2 < 80) load_mat<NC, E, A>(wp + 2 * (q + 2) * NC * NC, Wa);
+            hop(q + 1, Wb);
+        }
+    } else {
+        // large N_c: one N_c x N_c buffer (the register file holds no second one)
+#pragma unroll 1
+        for (int q = 0; q < 80; ++q) {
+            cx<A> Wm[NC][NC];
+            load_mat<NC, E, A>(wp + 2 * q * NC * NC, Wm);
+            hop(q, Wm);
+        }
     }
     lap_write<NC, NS, VR, LAYOUT, E, A>(in, out, g, n, j, centre, acc);
 }
