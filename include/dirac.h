@@ -268,7 +268,7 @@ int dirac_halo_unpack(const dirac_op *op, const void *buf, int t, int proj, void
 /* ----------------------------------------------------- launch tuning
  * A stencil launch variant is (vr, minb, block): vr = right-hand sides per
  * thread (1, 2 or 4, dividing N_v); minb = register class, the cap of minb
- * resident 128-thread blocks per SM (1 = the compiler's choice; 3, 4, 6
+ * resident 128-thread blocks per SM (1 = the compiler's choice; 3, 4, 5, 6
  * compiled for N_c = 3 only); block = threads per block, a multiple of 32 up
  * to 128 minb (0 = 128).  vr = 0 restores the default choice.  Errors:
  * DIRAC_ERR_INVALID_ARG for a variant that is not compiled, a vr that does

@@ -393,7 +393,7 @@ int dirac_op_set_launch(dirac_op *op, int vr, int minb, int block) {
         op->vr = op->minb = op->block = 0;
         return DIRAC_OK;
     }
-    if (!variant_compiled(op->nc, vr, minb) || op->nv % vr) return DIRAC_ERR_INVALID_ARG;
+    if (!variant_ok(op, vr, minb)) return DIRAC_ERR_INVALID_ARG;
     if (block == 0) block = kStencilBlock;
     if (block < 32 || block % 32 || block > stencil_max_threads(minb)) return DIRAC_ERR_INVALID_ARG;
     op->vr = vr;
@@ -426,7 +426,7 @@ int dirac_op_autotune(dirac_op *op, double m0, void *stream, double *best_ms) {
     for (int vr : vrs)
         for (int mb : minbs)
             for (int bl : blocks)
-                if (variant_compiled(op->nc, vr, mb) && op->nv % vr == 0 && bl <= stencil_max_threads(mb))
+                if (variant_ok(op, vr, mb) && bl <= stencil_max_threads(mb))
                     cands.push_back(Cand{vr, mb, bl, 1e30f});
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);

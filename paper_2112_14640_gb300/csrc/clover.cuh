@@ -43,7 +43,7 @@ __device__ __forceinline__ void write_site(const E *__restrict__ in, E *__restri
             }
         return;
     }
-    const long long ms = L::mat_stride(g);
+    const long long ms = L::template mat_stride<NC>(g);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         // the output of spins 2h, 2h+1 is built in place in acc

@@ -213,8 +213,8 @@ __device__ __forceinline__ long long neighbour(const Lat &g, long long n, const 
 // number of internal components per site (N_c*4 or N_c), cs one of them.
 //   OUTER: ((site * ncs + cs) * nv + v)      INNER: ((cs * V + site) * nv + v)
 // Links and clover blocks, element e of matrix k (k = mu or block) of site n,
-// for either vector layout: blocks of kLinkBlock consecutive sites, within a
-// block [k][e][n % kLinkBlock] (link_index).  Consecutive sites' elements are
+// for either vector layout and N_c <= 4: blocks of kLinkBlock consecutive
+// sites, within a block [k][e][n % kLinkBlock] (link_index).  Consecutive sites' elements are
 // adjacent, so the link loads of a warp coalesce whether its threads cover 32
 // sites (one RHS) or a few sites with many RHS each, and one block's matrices
 // stay within a few KB.  (Measured at 16^3x32, FP32: [k][e][site] over the
@@ -225,8 +225,15 @@ constexpr int kLinkBlockLog2 = 5, kLinkBlock = 1 << kLinkBlockLog2;
 __host__ __device__ __forceinline__ long long link_sites(long long V) {
     return (V + kLinkBlock - 1) >> kLinkBlockLog2 << kLinkBlockLog2;
 }
+// Above N_c = 4 (per = N_c^2 > 16) the stencils read a link one row at a
+// time, one RHS per thread: there a site's matrices stay contiguous
+// ([site][k][a][b], element stride 1), so that a row is one run of N_c
+// complex numbers (32-site blocks measured 15-35% slower for D_W and D_S at
+// N_c = 6, 8).
+__host__ __device__ constexpr int link_stride(int per) { return per > 16 ? 1 : kLinkBlock; }
 // site >= 0: shifts instead of signed division
 __host__ __device__ __forceinline__ long long link_index(long long site, int nk, int per, int k, int e) {
+    if (per > 16) return (site * nk + k) * per + e;
     return (((site >> kLinkBlockLog2) * nk * per + (long long)k * per + e) << kLinkBlockLog2) +
            (site & (kLinkBlock - 1));
 }
@@ -247,7 +254,8 @@ struct Layout {
         return link_index(site, nk, NC * NC, k, 0);
     }
     // distance between consecutive matrix elements
-    static __host__ __device__ __forceinline__ long long mat_stride(const Lat &) { return kLinkBlock; }
+    template <int NC>
+    static __host__ __device__ __forceinline__ long long mat_stride(const Lat &) { return link_stride(NC * NC); }
 };
 
 // NC x NC matrix whose elements are `stride` complex numbers apart.

@@ -75,7 +75,7 @@ __device__ __forceinline__ void force_out(const E *__restrict__ U, E *__restrict
     }
     // M = U B - C U^dag, U = phased link
     cx<A> Lk[NC][NC], M[NC][NC];
-    load_mat_s<NC, E, A>(U + 2 * L::template mat<NC>(g, n, 4, mu), L::mat_stride(g), Lk);
+    load_mat_s<NC, E, A>(U + 2 * L::template mat<NC>(g, n, 4, mu), L::template mat_stride<NC>(g), Lk);
     for (int a = 0; a < NC; ++a)
         for (int b = 0; b < NC; ++b) {
             cx<A> acc = {0, 0};

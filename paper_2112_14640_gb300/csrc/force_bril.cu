@@ -63,7 +63,7 @@ __device__ __forceinline__ void hop_link(const E *__restrict__ U, const Lat &g, 
     if (sign < 0) y[mu] = (y[mu] == 0) ? ext[mu] - 1 : y[mu] - 1;
     const long long site = (((long long)y[3] * g.nz + y[2]) * g.ny + y[1]) * g.nx + y[0];
     const E *p = U + 2 * Layout<0>::template mat<NC>(g, site, 4, mu);
-    const long long ls = Layout<0>::mat_stride(g);
+    const long long ls = Layout<0>::template mat_stride<NC>(g);
 #pragma unroll
     for (int a = 0; a < NC; ++a)
 #pragma unroll
@@ -279,7 +279,7 @@ __global__ void bril_force_link_kernel(const E *__restrict__ U, const E *__restr
     }
     // F = P_TA(U K), U the phased link
     cx<A> Lk[NC][NC], M[NC][NC];
-    load_mat_s<NC, E, A>(U + 2 * Layout<0>::template mat<NC>(g, m, 4, mu), Layout<0>::mat_stride(g), Lk);
+    load_mat_s<NC, E, A>(U + 2 * Layout<0>::template mat<NC>(g, m, 4, mu), Layout<0>::template mat_stride<NC>(g), Lk);
     for (int a = 0; a < NC; ++a)
         for (int b = 0; b < NC; ++b) {
             cx<A> acc = {0, 0};

@@ -151,6 +151,9 @@ inline bool variant_compiled(int nc, int vr, int minb) {
     if (minb == 1) return true;
     return nc == 3 && (minb >= 3 && minb <= 6);
 }
+inline bool variant_ok(const dirac_op *op, int vr, int minb) {
+    return variant_compiled(op->nc, vr, minb) && op->nv % vr == 0;
+}
 
 template <typename F>
 int dispatch_layout(int layout, F &&f) {

@@ -70,20 +70,29 @@ __device__ __forceinline__ void lap_hop(cx<A> (&acc)[NC][NS][VR], const cx<A> (&
     const cx<A>(*L)[NC] = FOLD ? (const cx<A>(*)[NC])Lf : Lin;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
-        cx<A> p[NC][VR];
+        if constexpr (FOLD) {
+            // one colour component of the neighbour at a time (VR complex
+            // numbers in registers, not N_c VR)
 #pragma unroll
-        for (int k = 0; k < NC; ++k) load_cx<E, VR, A>(psi + 2 * (k * NS + s) * cs_stride, p[k]);
+            for (int k = 0; k < NC; ++k) {
+                cx<A> pk[VR];
+                load_cx<E, VR, A>(psi + 2 * (k * NS + s) * cs_stride, pk);
 #pragma unroll
-        for (int c = 0; c < NC; ++c)
+                for (int c = 0; c < NC; ++c)
 #pragma unroll
-            for (int v = 0; v < VR; ++v) {
-                if constexpr (FOLD) {
-#pragma unroll
-                    for (int k = 0; k < NC; ++k) {
-                        if constexpr (DAG) cmac_conj(acc[c][s][v], L[k][c], p[k][v]);
-                        else cmac(acc[c][s][v], L[c][k], p[k][v]);
+                    for (int v = 0; v < VR; ++v) {
+                        if constexpr (DAG) cmac_conj(acc[c][s][v], L[k][c], pk[v]);
+                        else cmac(acc[c][s][v], L[c][k], pk[v]);
                     }
-                } else {
+            }
+        } else {
+            cx<A> p[NC][VR];
+#pragma unroll
+            for (int k = 0; k < NC; ++k) load_cx<E, VR, A>(psi + 2 * (k * NS + s) * cs_stride, p[k]);
+#pragma unroll
+            for (int c = 0; c < NC; ++c)
+#pragma unroll
+                for (int v = 0; v < VR; ++v) {
                     cx<A> t = {0, 0};
 #pragma unroll
                     for (int k = 0; k < NC; ++k) {
@@ -92,7 +101,7 @@ __device__ __forceinline__ void lap_hop(cx<A> (&acc)[NC][NS][VR], const cx<A> (&
                     }
                     rmac(acc[c][s][v], f, t);
                 }
-            }
+        }
     }
 }
 
@@ -130,7 +139,7 @@ __global__ void __launch_bounds__(stencil_max_threads(MINB), (MINB > 1 ? 1 : 0))
     split_tid(tid, nchunk, i, j);
     const long long n = g.n0 + i;
     const Coord c = site_coords(g, n);
-    const long long cs = L::cs_stride(g), ls = L::mat_stride(g);
+    const long long cs = L::cs_stride(g), ls = L::template mat_stride<NC>(g);
 
     cx<A> acc[NC][NS][VR];
 #pragma unroll

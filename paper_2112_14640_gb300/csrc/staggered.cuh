@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(stencil_max_threads(MINB), (MINB > 1 ? 1 : 0))
     const long long n = g.n0 + i;
     const Coord c = site_coords(g, n);
     using L = Layout<LAYOUT>;
-    const long long cs = L::cs_stride(g), ls = L::mat_stride(g);
+    const long long cs = L::cs_stride(g), ls = L::template mat_stride<NC>(g);
 
     cx<A> acc[NC][VR];
 #pragma unroll

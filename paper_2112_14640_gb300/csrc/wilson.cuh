@@ -149,7 +149,7 @@ __device__ __forceinline__ void wilson_dir(cx<A> (&acc)[NC][4][VR], const EL *__
     using L = Layout<LAYOUT>;
     const long long fw = neighbour(g, n, c, MU, +1);
     const long long bw = neighbour(g, n, c, MU, -1);
-    const long long cs = L::cs_stride(g), ls = L::mat_stride(g);
+    const long long cs = L::cs_stride(g), ls = L::template mat_stride<NC>(g);
     if constexpr (NC <= kMaxNcSmall) {
         // both links of the direction are requested before either hop, so
         // their loads are in flight together
