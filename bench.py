@@ -434,15 +434,19 @@ def main():
         # operator's copies overlap the others' stencils), one wait per step;
         # the longest stencil first, so that its copies go out last
         order = sorted(kinds, key=lambda k: -per_op[D.KIND_NAMES[k]]["ms"])
+        enq = 0.0
         t0 = time.perf_counter()
         for _ in range(Ke):
+            te = time.perf_counter()
             for k in order:
                 ops[k].apply_host_async(hin[k], hout[k], m0=MASS[k])
+            enq += time.perf_counter() - te
             torch.cuda.current_stream().synchronize()
         dt = (time.perf_counter() - t0) / Ke
         nbytes = sum(ops[k].vec_bytes() for k in kinds)
         line["e2e"] = {"value": step_flop / dt / 1e9, "unit": "Gflop/s", "h2d_bytes_per_step": nbytes,
                        "d2h_bytes_per_step": nbytes, "ms_per_step": dt * 1e3,
+                       "host_enqueue_ms_per_step": enq / Ke * 1e3,
                        "pinned_copy": pinned_copy_rate(torch, ops[kinds[0]].vec_bytes())}
 
     if not args.ncu and not args.no_sweep:

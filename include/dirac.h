@@ -298,6 +298,17 @@ int dirac_vec_norm2(const dirac_op *op, const void *v, double *out_dev, void *st
 int dirac_vec_dot(const dirac_op *op, const void *u, const void *v, double *out_dev, void *stream);
 /* y += alpha x per RHS (Eq. def_incr with complex alpha); alpha_dev: N_v (re, im) pairs. */
 int dirac_vec_axpy(const dirac_op *op, const double *alpha_dev, const void *x, void *y, void *stream);
+/* z = a x + b y per RHS; a_dev, b_dev: N_v (re, im) pairs; z may alias x or y. */
+int dirac_vec_axpby(const dirac_op *op, const double *a_dev, const void *x, const double *b_dev, const void *y,
+                    void *z, void *stream);
+/* dirac_vec_norm2 / dirac_vec_dot over the sites [site0, site0 + nsites)
+ * only (site order of the layout; 1 <= nsites, site0 + nsites <= volume,
+ * else DIRAC_ERR_INVALID_ARG): the owned sites of a slab operator, whose
+ * ghost slices must not enter the dot products of a distributed solver. */
+int dirac_vec_norm2_range(const dirac_op *op, const void *v, long long site0, long long nsites, double *out_dev,
+                          void *stream);
+int dirac_vec_dot_range(const dirac_op *op, const void *u, const void *v, long long site0, long long nsites,
+                        double *out_dev, void *stream);
 /* v = gamma5 v (4 spin components) or epsilon v (colour-only vectors), in place. */
 int dirac_vec_gamma5(const dirac_op *op, void *v, void *stream);
 /* Convert a vector between precisions (same shape): src in src_prec, dst in dst_prec. */

@@ -126,8 +126,19 @@ struct RedAcc<float> {
     const bool live = r < R;                                \
     const long long stride = (long long)gridDim.x * R;
 
+// Rows of a reduction over part of a vector: `rows` logical rows in segments
+// of seg_len, segment k starting at row k * seg_stride + seg_off (the sites
+// [site0, site0 + nsites) of every component of a site-inner vector).
+struct RowMap {
+    long long seg_len = 0, seg_stride = 0, seg_off = 0;   // seg_len = 0: identity
+    __device__ __forceinline__ long long operator()(long long row) const {
+        return seg_len ? (row / seg_len) * seg_stride + seg_off + row % seg_len : row;
+    }
+};
+
 template <typename E, int G>
-__global__ void norm2_kernel(const E *__restrict__ x, long long rows, int nv, double *__restrict__ partial) {
+__global__ void norm2_kernel(const E *__restrict__ x, long long rows, int nv, double *__restrict__ partial,
+                             RowMap rm = RowMap{}) {
     extern __shared__ double sh[];
     using A = typename Acc<E>::T;
     BLAS_THREAD_SETUP
@@ -144,13 +155,13 @@ __global__ void norm2_kernel(const E *__restrict__ x, long long rows, int nv, do
         for (; row + 3 * stride < rows; row += 4 * stride) {
             cx<A> a[4][G];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) load_cx<E, G, A>(x + 2 * ((row + u * stride) * nv + vg * G), a[u]);
+            for (int u = 0; u < 4; ++u) load_cx<E, G, A>(x + 2 * (rm(row + u * stride) * nv + vg * G), a[u]);
 #pragma unroll
             for (int u = 0; u < 4; ++u) add(a[u]);
         }
         for (; row < rows; row += stride) {
             cx<A> a[1][G];
-            load_cx<E, G, A>(x + 2 * (row * nv + vg * G), a[0]);
+            load_cx<E, G, A>(x + 2 * (rm(row) * nv + vg * G), a[0]);
             add(a[0]);
         }
     }
@@ -162,7 +173,7 @@ __global__ void norm2_kernel(const E *__restrict__ x, long long rows, int nv, do
 
 template <typename E, int G>
 __global__ void dot_kernel(const E *__restrict__ x, const E *__restrict__ y, long long rows, int nv,
-                           double *__restrict__ partial) {
+                           double *__restrict__ partial, RowMap rm = RowMap{}) {
     extern __shared__ double sh[];
     using A = typename Acc<E>::T;
     BLAS_THREAD_SETUP
@@ -182,16 +193,18 @@ __global__ void dot_kernel(const E *__restrict__ x, const E *__restrict__ y, lon
             cx<A> a[4][G], b[4][G];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                load_cx<E, G, A>(x + 2 * ((row + u * stride) * nv + vg * G), a[u]);
-                load_cx<E, G, A>(y + 2 * ((row + u * stride) * nv + vg * G), b[u]);
+                const long long e = 2 * (rm(row + u * stride) * nv + vg * G);
+                load_cx<E, G, A>(x + e, a[u]);
+                load_cx<E, G, A>(y + e, b[u]);
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) add(a[u], b[u]);
         }
         for (; row < rows; row += stride) {
             cx<A> a[1][G], b[1][G];
-            load_cx<E, G, A>(x + 2 * (row * nv + vg * G), a[0]);
-            load_cx<E, G, A>(y + 2 * (row * nv + vg * G), b[0]);
+            const long long e = 2 * (rm(row) * nv + vg * G);
+            load_cx<E, G, A>(x + e, a[0]);
+            load_cx<E, G, A>(y + e, b[0]);
             add(a[0], b[0]);
         }
     }
@@ -447,6 +460,58 @@ int blas_dot_re(const dirac_op *op, dirac_prec p, const void *u, const void *v, 
             dot_kernel<E, G><<<red_grid(op), L.tb, L.sh, s>>>((const E *)u, (const E *)v, op->rows, op->nv,
                                                               op->red_partial);
             finalize_kernel<2, 1><<<1, kFinThreads, 0, s>>>(op->red_partial, red_grid(op), op->nv, out);
+            return launch_check("dot_kernel");
+        });
+    });
+}
+
+// The rows of sites [site0, site0 + nsites): one run for site-outer vectors,
+// one run per internal component for site-inner ones.
+static void site_rows(const dirac_op *op, long long site0, long long nsites, long long &first, long long &rows,
+                      RowMap &rm) {
+    const long long ncs = op->rows / op->V;
+    rows = nsites * ncs;
+    if (op->geom.layout == DIRAC_LAYOUT_SITE_OUTER) {
+        first = site0 * ncs;
+        rm = RowMap{};
+    } else {
+        first = 0;
+        rm = RowMap{nsites, op->V, site0};
+    }
+}
+
+int blas_norm2_range(const dirac_op *op, dirac_prec p, const void *v, long long site0, long long nsites, double *out,
+                     cudaStream_t s) {
+    long long first, rows;
+    RowMap rm;
+    site_rows(op, site0, nsites, first, rows, rm);
+    return dispatch_prec(p, [&](auto tag) {
+        using E = std::remove_pointer_t<decltype(tag)>;
+        const RedLaunch L = red_launch(p, op->nv, 1);
+        return dispatch_group(L.G, [&](auto gc) {
+            constexpr int G = decltype(gc)::value;
+            norm2_kernel<E, G><<<red_grid(op), L.tb, L.sh, s>>>((const E *)v + 2 * first * op->nv, rows, op->nv,
+                                                                op->red_partial, rm);
+            finalize_kernel<1, 1><<<1, kFinThreads, 0, s>>>(op->red_partial, red_grid(op), op->nv, out);
+            return launch_check("norm2_kernel");
+        });
+    });
+}
+
+int blas_dot_range(const dirac_op *op, dirac_prec p, const void *u, const void *v, long long site0, long long nsites,
+                   double *out, cudaStream_t s) {
+    long long first, rows;
+    RowMap rm;
+    site_rows(op, site0, nsites, first, rows, rm);
+    return dispatch_prec(p, [&](auto tag) {
+        using E = std::remove_pointer_t<decltype(tag)>;
+        const RedLaunch L = red_launch(p, op->nv, 2);
+        return dispatch_group(L.G, [&](auto gc) {
+            constexpr int G = decltype(gc)::value;
+            dot_kernel<E, G><<<red_grid(op), L.tb, L.sh, s>>>((const E *)u + 2 * first * op->nv,
+                                                              (const E *)v + 2 * first * op->nv, rows, op->nv,
+                                                              op->red_partial, rm);
+            finalize_kernel<2, 2><<<1, kFinThreads, 0, s>>>(op->red_partial, red_grid(op), op->nv, out);
             return launch_check("dot_kernel");
         });
     });

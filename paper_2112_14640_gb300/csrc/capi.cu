@@ -619,6 +619,36 @@ int dirac_vec_axpy(const dirac_op *op, const double *alpha_dev, const void *x, v
     return rc ? rc : blas_axpy(op, op->prec, alpha_dev, x, y, (cudaStream_t)stream);
 }
 
+int dirac_vec_axpby(const dirac_op *op, const double *a_dev, const void *x, const double *b_dev, const void *y,
+                    void *z, void *stream) {
+    if (!op || !a_dev || !b_dev) return DIRAC_ERR_INVALID_ARG;
+    int rc = check_vec(x);
+    if (!rc) rc = check_vec(y);
+    if (!rc) rc = check_vec(z);
+    return rc ? rc : blas_axpby(op, op->prec, z, x, a_dev, 1.0, y, b_dev, 1.0, nullptr, (cudaStream_t)stream);
+}
+
+static int check_range(const dirac_op *op, long long site0, long long nsites) {
+    return (site0 < 0 || nsites < 1 || site0 + nsites > op->V) ? DIRAC_ERR_INVALID_ARG : DIRAC_OK;
+}
+
+int dirac_vec_norm2_range(const dirac_op *op, const void *v, long long site0, long long nsites, double *out_dev,
+                          void *stream) {
+    if (!op || !out_dev) return DIRAC_ERR_INVALID_ARG;
+    int rc = check_vec(v);
+    if (!rc) rc = check_range(op, site0, nsites);
+    return rc ? rc : blas_norm2_range(op, op->prec, v, site0, nsites, out_dev, (cudaStream_t)stream);
+}
+
+int dirac_vec_dot_range(const dirac_op *op, const void *u, const void *v, long long site0, long long nsites,
+                        double *out_dev, void *stream) {
+    if (!op || !out_dev) return DIRAC_ERR_INVALID_ARG;
+    int rc = check_vec(u);
+    if (!rc) rc = check_vec(v);
+    if (!rc) rc = check_range(op, site0, nsites);
+    return rc ? rc : blas_dot_range(op, op->prec, u, v, site0, nsites, out_dev, (cudaStream_t)stream);
+}
+
 int dirac_vec_gamma5(const dirac_op *op, void *v, void *stream) {
     if (!op) return DIRAC_ERR_INVALID_ARG;
     int rc = check_vec(v);

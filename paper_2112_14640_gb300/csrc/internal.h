@@ -244,6 +244,10 @@ int blas_norm2(const dirac_op *op, dirac_prec p, const void *v, double *out, cud
 int blas_dot(const dirac_op *op, dirac_prec p, const void *u, const void *v, double *out, cudaStream_t s);
 // Re <u, v> per column: out[v] (N_v doubles)
 int blas_dot_re(const dirac_op *op, dirac_prec p, const void *u, const void *v, double *out, cudaStream_t s);
+int blas_norm2_range(const dirac_op *op, dirac_prec p, const void *v, long long site0, long long nsites, double *out,
+                     cudaStream_t s);
+int blas_dot_range(const dirac_op *op, dirac_prec p, const void *u, const void *v, long long site0, long long nsites,
+                   double *out, cudaStream_t s);
 int blas_axpy(const dirac_op *op, dirac_prec p, const double *alpha, const void *x, void *y, cudaStream_t s);
 // z = a x + b y per RHS; a = as * a_coef[v] (complex pairs) or as when a_coef is null (same for b);
 // x or y may be null; z may alias x or y; norm_out (device, nv doubles) receives |z|^2 if non-null.

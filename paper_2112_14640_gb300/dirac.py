@@ -90,6 +90,9 @@ SIGNATURES = {
     "dirac_vec_norm2": (_I, [_P, _P, _P, _P]),
     "dirac_vec_dot": (_I, [_P, _P, _P, _P, _P]),
     "dirac_vec_axpy": (_I, [_P, _P, _P, _P, _P]),
+    "dirac_vec_axpby": (_I, [_P, _P, _P, _P, _P, _P, _P]),
+    "dirac_vec_norm2_range": (_I, [_P, _P, ctypes.c_longlong, ctypes.c_longlong, _P, _P]),
+    "dirac_vec_dot_range": (_I, [_P, _P, _P, ctypes.c_longlong, ctypes.c_longlong, _P, _P]),
     "dirac_vec_gamma5": (_I, [_P, _P, _P]),
     "dirac_vec_convert": (_I, [_P, _P, _I, _P, _I, _P]),
     "dirac_vec_norm2_noalloc": (_I, [_P, _I, ctypes.c_longlong, _I, _P, _P]),
@@ -439,6 +442,29 @@ class DiracOp:
         _check(lib().dirac_vec_axpy(self._h, _ptr(a), self._vec(x, "x"), self._vec(y, "y"), _stream(stream)),
                "dirac_vec_axpy")
         return y
+
+    def axpby(self, a, x, b, y, z=None, stream=None):
+        """z = a x + b y per RHS (a, b: N_v complex coefficients; z may be x or y)."""
+        z = self.new_vector(zero=False) if z is None else z
+        a = a.to(device=self.device, dtype=torch.complex128).contiguous()
+        b = b.to(device=self.device, dtype=torch.complex128).contiguous()
+        _check(lib().dirac_vec_axpby(self._h, _ptr(a), self._vec(x, "x"), _ptr(b), self._vec(y, "y"),
+                                     self._vec(z, "z"), _stream(stream)), "dirac_vec_axpby")
+        return z
+
+    def norm2_range(self, v, site0, nsites, stream=None):
+        """Per-RHS |v|^2 over the sites [site0, site0 + nsites) only."""
+        out = torch.empty(self.nv, dtype=torch.float64, device=self.device)
+        _check(lib().dirac_vec_norm2_range(self._h, self._vec(v, "v"), int(site0), int(nsites), _ptr(out),
+                                           _stream(stream)), "dirac_vec_norm2_range")
+        return out
+
+    def dot_range(self, u, v, site0, nsites, stream=None):
+        """Per-RHS <u, v> over the sites [site0, site0 + nsites) only."""
+        out = torch.empty(self.nv, dtype=torch.complex128, device=self.device)
+        _check(lib().dirac_vec_dot_range(self._h, self._vec(u, "u"), self._vec(v, "v"), int(site0), int(nsites),
+                                         _ptr(out), _stream(stream)), "dirac_vec_dot_range")
+        return out
 
     def gamma5_(self, v, stream=None):
         _check(lib().dirac_vec_gamma5(self._h, self._vec(v, "v"), _stream(stream)), "dirac_vec_gamma5")

@@ -13,8 +13,10 @@ one slice in t, so one ghost slice per side is the whole halo.  An apply is
     unpack into the ghost slices      (dirac_halo_unpack)
     D on the owned slices             (dirac_apply_range)
 
-All arithmetic runs in libdirac kernels; this module marshals tensors and
-moves the packed slices.  The global boundary phase in t is folded into the
+All vector arithmetic runs in libdirac kernels; this module marshals
+tensors, moves the packed slices and, in the distributed CG, forms the N_v
+step lengths on the host from the reduced dot products (as the library's own
+CG does).  The global boundary phase in t is folded into the
 slab's links here (the slab operator itself is created periodic in t); the
 spatial phases stay with the operator (spatial extents are global).
 """
@@ -151,3 +153,89 @@ def apply_in_process(slabs, xs, outs, m0, dagger=False):
     for s, x, o in zip(slabs, xs, outs):
         s.apply_owned(x, o, m0, dagger)
     return outs
+
+
+def _reduce_sum(parts, world, group):
+    """Sum of per-slab partial reductions (device tensors of N_v entries):
+    over the slabs held here, then over the ranks (all-reduce) when world > 1."""
+    total = parts[0].clone()
+    for t in parts[1:]:
+        total += t
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(total, op=dist.ReduceOp.SUM, group=group)
+    return total
+
+
+def cg_normal(slabs, bs, m0, tol=1e-10, maxit=10000, group=None):
+    """CG on the normal equations D^dag D x = D^dag b over a slab-decomposed
+    lattice (Sec. 9's CG, one independent recurrence per RHS): every
+    application of D and D^dag exchanges the halos, every dot product runs on
+    the owned sites of each slab (dirac_vec_dot_range) and is summed over the
+    slabs -- the all-reduce of N_v scalars per dot that a distributed solver
+    adds.  `slabs`: every slab of the lattice held by this process (one GPU,
+    the exchange a device copy), or this rank's single slab (one slab per
+    rank, the exchange and the all-reduce over `group`).  bs: the slabs'
+    right-hand sides (ghost slices are ignored).  Returns (xs, iterations,
+    relative normal residual per RHS)."""
+    import numpy as np
+    R = len(slabs)
+    nslab = slabs[0].world
+    if R == nslab:
+        distributed, world = False, 1        # every slab here: sums stay local
+    elif R == 1:
+        distributed, world = True, nslab     # one slab per rank: all-reduce
+    else:
+        raise ValueError("hold every slab of the lattice, or one slab per rank")
+    nv = slabs[0].op.nv
+    dev = slabs[0].op.device
+
+    def owned(s):
+        return s.slice_sites, s.nt_local * s.slice_sites
+
+    def apply(xs, outs, dagger):
+        if distributed:
+            apply_distributed(slabs[0], xs[0], outs[0], m0, dagger, group)
+        else:
+            apply_in_process(slabs, xs, outs, m0, dagger)
+
+    def norm2(vs):
+        return _reduce_sum([s.op.norm2_range(v, *owned(s)) for s, v in zip(slabs, vs)], world, group)
+
+    def dot_re(us, vs):
+        return _reduce_sum([s.op.dot_range(u, v, *owned(s)).real.contiguous() for s, u, v in zip(slabs, us, vs)],
+                           world, group)
+
+    one = torch.ones(nv, dtype=torch.complex128, device=dev)
+    zero = torch.zeros(nv, dtype=torch.complex128, device=dev)
+    # the right-hand side D^dag b (b's halos are exchanged in a copy: b is not modified)
+    bcopy = [s.op.axpby(one, b, zero, b) for s, b in zip(slabs, bs)]
+    rhs = [s.op.new_vector() for s in slabs]
+    apply(bcopy, rhs, True)
+    xs = [s.op.new_vector() for s in slabs]
+    rs = [s.op.axpby(one, h, zero, h) for s, h in zip(slabs, rhs)]
+    ps = [s.op.axpby(one, h, zero, h) for s, h in zip(slabs, rhs)]
+    ts = [s.op.new_vector() for s in slabs]
+    aps = [s.op.new_vector() for s in slabs]
+    nb = norm2(rhs).cpu().numpy()
+    rr = nb.copy()
+    done = nb == 0
+    it = 0
+    while it < maxit and not np.all(done | (np.sqrt(rr) < tol * np.sqrt(nb))):
+        apply(ps, ts, False)
+        apply(ts, aps, True)
+        pap = dot_re(ps, aps).cpu().numpy()
+        alpha = np.where(pap > 0, rr / np.where(pap > 0, pap, 1.0), 0.0)
+        a = torch.from_numpy(alpha.astype(np.complex128)).to(dev)
+        for s, x, p, r, ap in zip(slabs, xs, ps, rs, aps):
+            s.op.axpby(one, x, a, p, x)          # x += alpha p
+            s.op.axpby(one, r, -a, ap, r)        # r -= alpha A p
+        rr_new = norm2(rs).cpu().numpy()
+        beta = np.where(rr > 0, rr_new / np.where(rr > 0, rr, 1.0), 0.0)
+        bt = torch.from_numpy(beta.astype(np.complex128)).to(dev)
+        for s, p, r in zip(slabs, ps, rs):
+            s.op.axpby(one, r, bt, p, p)         # p = r + beta p
+        rr = rr_new
+        it += 1
+    relres = np.where(nb > 0, np.sqrt(rr / np.where(nb > 0, nb, 1.0)), 0.0)
+    return xs, it, relres

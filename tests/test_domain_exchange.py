@@ -51,6 +51,40 @@ def test_exchange_ring(world):
         assert recv_hi == [10.0 * nxt + 1] * 5       # upper neighbour's first slice -> upper ghost
 
 
+def _rank_reduce(rank, world, port, out):
+    import torch
+    import torch.distributed as dist
+    from paper_2112_14640_gb300 import domain
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    # each rank's partial dot products (N_v = 3 RHS) of the slabs it holds
+    parts = [torch.tensor([1.0, 2.0, 3.0], dtype=torch.float64) * (rank + 1),
+             torch.tensor([0.5, 0.0, -1.0], dtype=torch.float64)]
+    out[rank] = domain._reduce_sum(parts[:1], world, None).tolist()
+    out[10 + rank] = parts[0].tolist()   # the input is not modified in place
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_distributed_cg_reductions_are_summed_over_ranks():
+    """The per-RHS partial reductions of the slab CG are all-reduced over the
+    ranks (gloo, world size 2); in-process slabs are summed locally."""
+    import torch
+    from paper_2112_14640_gb300 import domain
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as m:
+        out = m.dict()
+        mp.start_processes(_rank_reduce, args=(world, port, out), nprocs=world, join=True, start_method="spawn")
+        got = dict(out)
+    for r in range(world):
+        assert got[r] == [3.0, 6.0, 9.0]                  # (1 + 2) x [1, 2, 3]
+        assert got[10 + r] == [1.0 * (r + 1), 2.0 * (r + 1), 3.0 * (r + 1)]
+    a, b = torch.tensor([1.0, 2.0]), torch.tensor([3.0, -1.0])
+    assert domain._reduce_sum([a, b], 1, None).tolist() == [4.0, 1.0]
+    assert a.tolist() == [1.0, 2.0]
+
+
 def test_single_slab_exchanges_with_itself():
     import torch
     from paper_2112_14640_gb300 import domain
