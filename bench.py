@@ -485,6 +485,7 @@ def main():
         line["large_lattice"] = large_lattice_timing(D, I, torch, pk, fp32_peak)
     if not args.ncu:
         line["force"] = force_timing(D, I, torch)
+        line["link_setup"] = link_setup_timing(D, I, torch)
     if not args.ncu and not args.no_nc_sweep:
         line["nc_sweep"] = nc_sweep(D, I, torch)
     if args.solve:
@@ -617,6 +618,31 @@ def nc_sweep(D, I, torch, dims=(24, 24, 24, 48), nv=24, ncs=(2, 3, 4, 6, 8)):
         out["nc=%d" % nc] = row
         del U
         torch.cuda.empty_cache()
+    return out
+
+
+def link_setup_timing(D, I, torch, dims=(16, 16, 16, 32), nv=12):
+    """A new gauge field handed to an existing operator (dirac_op_update_links:
+    boundary phases, and for D_B the 80 path-averaged W links of every site),
+    as in every molecular-dynamics step of an HMC: time per update, FP32."""
+    import numpy as np
+    U = torch.from_numpy(I.gauge_field(dims, NC, EPS, 11)).cuda()
+    st = torch.cuda.current_stream()
+    out = {"lattice": "x".join(map(str, dims))}
+    for k in (D.WILSON, D.BRILLOUIN):
+        op = D.DiracOp(k, U, nv, BC, D.F32)
+        op.update_links(U)
+        reps = 5
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(reps):
+            op.update_links(U)
+        e1.record(st)
+        torch.cuda.synchronize()
+        out[D.KIND_NAMES[k] + "_ms"] = e0.elapsed_time(e1) / reps
+        op.close()
+    del U
+    torch.cuda.empty_cache()
     return out
 
 

@@ -98,23 +98,40 @@ __global__ void __launch_bounds__(96) build_w_kernel(const UE *__restrict__ U, E
                 for (int b = 0; b < NC; ++b) Ws[40][a * NC + b] = cx<AB>{(AB)(a == b ? 1 : 0), (AB)0};
     }
     const int pow3[4] = {1, 3, 9, 27};
+    // the last hop of the term along mu starts at n + s - s_mu mu
+    auto last_hop = [&](int mu, cx<AB> (&L)[NC][NC]) {
+        int m[4];
+        for (int nu = 0; nu < 4; ++nu) {
+            int v = x0[nu] + (nu == mu ? 0 : s[nu]);
+            m[nu] = (v + ext[nu]) % ext[nu];
+        }
+        signed_link<NC, UE, AB>(U, g, ph, m, mu, s[mu], L);
+    };
+    // N_c <= 4: every link this offset needs (one per axis it moves along) is
+    // requested before the first level, so that the four levels do not each
+    // wait for their own loads
+    constexpr bool kPreload = NC <= kMaxNcSmall;
+    cx<AB> Lpre[kPreload ? 4 : 1][NC][NC];   // by axis: compile-time indices keep them in registers
+    if constexpr (kPreload) {
+        if (dir < 81) {
+#pragma unroll
+            for (int mu = 0; mu < 4; ++mu)
+                if (s[mu] != 0) last_hop(mu, Lpre[mu]);
+        }
+    }
     __syncthreads();   // the identity at the centre feeds level 1
     for (int level = 1; level <= 4; ++level) {
         if (dir < 81 && k == level) {
             cx<AB> acc[NC][NC];
             for (int a = 0; a < NC; ++a)
                 for (int b = 0; b < NC; ++b) acc[a][b] = cx<AB>{0, 0};
+#pragma unroll
             for (int mu = 0; mu < 4; ++mu) {
                 if (s[mu] == 0) continue;
                 const int prev = dir - s[mu] * pow3[mu];   // offset s - s_mu mu
-                // last hop starts at n + s - s_mu mu
-                int m[4];
-                for (int nu = 0; nu < 4; ++nu) {
-                    int v = x0[nu] + (nu == mu ? 0 : s[nu]);
-                    m[nu] = (v + ext[nu]) % ext[nu];
-                }
-                cx<AB> L[NC][NC];
-                signed_link<NC, UE, AB>(U, g, ph, m, mu, s[mu], L);
+                cx<AB> Lrt[NC][NC];
+                if constexpr (!kPreload) last_hop(mu, Lrt);
+                const cx<AB>(&L)[NC][NC] = kPreload ? Lpre[kPreload ? mu : 0] : Lrt;
                 for (int a = 0; a < NC; ++a)
                     for (int b = 0; b < NC; ++b)
                         for (int q = 0; q < NC; ++q) cmac(acc[a][b], Ws[prev][a * NC + q], L[q][b]);
