@@ -24,6 +24,7 @@
 // Arithmetic in FP64 for FP64 operators and FP32 otherwise, like the W builder.
 #include "bril_dirs.h"
 #include "internal.h"
+#include "linkalg.cuh"
 
 namespace dgb {
 
@@ -42,11 +43,25 @@ __host__ __device__ constexpr int slot_base(int d) {
     return o;
 }
 constexpr int kSlots = 216;   // sum over offsets of their hop count
-__host__ __device__ inline int slot_of(int d, int mu) {
-    int o = slot_base(d);
-    for (int nu = 0; nu < mu; ++nu) o += comp(d, nu) != 0;
-    return o;
+// slot of the link term (d, mu), -1 where offset d does not move along mu:
+// a table in constant memory, built at compile time (computing it per call
+// took an O(d) loop of integer divisions, which made both force kernels
+// integer-bound)
+struct SlotTable {
+    short slot[81][4];
+};
+__host__ __device__ constexpr SlotTable make_slot_table() {
+    SlotTable t{};
+    for (int d = 0; d < 81; ++d) {
+        int o = slot_base(d);
+        for (int mu = 0; mu < 4; ++mu) t.slot[d][mu] = comp(d, mu) != 0 ? (short)o++ : (short)-1;
+    }
+    return t;
 }
+static __constant__ SlotTable kSlotTable = make_slot_table();
+__device__ __forceinline__ int slot_of(int d, int mu) { return kSlotTable.slot[d][mu]; }
+// x + off on a periodic axis of extent ext, off in {-1, 0, 1}
+__device__ __forceinline__ int wrap(int x, int ext) { return x < 0 ? x + ext : (x >= ext ? x - ext : x); }
 constexpr int pow3(int mu) { return mu == 0 ? 1 : mu == 1 ? 3 : mu == 2 ? 9 : 27; }
 
 template <int NC, typename E>
@@ -109,7 +124,7 @@ __global__ void __launch_bounds__(96) bril_force_site_kernel(const E *__restrict
     auto Ws = reinterpret_cast<cx<AB>(*)[NC * NC]>(bf_smem);
     auto Gs = Ws + 81;
     const long long n = blockIdx.x;
-    const int d = threadIdx.x;
+    const int d = threadIdx.x < 81 ? kLevelOrder.d[threadIdx.x] : 81;   // offsets of a level share warps
     const Coord c = site_coords(g, n);
     const int x0[4] = {c.x, c.y, c.z, c.t};
     const int ext[4] = {g.nx, g.ny, g.nz, g.nt};
@@ -132,7 +147,7 @@ __global__ void __launch_bounds__(96) bril_force_site_kernel(const E *__restrict
                 if (s[mu] == 0) continue;
                 const int prev = d - s[mu] * bforce::pow3(mu);
                 int m[4];
-                for (int nu = 0; nu < 4; ++nu) m[nu] = (x0[nu] + (nu == mu ? 0 : s[nu]) + ext[nu]) % ext[nu];
+                for (int nu = 0; nu < 4; ++nu) m[nu] = bforce::wrap(x0[nu] + (nu == mu ? 0 : s[nu]), ext[nu]);
                 cx<AB> V[NC][NC];
                 bforce::hop_link<NC, E, AB>(U, g, m, mu, s[mu], V);
                 for (int a = 0; a < NC; ++a)
@@ -150,7 +165,7 @@ __global__ void __launch_bounds__(96) bril_force_site_kernel(const E *__restrict
         const AB rho = (AB)bril::rho(k);
         const AB lam_half = (AB)(0.5 * (double)(1 << (4 - k)) / 64.0);   // lambda_k / 2, lambda = (8,4,2,1)/64
         int m[4];
-        for (int nu = 0; nu < 4; ++nu) m[nu] = (x0[nu] + s[nu] + ext[nu]) % ext[nu];
+        for (int nu = 0; nu < 4; ++nu) m[nu] = bforce::wrap(x0[nu] + s[nu], ext[nu]);
         const long long ns = (((long long)m[3] * g.nz + m[2]) * g.ny + m[1]) * g.nx + m[0];
         const long long csd = L::cs_stride(g);
         const long long pb = L::vec(g, ns, NC * 4, 0), cb = L::vec(g, n, NC * 4, 0);
@@ -159,14 +174,18 @@ __global__ void __launch_bounds__(96) bril_force_site_kernel(const E *__restrict
             for (int b = 0; b < NC; ++b) M[a][b] = cx<AB>{0, 0};
         for (int v = 0; v < g.nv; ++v) {
             cx<AB> sp[NC][4], ch[NC][4];
+#pragma unroll
             for (int a = 0; a < NC; ++a) {
                 cx<AB> p[4];
+#pragma unroll
                 for (int sg = 0; sg < 4; ++sg) {
                     p[sg] = ld1<E, AB>(psi + 2 * (pb + (long long)(a * 4 + sg) * csd + v));
                     ch[a][sg] = ld1<E, AB>(chi + 2 * (cb + (long long)(a * 4 + sg) * csd + v));
                 }
+#pragma unroll
                 for (int sg = 0; sg < 4; ++sg) {
                     cx<AB> f = {-lam_half * p[sg].re, -lam_half * p[sg].im};
+#pragma unroll
                     for (int mu = 0; mu < 4; ++mu) {
                         if (s[mu] == 0) continue;
                         const cx<AB> t = bforce::gamma_comp<AB>(mu, sg, p);
@@ -177,8 +196,11 @@ __global__ void __launch_bounds__(96) bril_force_site_kernel(const E *__restrict
                     sp[a][sg] = f;
                 }
             }
+#pragma unroll
             for (int a = 0; a < NC; ++a)
+#pragma unroll
                 for (int b = 0; b < NC; ++b)
+#pragma unroll
                     for (int sg = 0; sg < 4; ++sg) cmac(M[a][b], sp[a][sg], conj(ch[b][sg]));
         }
         for (int a = 0; a < NC; ++a)
@@ -208,7 +230,7 @@ __global__ void __launch_bounds__(96) bril_force_site_kernel(const E *__restrict
             // G_p += (1/level) V_{sign mu}(n + p) G_{p + sign mu}  over the parents of p
             const AB inv = (AB)1 / (AB)level;
             int m[4];
-            for (int nu = 0; nu < 4; ++nu) m[nu] = (x0[nu] + s[nu] + ext[nu]) % ext[nu];
+            for (int nu = 0; nu < 4; ++nu) m[nu] = bforce::wrap(x0[nu] + s[nu], ext[nu]);
             cx<AB> acc[NC][NC];
             for (int a = 0; a < NC; ++a)
                 for (int b = 0; b < NC; ++b) acc[a][b] = Gs[d][a * NC + b];
@@ -253,10 +275,11 @@ __global__ void bril_force_link_kernel(const E *__restrict__ U, const E *__restr
         if (smu == 0) continue;
         // forward hop (s_mu = +1): n = m + mu - s;  backward hop (s_mu = -1): n = m - s
         int nn[4];
+#pragma unroll
         for (int nu = 0; nu < 4; ++nu) {
             const int sn = bforce::comp(d, nu);
             const int off = (smu > 0 && nu == mu) ? 1 - sn : -sn;
-            nn[nu] = ((xm[nu] + off) % ext[nu] + ext[nu]) % ext[nu];
+            nn[nu] = bforce::wrap(xm[nu] + off, ext[nu]);
         }
         const long long n = (((long long)nn[3] * g.nz + nn[2]) * g.ny + nn[1]) * g.nx + nn[0];
         const E *x = X + 2 * ((n * bforce::kSlots + bforce::slot_of(d, mu)) * NC * NC);

@@ -7,6 +7,28 @@
 
 namespace dgb {
 
+// The 81 offsets d = (st+1)*27 + (sz+1)*9 + (sy+1)*3 + (sx+1) of the
+// 3^4 hypercube, ordered by level (the number of axes an offset moves
+// along: 8, 24, 32, 16 of them) with the centre last.  Kernels that run
+// one thread per offset and work level by level map thread t to offset
+// kLevelOrder.d[t], so that each level occupies whole warps (threads 0-31:
+// levels 1 and 2, 32-63: level 3, 64-79: level 4) instead of a few lanes of
+// every warp.
+struct LevelOrder {
+    int d[81];
+};
+__host__ __device__ constexpr LevelOrder make_level_order() {
+    LevelOrder t{};
+    int i = 0;
+    for (int k = 1; k <= 4; ++k)
+        for (int d = 0; d < 81; ++d)
+            if ((d % 3 != 1) + ((d / 3) % 3 != 1) + ((d / 9) % 3 != 1) + (d / 27 != 1) == k) t.d[i++] = d;
+    t.d[i] = 40;
+    return t;
+}
+static __constant__ LevelOrder kLevelOrder = make_level_order();
+
+
 template <typename UE>
 __device__ __forceinline__ cx<double> ld_u(const UE *U, long long idx) {
     return cx<double>{(double)U[2 * idx], (double)U[2 * idx + 1]};

@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(96) build_w_kernel(const UE *__restrict__ U, E
     extern __shared__ __align__(16) unsigned char w_smem[];
     auto Ws = reinterpret_cast<cx<AB>(*)[NC * NC]>(w_smem);
     const long long n = blockIdx.x;
-    const int dir = threadIdx.x;
+    const int dir = threadIdx.x < 81 ? kLevelOrder.d[threadIdx.x] : 81;   // offsets of a level share warps
     const Coord c = site_coords(g, n);
     const int x0[4] = {c.x, c.y, c.z, c.t};
     const int ext[4] = {g.nx, g.ny, g.nz, g.nt};
